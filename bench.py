@@ -1,0 +1,357 @@
+"""Benchmark: incremental elastoplastic load path on one GB300 through the C ABI.
+
+A step is one load step of the workload's load path: semismooth Newton to the
+relative residual tolerance (every iteration: fused return mapping + tangent
+assembly + internal forces, residual and norms, preconditioned Krylov solve,
+update) followed by the state commit.  Step j runs load step (j mod n_steps)
+of the path; the state is reset to virgin when the path wraps.  The default
+K = 40 times exactly one full 40-step load path.
+
+value = integration points assembled per second over the timed region
+        (n_int x assemblies / elapsed), i.e. the rate at which the solver
+        drives every integration point through return mapping + tangent
+        assembly, Krylov and update included.
+roofline: the dominant kernel of the step (measured with CUDA events around
+        every launch inside the timed region, on the context's stream).
+e2e:    the same metric through the C ABI with host buffers: each step
+        copies its load factor host->device and reads u_k back to the host.
+
+--impl reference times the CPU oracle (numpy/scipy, FP64) on a reduced copy
+of the workload instead; it is a deliberately slow baseline, not the target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tangent assembly Gpts/s & load-path time at 1e-10 resid: mixed vs FP64 GPU"
+UNIT = "Gpts/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 FMA pipe of a GB300: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _workload(name: str, full: bool = True):
+    from synthetic import problems as P
+    if name == "p2_plane_dp":
+        return P.p2_plane_dp() if full else P.p2_plane_dp(n=64)
+    if name == "p1_plane_vm":
+        return P.p1_plane_vm()
+    if name == "q1_cube_vm":
+        return P.q1_cube_vm() if full else P.q1_cube_vm(n=16)
+    if name == "p2_tet_strip_dp":
+        return P.p2_tet_strip_dp() if full else P.p2_tet_strip_dp(n=12)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _workload_config(name, prob, extra=None):
+    m = prob.mesh
+    cfg = {"workload": f"{name}: {m.elem_type} {m.dim}D {'x'.join(map(str, m.shape))} cells, "
+                       f"{m.n_elem} elements, {prob.n_dof} DOFs, {len(prob.zeta)} load steps",
+           "n_int": None, "newton_rtol": prob.newton_rtol,
+           "l2": "inputs larger than L2 (129 MB): K alone is " + f"{m.n_nodes} node rows"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _spmv_bytes(info, dim):
+    """Algorithmic bytes of one masked block-CSR SpMV: values + column indices + row pointers +
+    x read once + y written once + free mask."""
+    nnzb, n_rows = info.nnz_blocks, info.n_nodes
+    n = n_rows * dim
+    return nnzb * (dim * dim * 8 + 4) + (n_rows + 1) * 4 + n * 8 * 2 + n
+
+
+def _assembly_bytes(info, dim, n_p, n_comp):
+    """Algorithmic bytes of one fused assembly launch (split or full form): cached gradients and
+    weights, connectivity, slot map, displacement gather, state read, F and K block updates."""
+    n_int, n_e = info.n_int, info.n_elem
+    return (n_int * (n_p * dim + 1) * 8 + n_e * n_p * 4 + n_e * n_p * n_p * 4 + n_e * n_p * dim * 8
+            + n_int * (n_comp + 1) * 8 + info.n_nodes * dim * 8 * 2 + info.nnz_blocks * dim * dim * 8 * 2)
+
+
+def _assembly_flops(info, dim, n_p, n_q, sym):
+    """FP64 FLOPs of the local tangents per assembly: H = (wD)G per point and node, K blocks."""
+    ns = 3 if dim == 2 else 6
+    h = n_p * ns * dim * (2 if dim == 2 else 3) * 2
+    nb = n_p * (n_p + 1) // 2 if sym else n_p * n_p
+    kb = nb * dim * dim * (2 if dim == 2 else 3) * 2
+    return info.n_int * h + info.n_elem * n_q * kb
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on a reduced copy of the workload."""
+    from oracle.newton import OracleSolver
+    prob = _workload(args.workload, full=False)
+    s = OracleSolver(prob)
+    n_path = len(prob.zeta)
+    for j in range(args.warmup):
+        s.solve_step(float(prob.zeta[j % n_path]), tol=prob.newton_rtol)
+    s = OracleSolver(prob)
+    t0 = time.perf_counter()
+    assemblies = 0
+    for j in range(args.steps):
+        if j > 0 and j % n_path == 0:
+            s = OracleSolver(prob)
+        r = s.solve_step(float(prob.zeta[j % n_path]), tol=prob.newton_rtol)
+        assemblies += r.newton_its + 1
+    dt = time.perf_counter() - t0
+    n_int = s.geom.n_int
+    value = n_int * assemblies / dt / 1e9
+    sample = (f"oracle on a reduced copy ({prob.mesh.elem_type} {prob.mesh.dim}D "
+              f"{'x'.join(map(str, prob.mesh.shape))}, {n_int} points), {args.steps} load steps, splu solves")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload_config(args.workload, prob, {"n_int": n_int}), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        blas = max((i.get("num_threads", 1) for i in info), default=1)
+    except Exception:
+        blas = 1
+    return int(blas)
+
+
+def cpu_baseline(args, budget_s=15.0):
+    """Oracle IP-assembly throughput on a bounded sample: reduced copy, as many load steps as fit."""
+    from oracle.newton import OracleSolver
+    prob = _workload(args.workload, full=False)
+    s = OracleSolver(prob)
+    t0 = time.perf_counter()
+    assemblies, steps = 0, 0
+    for z in prob.zeta:
+        r = s.solve_step(float(z), tol=prob.newton_rtol)
+        assemblies += r.newton_its + 1
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": s.geom.n_int * assemblies / dt / 1e9, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"first {steps} load steps of a reduced copy ({prob.mesh.elem_type} "
+                      f"{'x'.join(map(str, prob.mesh.shape))}, {s.geom.n_int} points), splu solves, "
+                      f"{dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="p2_plane_dp")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1805_04155_gb300 import build as B
+    B.build()
+    import paper_1805_04155_gb300.ep as ep
+
+    prob = _workload(args.workload)
+    stream = torch.cuda.current_stream()
+    ctx = ep.Context.from_problem(prob, device=local, stream=stream)
+    info = ctx.info
+    n_path = len(prob.zeta)
+    opts = ep.default_opts(newton_rtol=prob.newton_rtol, profile=1)
+    zeros = {f: np.zeros(*ctx.field_shape(f)) for f in (ep.EP_U, ep.EP_PLASTIC_STRAIN, ep.EP_HARDENING,
+                                                          ep.EP_STRESS, ep.EP_PLASTIC_FLAG)}
+
+    def reset():
+        for f, v in zeros.items():
+            ctx.set(f, v)
+
+    # warm-up: first W load steps, then back to the virgin state
+    for j in range(args.warmup):
+        ctx.solve_load_path([prob.zeta[j % n_path]], opts)
+    reset()
+
+    def timed(e2e: bool):
+        reps = []
+        u_host = np.empty(ctx.n_dof) if e2e else None
+        zbuf = np.empty(1)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_wall0 = time.perf_counter()
+        ev0.record(stream)
+        for j in range(args.steps):
+            if j > 0 and j % n_path == 0:
+                reset()
+            zbuf[0] = prob.zeta[j % n_path]
+            reps.extend(ctx.solve_load_path(zbuf, opts))
+            if e2e:
+                ctx.get(ep.EP_U, out=u_host)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = ev0.elapsed_time(ev1)
+        wall = time.perf_counter() - t_wall0
+        return ms, wall, reps
+
+    clocks = Clocks(local)
+    ms, wall, reps = timed(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    assemblies = sum(r.n_assemble for r in reps)
+    n_int = info.n_int
+    value = world * n_int * assemblies / (ms / 1e3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        reset()
+        ms_e2e, _, reps_e2e = timed(True)
+        a2 = sum(r.n_assemble for r in reps_e2e)
+        e2e = {"value": world * n_int * a2 / (ms_e2e / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8,
+               "d2h_bytes_per_step": int(ctx.n_dof * 8)}
+
+    # roofline of the dominant kernel (the SpMV inside the Krylov solves, or the assembly)
+    dim = info.dim
+    peaks, peaks_kind = _peaks()
+    t_spmv = sum(r.t_spmv_kernel_ms for r in reps)
+    n_spmv = sum(r.n_spmv for r in reps)
+    t_asmk = sum(r.t_assemble_kernel_ms for r in reps)
+    sym = prob.material.model != 3
+    roof_spmv = roof_asm = None
+    if n_spmv:
+        dur = t_spmv / n_spmv / 1e3
+        by = _spmv_bytes(info, dim)
+        gbs = by / dur / 1e9
+        fl = 2.0 * info.nnz_blocks * dim * dim / dur / 1e12
+        roof_spmv = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "k_spmv (masked block-CSR, FP64)", "launches": n_spmv, "avg_us": dur * 1e6,
+                     "bytes_per_launch": by, "fp64_tflops": fl, "fp64_frac": fl / FP64_PEAK_TFLOPS,
+                     "peak_source": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)", "share_of_step": t_spmv / ms}
+    if assemblies:
+        dur = t_asmk / assemblies / 1e3
+        fl = _assembly_flops(info, dim, info.n_p, info.n_q, sym) / dur / 1e12
+        by = _assembly_bytes(info, dim, info.n_p, info.n_comp)
+        roof_asm = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": fl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_assemble (fused, FP64)",
+                    "launches": assemblies, "avg_us": dur * 1e6, "hbm_gbs": by / dur / 1e9,
+                    "hbm_frac": by / dur / 1e9 / peaks["hbm_gbs"],
+                    "assembled_gpts_s": n_int / dur / 1e9,
+                    "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
+                    "share_of_step": t_asmk / ms}
+    dominant = roof_spmv if (roof_spmv and t_spmv >= t_asmk) else roof_asm
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload_config(args.workload, prob, {
+                "n_int": n_int, "parallelism": "replicas" if world > 1 else "single GPU",
+                "krylov": "BiCGStab" if prob.material.model == 3 and prob.material.psi != prob.material.phi
+                else "CG", "precond": "block Jacobi", "split_elastic_cache": True}),
+            "roofline": dominant, "roofline_assembly": roof_asm, "roofline_spmv": roof_spmv,
+            "clocks": clk, "gpu_launches": int(sum(r.launches for r in reps)),
+            "load_path_s": ms / 1e3 * n_path / args.steps,
+            "newton_its": int(sum(r.newton_its for r in reps)), "krylov_its": int(sum(r.krylov_its for r in reps)),
+            "n_plastic_final": int(reps[-1].n_plastic) if reps else 0,
+            "max_rel_resid": max(r.rel_resid for r in reps) if reps else None,
+            "wall_s": wall}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

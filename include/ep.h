@@ -1,0 +1,243 @@
+/*
+ * ep.h -- C ABI of the GB300 elastoplastic hot path.
+ *
+ * The library solves the incremental elastoplastic problem (P_k) of Section 1
+ * (eq. (eqn)) by the finite element method of Section 3 and the semismooth
+ * Newton method ALG-NEWTON of Section 4.  Every Newton iteration evaluates the
+ * stress-strain operator T_k and its consistent tangent T_k^o at all
+ * integration points (Sections 2.2, 2.3), assembles the internal forces F and
+ * the tangent stiffness K = B^T W D_p B (Section 7, eq. (K-split); Section 9,
+ * eq. (K-split_Petr)) into a block-CSR pattern fixed by the mesh, and solves
+ * eq. (lin_syst) on the free DOFs with a preconditioned Krylov method.
+ *
+ * Conventions (Section 5):
+ *   - DOF index = dim*node + component (the ordering of U(:)).
+ *   - Integration point index = element*n_q + q.
+ *   - Voigt order, 3D: (11,22,33,12,23,13); stresses stress-type, strains
+ *     and plastic strains strain-type (engineering shear).
+ *   - Plane strain (dim = 2) stores n_comp = 4 components per point in the
+ *     order (11,22,12,33); 3D stores n_comp = 6.
+ *   - Per-point fields are structure-of-arrays: [n_comp][n_int].
+ *
+ * Memory and errors:
+ *   - Inputs passed to ep_create are host arrays, copied during the call; the
+ *     caller keeps ownership.  The library owns every device buffer of a
+ *     context and frees them in ep_destroy.
+ *   - Every function returns an ep_status and never aborts or traps.  The
+ *     message of the last failure of a context is available from
+ *     ep_last_error.  A load step that fails leaves the state at the last
+ *     converged step.
+ *   - All device work of a context runs on the CUDA stream given to
+ *     ep_create; one context must not be used from two host threads at once.
+ */
+#ifndef EP_H
+#define EP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EP_OK = 0,
+    EP_ERR_INVALID_ARG = 1,          /* bad pointer, size, enum value or node index */
+    EP_ERR_CUDA = 2,                 /* a CUDA runtime call failed; see ep_last_error */
+    EP_ERR_OOM = 3,                  /* device allocation failed */
+    EP_ERR_BAD_ELEMENT = 4,          /* det J <= 0 at an integration point (Section 6.1) */
+    EP_ERR_RETURN_MAP = 5,           /* Drucker-Prager apex with K*eta*eta_bar + Hc = 0: no admissible stress */
+    EP_ERR_NEWTON_NO_CONVERGENCE = 6,/* newton_maxit reached */
+    EP_ERR_KRYLOV = 7,               /* Krylov iteration cap or breakdown */
+    EP_ERR_NAN = 8,                  /* NaN/Inf in a residual norm */
+    EP_ERR_STATE = 9                 /* call out of order (e.g. no assembled matrix) */
+} ep_status;
+
+/* Element families of the Appendix (3D) and their plane analogues (2D). */
+typedef enum { EP_P1 = 0, EP_P2 = 1, EP_Q1 = 2, EP_Q2 = 3 } ep_elem;
+
+/* Constitutive models (Sections 2.2, 2.3 and their extensions). */
+typedef enum {
+    EP_ELASTIC = 0,   /* T = C eps (eq. (elastic_operator)) */
+    EP_VM_KIN = 1,    /* von Mises, linear kinematic hardening a = H (eqs. (T_kinematic), (DT_kinematic)) */
+    EP_VM_ISO = 2,    /* von Mises, linear isotropic hardening: |s| <= Y + H*alpha */
+    EP_DP = 3         /* Drucker-Prager; nonassociated (psi != phi) and cohesion hardening Hc optional */
+} ep_model;
+
+typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
+
+/* Mesh (Section 6: ELEM and COORD).  Host pointers, copied by ep_create. */
+typedef struct {
+    int32_t dim;                 /* 2 (plane strain) or 3 */
+    int32_t elem;                /* ep_elem */
+    int64_t n_nodes;
+    int64_t n_elem;
+    const double* coords;        /* [n_nodes][dim] */
+    const int32_t* elem_nodes;   /* [n_elem][n_p], 0-based, reference node order of the Appendix */
+} ep_mesh;
+
+/* Material (Sections 2.2, 2.3, 8.3).  K = E/(3(1-2nu)), G = E/(2(1+nu)). */
+typedef struct {
+    int32_t model;               /* ep_model */
+    double E, nu;
+    double Y, H;                 /* von Mises: yield value (Frobenius norm of the deviator) and hardening modulus */
+    double c0, phi, psi, Hc;     /* Drucker-Prager: cohesion, friction and dilatancy angles [rad], cohesion hardening */
+} ep_material;
+
+/* Boundary conditions and loads (Section 4: u_D, f).  Host pointers, copied. */
+typedef struct {
+    const uint8_t* dirichlet_mask;  /* [n_nodes*dim], 1 = prescribed DOF (complement of Q, Section 5) */
+    const double* u_D_unit;         /* [n_nodes*dim], prescribed values at zeta = 1 (NULL = zero) */
+    const double* f_ext_unit;       /* [n_nodes*dim], external load vector at zeta = 1 (NULL = zero) */
+} ep_bc;
+
+typedef struct {
+    int32_t precision;           /* ep_precision (EP_FP64 only in this version) */
+    double newton_rtol;          /* ||(f - F)_free|| <= rtol * max(||f_free||, ||F||) */
+    int32_t newton_maxit;
+    int32_t krylov;              /* 0 auto (CG if the tangent is symmetric, else BiCGStab), 1 CG, 2 BiCGStab */
+    double krylov_rtol;          /* > 0: fixed relative tolerance; 0: adaptive forcing term */
+    int32_t krylov_maxit;
+    int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks) */
+    int32_t split_elastic_cache; /* 1: K = K_elast + sum over plastic points (eq. (K-split)); 0: K = B^T D B */
+    int32_t warm_start;          /* 0: last converged u; 1: linear extrapolation of the last two steps */
+    int32_t profile;             /* 1: time the assembly and SpMV kernels with CUDA events (fills t_*_kernel_ms) */
+} ep_opts;
+
+typedef struct {
+    int32_t newton_its;
+    int32_t krylov_its;          /* summed over the step's linear solves */
+    int64_t n_plastic;           /* plastic integration points after the step */
+    double rel_resid;
+    double t_assemble_ms, t_solve_ms, t_step_ms;
+    int32_t status;              /* ep_status of the step */
+    int32_t launches;            /* kernels of this library launched during the step */
+    int32_t n_assemble;          /* assembly kernel launches */
+    int32_t n_spmv;              /* SpMV kernel launches that did work (profile = 1) */
+    double t_assemble_kernel_ms; /* summed duration of the assembly kernel launches (profile = 1) */
+    double t_spmv_kernel_ms;     /* summed duration of those SpMV launches (profile = 1) */
+} ep_step_report;
+
+/* Fields readable with ep_get / writable with ep_set. */
+typedef enum {
+    EP_U = 0,                /* double [n_nodes*dim], displacements u_k */
+    EP_STRESS = 1,           /* double [n_comp][n_int], committed stress sigma_k */
+    EP_PLASTIC_STRAIN = 2,   /* double [n_comp][n_int], committed eps^p_k (strain-type) */
+    EP_HARDENING = 3,        /* double [n_int] (alpha) or [n_comp][n_int] (back stress, EP_VM_KIN) */
+    EP_PLASTIC_FLAG = 4,     /* uint8 [n_int]: 0 elastic, 1 plastic (DP: 1 smooth, 2 apex) */
+    EP_F_INT = 5,            /* double [n_nodes*dim], internal forces F of the last assembly (read only) */
+    EP_K_ROW_PTR = 6,        /* int32 [n_nodes+1], block-CSR row pointers (read only) */
+    EP_K_COL_IDX = 7,        /* int32 [nnz_blocks], block column (node) indices (read only) */
+    EP_K_VALUES = 8,         /* double [nnz_blocks][dim][dim], K of the last assembly, row-major blocks (read only) */
+    EP_K_ELASTIC = 9,        /* double [nnz_blocks][dim][dim], K_elast (read only) */
+    EP_WEIGHT = 10,          /* double [n_int], |det J| w_q (Section 6.3, WEIGHT) (read only) */
+    EP_DPHI = 11,            /* double [n_int][n_p][dim], physical basis gradients (Section 6.1, DPhi) (read only) */
+    EP_SOLUTION = 12         /* double [n_nodes*dim], x of the last ep_linear_solve (read only) */
+} ep_field;
+
+/* Sizes of a context: n_int, n_comp, nnz_blocks, n_p, n_q. */
+typedef struct {
+    int64_t n_nodes, n_elem, n_int, nnz_blocks;
+    int32_t dim, n_p, n_q, n_comp;
+} ep_info;
+
+/* Fill *opts with defaults (FP64, rtol 1e-10, adaptive Krylov, block Jacobi, split on, no profiling). */
+void ep_default_opts(ep_opts* opts);
+
+/*
+ * Create a context: copy the mesh, material, BCs and loads to the device on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream) of `device`,
+ * build the block-CSR pattern of K and the element-to-slot map, compute the
+ * per-point geometry (Section 6.1: J, det J, J^-1, DPhi, WEIGHT) and assemble
+ * K_elast = B^T D_elast B (Section 6.3).  The state starts virgin (u = 0,
+ * eps^p = 0, hardening 0).  Errors: EP_ERR_INVALID_ARG for bad sizes/indices,
+ * EP_ERR_BAD_ELEMENT if det J <= 0 anywhere, EP_ERR_OOM, EP_ERR_CUDA.  On error
+ * *out is NULL.
+ */
+ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, const ep_bc* bc,
+                    int32_t device, void* cuda_stream);
+
+ep_status ep_destroy(void* ctx);
+
+ep_status ep_get_info(const void* ctx, ep_info* info);
+
+/*
+ * Solve load steps k = 1..n_steps with load factors zeta[k] (host array):
+ * f_k = zeta_k f_ext_unit, u_{D,k} = zeta_k u_D_unit, ALG-NEWTON (Section 4) to
+ * opts->newton_rtol, then commit eps^p_k and the hardening variable (Sections
+ * 2.1, 2.2, 2.3).  `reports` is a caller-allocated host array [n_steps] (may be
+ * NULL).  Stops at the first failing step and returns its status; earlier
+ * steps stay committed.  Continues from the context's current state, so
+ * consecutive calls continue one load path.
+ */
+ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, const ep_opts* opts,
+                             ep_step_report* reports);
+
+/*
+ * Copy a field (ep_field) to `dst` (host, or device when dst_is_device != 0).
+ * `bytes` must equal the field's size.  Synchronises the context's stream.
+ */
+ep_status ep_get(void* ctx, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
+
+/*
+ * Overwrite a state field (EP_U, EP_PLASTIC_STRAIN, EP_HARDENING, EP_STRESS,
+ * EP_PLASTIC_FLAG) from `src` (host or device).  Used to resume from a saved
+ * state and to evaluate K and F at a given iterate.
+ */
+ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_t src_is_device);
+
+/*
+ * One evaluation of the hot path at displacement u (host or device array
+ * [n_nodes*dim]) with the committed state as eps^p_{k-1}: strains (Section
+ * 6.2), return mapping (Sections 2.2, 2.3), internal forces F = B^T (W S) and
+ * the tangent K (Section 7).  split != 0 uses K = K_elast + B^T (D_t - D_e) B
+ * over plastic points only (eq. (K-split)); split == 0 sums B^T D_t B over all
+ * points (eq. (K-split_Petr)).  Results stay on the device (EP_F_INT,
+ * EP_K_VALUES); *n_plastic (may be NULL) receives the number of plastic points.
+ */
+ep_status ep_assemble(void* ctx, const double* u, int32_t u_is_device, int32_t split, int64_t* n_plastic);
+
+/*
+ * Commit the state at displacement u (host or device): evaluate the return
+ * mapping at every point and store sigma_k, eps^p_k, the hardening variable
+ * and the plastic flags (Sections 2.2, 2.3, the T_other updates) as the new
+ * committed state; u becomes EP_U.
+ */
+ep_status ep_commit(void* ctx, const double* u, int32_t u_is_device);
+
+/*
+ * Solve K x = b on the free DOFs with the matrix of the last ep_assemble
+ * (eq. (lin_syst)); b is a host or device array [n_nodes*dim] (prescribed
+ * entries ignored), x is kept as EP_SOLUTION (zero on prescribed DOFs).  Uses
+ * opts->krylov, krylov_rtol (must be > 0 here), krylov_maxit, precond.
+ * *iterations and *rel_resid (may be NULL) receive the iteration count and
+ * the final ||b - K x|| / ||b|| on the free DOFs.
+ */
+ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const ep_opts* opts,
+                          int32_t* iterations, double* rel_resid);
+
+/*
+ * Stand-alone return mapping on device arrays (Sections 2.2, 2.3): for n
+ * points with strains E [n_strain][n] (n_strain = 3 in 2D: e11,e22,2e12;
+ * 6 in 3D), previous plastic strain ep_prev [n_comp][n] and hardening
+ * hard_prev ([n] or [n_comp][n] for EP_VM_KIN), write the stress S
+ * [n_comp][n], the tangent DS [n_strain][n_strain][n] (row = stress, column =
+ * strain component), the flag [n], and the trial state ep_new, hard_new
+ * (same shapes as the inputs).  Runs on `cuda_stream`; does not synchronise.
+ * EP_ERR_RETURN_MAP is reported only through flag value 255 at failing points.
+ */
+ep_status ep_constitutive(const ep_material* mat, int32_t dim, int64_t n, const double* E,
+                          const double* ep_prev, const double* hard_prev, double* S, double* DS,
+                          uint8_t* flag, double* ep_new, double* hard_new, void* cuda_stream);
+
+/* Human-readable name of a status code. */
+const char* ep_status_str(int32_t status);
+/* Message of the last failure of `ctx`; with ctx == NULL, the message of the
+ * last failed ep_create on the calling thread. */
+const char* ep_last_error(const void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EP_H */

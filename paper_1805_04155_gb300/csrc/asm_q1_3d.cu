@@ -1,0 +1,5 @@
+// Hot-path kernels instantiated for the Q1_3D element (one translation unit per
+// element type keeps the build parallel).
+#include "assemble.cuh"
+
+EP_DEFINE_ELEM_LAUNCHERS(6)

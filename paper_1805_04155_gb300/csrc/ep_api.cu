@@ -1,0 +1,812 @@
+// C-ABI entry points and the Newton / load-path driver (Section 4, ALG-NEWTON).
+//
+// Each Newton iteration on the device: assemble F(u) and K(u) (fused kernel,
+// Section 7), residual r = f_k - F on the free DOFs with its norms, Krylov
+// solve of K dr = r (eq. (lin_syst)), update u += du.  After convergence the
+// state is committed (Sections 2.2, 2.3).  The only per-iteration device-to-
+// host traffic is the three residual norms and the Krylov record.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ep_internal.h"
+
+namespace ep {
+
+cudaError_t launch_assemble_0(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_1(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_2(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_3(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_4(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_5(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_6(const AsmArgs&, cudaStream_t);
+cudaError_t launch_assemble_7(const AsmArgs&, cudaStream_t);
+cudaError_t launch_commit_0(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_1(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_2(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_3(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_4(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_5(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_6(const CommitArgs&, cudaStream_t);
+cudaError_t launch_commit_7(const CommitArgs&, cudaStream_t);
+cudaError_t launch_geometry_0(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_1(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_2(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_3(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_4(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_5(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_6(const GeomArgs&, cudaStream_t);
+cudaError_t launch_geometry_7(const GeomArgs&, cudaStream_t);
+
+cudaError_t launch_assemble(int id, const AsmArgs& a, cudaStream_t s) {
+    switch (id) {
+        case 0: return launch_assemble_0(a, s);
+        case 1: return launch_assemble_1(a, s);
+        case 2: return launch_assemble_2(a, s);
+        case 3: return launch_assemble_3(a, s);
+        case 4: return launch_assemble_4(a, s);
+        case 5: return launch_assemble_5(a, s);
+        case 6: return launch_assemble_6(a, s);
+        case 7: return launch_assemble_7(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t launch_commit(int id, const CommitArgs& a, cudaStream_t s) {
+    switch (id) {
+        case 0: return launch_commit_0(a, s);
+        case 1: return launch_commit_1(a, s);
+        case 2: return launch_commit_2(a, s);
+        case 3: return launch_commit_3(a, s);
+        case 4: return launch_commit_4(a, s);
+        case 5: return launch_commit_5(a, s);
+        case 6: return launch_commit_6(a, s);
+        case 7: return launch_commit_7(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t launch_geometry(int id, const GeomArgs& a, cudaStream_t s) {
+    switch (id) {
+        case 0: return launch_geometry_0(a, s);
+        case 1: return launch_geometry_1(a, s);
+        case 2: return launch_geometry_2(a, s);
+        case 3: return launch_geometry_3(a, s);
+        case 4: return launch_geometry_4(a, s);
+        case 5: return launch_geometry_5(a, s);
+        case 6: return launch_geometry_6(a, s);
+        case 7: return launch_geometry_7(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Material constants: K, G from E, nu; Drucker-Prager eta, c, eta_bar from
+// (c0, phi, psi) by the 3D or plane-strain formulas of Section 8.3.
+bool make_matconst(const ep_material& m, int dim, MatConst& out, std::string& err) {
+    if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5)) {
+        err = "material: need E > 0 and -1 < nu < 0.5";
+        return false;
+    }
+    if (m.model < 0 || m.model > 3) {
+        err = "material: unknown model";
+        return false;
+    }
+    out = MatConst{};
+    out.model = m.model;
+    out.K = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+    out.G = m.E / (2.0 * (1.0 + m.nu));
+    out.Y = m.Y;
+    out.H = m.H;
+    if ((m.model == 1 || m.model == 2) && (!(m.Y > 0.0) || !(m.H >= 0.0))) {
+        err = "material: von Mises needs Y > 0 and H >= 0";
+        return false;
+    }
+    if (m.model == 3) {
+        if (!(m.c0 >= 0.0) || !(m.phi >= 0.0 && m.phi < 1.5707963267948966) || !(m.psi >= 0.0 && m.psi < 1.5707963267948966) ||
+            !(m.Hc >= 0.0)) {
+            err = "material: Drucker-Prager needs c0 >= 0, 0 <= phi, psi < pi/2, Hc >= 0";
+            return false;
+        }
+        if (dim == 3) {
+            const double sp = std::sin(m.phi), ss = std::sin(m.psi);
+            out.eta = 6.0 * sp / (std::sqrt(3.0) * (3.0 + sp));
+            out.c = m.c0 * 6.0 * std::cos(m.phi) / (std::sqrt(3.0) * (3.0 + sp));
+            out.eta_bar = 6.0 * ss / (std::sqrt(3.0) * (3.0 + ss));
+        } else {
+            const double tp = std::tan(m.phi), ts = std::tan(m.psi);
+            const double qp = std::sqrt(9.0 + 12.0 * tp * tp), qs = std::sqrt(9.0 + 12.0 * ts * ts);
+            out.eta = 3.0 * tp / qp;
+            out.c = 3.0 * m.c0 / qp;
+            out.eta_bar = 3.0 * ts / qs;
+        }
+        out.Hc = m.Hc;
+    }
+    return true;
+}
+
+struct Ctx {
+    std::string err;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 152;
+    int dim = 0, family = 0, eid = 0, n_p = 0, n_q = 0, n_comp = 0;
+    int64_t n_nodes = 0, n_elem = 0, n_int = 0, n_dof = 0, nnzb = 0, hard_len = 0;
+    MatConst mat{};
+    // mesh and pattern
+    double* coords = nullptr;
+    int32_t *elem = nullptr, *slots = nullptr, *row_ptr = nullptr, *col_idx = nullptr, *diag_slot = nullptr;
+    double *dphi = nullptr, *wgt = nullptr;
+    double *Kel = nullptr, *Kt = nullptr;
+    // state
+    double *ep = nullptr, *hard = nullptr, *sig = nullptr;
+    uint8_t* flag = nullptr;
+    // vectors
+    double *u = nullptr, *u_prev = nullptr, *u_it = nullptr, *F = nullptr, *r = nullptr;
+    double *f_unit = nullptr, *uD_unit = nullptr;
+    uint8_t* free_dof = nullptr;
+    // scalars
+    unsigned long long* counter = nullptr;
+    int* err_flag = nullptr;
+    double* norms = nullptr;        // device [3]
+    double* norms_host = nullptr;   // pinned [3]
+    unsigned long long* counter_host = nullptr;
+    int* err_host = nullptr;
+    KrylovWork kw{};
+    bool K_valid = false;
+    int n_committed = 0;
+    double zeta_last = 0.0, zeta_prev = 0.0;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int launches = 0;          // kernels launched (instrumentation)
+    int profile = 0;
+    std::vector<void*> allocs;
+};
+
+static ep_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? EP_ERR_OOM : EP_ERR_CUDA;
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, #call);      \
+    } while (0)
+
+template <class T>
+static cudaError_t dalloc(Ctx* c, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e == cudaSuccess) c->allocs.push_back((void*)*p);
+    return e;
+}
+
+static MeshDev mesh_dev(const Ctx* c) {
+    MeshDev m;
+    m.n_nodes = c->n_nodes;
+    m.n_elem = c->n_elem;
+    m.n_int = c->n_int;
+    m.elem_nodes = c->elem;
+    m.slots = c->slots;
+    m.dphi = c->dphi;
+    m.wgt = c->wgt;
+    return m;
+}
+
+static StateDev state_dev(const Ctx* c) { return StateDev{c->ep, c->hard, c->sig, c->flag}; }
+
+static BsrDev bsr_dev(const Ctx* c, const double* vals) {
+    BsrDev b;
+    b.n_rows = c->n_nodes;
+    b.dim = c->dim;
+    b.row_ptr = c->row_ptr;
+    b.col_idx = c->col_idx;
+    b.diag_slot = c->diag_slot;
+    b.vals = vals;
+    b.free_dof = c->free_dof;
+    return b;
+}
+
+// Assemble F and K at u_dev with the committed state.  split: K = K_elast + plastic deltas.
+static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K) {
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->F, 0, sizeof(double) * c->n_dof, s));
+    CK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
+    const size_t kbytes = sizeof(double) * (size_t)c->nnzb * c->dim * c->dim;
+    if (want_K) {
+        if (split) CK(cudaMemcpyAsync(c->Kt, c->Kel, kbytes, cudaMemcpyDeviceToDevice, s));
+        else CK(cudaMemsetAsync(c->Kt, 0, kbytes, s));
+    }
+    AsmArgs a{};
+    a.mesh = mesh_dev(c);
+    a.mat = c->mat;
+    a.state = state_dev(c);
+    a.u = u_dev;
+    a.F = c->F;
+    a.Kvals = c->Kt;
+    a.mode = split ? ASM_DELTA : ASM_FULL;
+    a.want_K = want_K ? 1 : 0;
+    a.elastic_only = 0;
+    a.n_plastic = c->counter;
+    a.err_flag = c->err_flag;
+    if (c->profile) CK(cudaEventRecord(c->ev[4], s));
+    CK(launch_assemble(c->eid, a, s));
+    if (c->profile) CK(cudaEventRecord(c->ev[5], s));
+    c->launches += 1;
+    c->K_valid = want_K;
+    return EP_OK;
+}
+
+static ep_status read_flags(Ctx* c, unsigned long long* n_plastic, bool* rm_err) {
+    CK(cudaMemcpyAsync(c->counter_host, c->counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_plastic) *n_plastic = *c->counter_host;
+    if (rm_err) *rm_err = *c->err_host != 0;
+    return EP_OK;
+}
+
+static ep_status commit(Ctx* c, const double* u_dev, unsigned long long* n_plastic) {
+    CK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), c->stream));
+    CommitArgs a{};
+    a.mesh = mesh_dev(c);
+    a.mat = c->mat;
+    a.state = state_dev(c);
+    a.u = u_dev;
+    a.n_plastic = c->counter;
+    a.err_flag = c->err_flag;
+    CK(launch_commit(c->eid, a, c->stream));
+    c->launches += 1;
+    bool rm_err = false;
+    ep_status st = read_flags(c, n_plastic, &rm_err);
+    if (st != EP_OK) return st;
+    if (rm_err) {
+        c->err = "return mapping: apex reached with K*eta*eta_bar + Hc = 0 (no admissible stress)";
+        return EP_ERR_RETURN_MAP;
+    }
+    return EP_OK;
+}
+
+static int krylov_method(const Ctx* c, const ep_opts& o) {
+    if (o.krylov == 1 || o.krylov == 2) return o.krylov;
+    const bool sym = c->mat.model != 3 || (c->mat.eta == c->mat.eta_bar && c->mat.Hc == 0.0);
+    return sym ? 1 : 2;
+}
+
+}  // namespace ep
+
+using namespace ep;
+
+// message of the last failed ep_create on this thread (no context exists then)
+static thread_local std::string g_create_err;
+
+extern "C" {
+
+void ep_default_opts(ep_opts* o) {
+    if (!o) return;
+    o->precision = EP_FP64;
+    o->newton_rtol = 1e-10;
+    o->newton_maxit = 25;
+    o->krylov = 0;
+    o->krylov_rtol = 0.0;
+    o->krylov_maxit = 20000;
+    o->precond = 1;
+    o->split_elastic_cache = 1;
+    o->warm_start = 1;
+    o->profile = 0;
+}
+
+const char* ep_status_str(int32_t s) {
+    switch (s) {
+        case EP_OK: return "ok";
+        case EP_ERR_INVALID_ARG: return "invalid argument";
+        case EP_ERR_CUDA: return "CUDA error";
+        case EP_ERR_OOM: return "out of device memory";
+        case EP_ERR_BAD_ELEMENT: return "element with det J <= 0";
+        case EP_ERR_RETURN_MAP: return "return mapping failed (no admissible stress)";
+        case EP_ERR_NEWTON_NO_CONVERGENCE: return "Newton did not converge";
+        case EP_ERR_KRYLOV: return "Krylov solver failed";
+        case EP_ERR_NAN: return "NaN or Inf in a residual";
+        case EP_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* ep_last_error(const void* ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return static_cast<const Ctx*>(ctx)->err.c_str();
+}
+
+ep_status ep_destroy(void* ctx) {
+    if (!ctx) return EP_OK;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocs) cudaFree(p);
+    krylov_free(c->kw);
+    if (c->norms_host) cudaFreeHost(c->norms_host);
+    if (c->counter_host) cudaFreeHost(c->counter_host);
+    if (c->err_host) cudaFreeHost(c->err_host);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    cudaSetDevice(prev);
+    delete c;
+    return EP_OK;
+}
+
+ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, const ep_bc* bc, int32_t device,
+                    void* cuda_stream) {
+    if (!out) return EP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mesh || !mat || !bc || !mesh->coords || !mesh->elem_nodes || !bc->dirichlet_mask) return EP_ERR_INVALID_ARG;
+    if ((mesh->dim != 2 && mesh->dim != 3) || mesh->elem < 0 || mesh->elem > 3 || mesh->n_nodes <= 0 ||
+        mesh->n_elem <= 0 || mesh->n_nodes > INT32_MAX)
+        return EP_ERR_INVALID_ARG;
+    Ctx* c = new Ctx();
+    auto fail = [&](ep_status st) {
+        g_create_err = c->err;
+        ep_destroy(c);
+        return st;
+    };
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        c->err = "cudaSetDevice failed";
+        return fail(EP_ERR_CUDA);
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->dim = mesh->dim;
+    c->family = mesh->elem;
+    c->eid = elem_id(c->family, c->dim);
+    c->n_p = elem_np(c->eid);
+    c->n_q = elem_nq(c->eid);
+    c->n_comp = c->dim == 2 ? 4 : 6;
+    c->n_nodes = mesh->n_nodes;
+    c->n_elem = mesh->n_elem;
+    c->n_int = c->n_elem * c->n_q;
+    c->n_dof = c->n_nodes * c->dim;
+    if (!make_matconst(*mat, c->dim, c->mat, c->err)) return fail(EP_ERR_INVALID_ARG);
+    c->hard_len = (c->mat.model == 1) ? c->n_int * c->n_comp : c->n_int;
+
+    // pattern and slot map (host)
+    std::vector<int32_t> row_ptr, col_idx, slots;
+    if (!build_pattern(c->n_nodes, c->n_elem, c->n_p, mesh->elem_nodes, row_ptr, col_idx, slots, c->err))
+        return fail(EP_ERR_INVALID_ARG);
+    c->nnzb = (int64_t)col_idx.size();
+    std::vector<int32_t> diag(c->n_nodes);
+    for (int64_t n = 0; n < c->n_nodes; ++n) {
+        const int32_t* b = col_idx.data() + row_ptr[n];
+        const int32_t* e = col_idx.data() + row_ptr[n + 1];
+        const int32_t* it = std::lower_bound(b, e, (int32_t)n);
+        if (it == e || *it != n) {
+            c->err = "node " + std::to_string(n) + " belongs to no element";
+            return fail(EP_ERR_INVALID_ARG);
+        }
+        diag[n] = (int32_t)(it - col_idx.data());
+    }
+    std::vector<double> dhat, wq;
+    reference_tables(c->family, c->dim, dhat, wq);
+
+    const int d = c->dim;
+    cudaStream_t s = c->stream;
+#define CKF(call)                                                   \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return fail(cuda_fail(c, _e, #call)); \
+    } while (0)
+    double *d_dhat = nullptr, *d_wq = nullptr;
+    int* bad = nullptr;
+    CKF(dalloc(c, &c->coords, c->n_nodes * d));
+    CKF(dalloc(c, &c->elem, c->n_elem * c->n_p));
+    CKF(dalloc(c, &c->slots, c->n_elem * c->n_p * c->n_p));
+    CKF(dalloc(c, &c->row_ptr, c->n_nodes + 1));
+    CKF(dalloc(c, &c->col_idx, c->nnzb));
+    CKF(dalloc(c, &c->diag_slot, c->n_nodes));
+    CKF(dalloc(c, &c->dphi, c->n_int * c->n_p * d));
+    CKF(dalloc(c, &c->wgt, c->n_int));
+    CKF(dalloc(c, &c->Kel, c->nnzb * d * d));
+    CKF(dalloc(c, &c->Kt, c->nnzb * d * d));
+    CKF(dalloc(c, &c->ep, c->n_int * c->n_comp));
+    CKF(dalloc(c, &c->hard, c->hard_len));
+    CKF(dalloc(c, &c->sig, c->n_int * c->n_comp));
+    CKF(dalloc(c, &c->flag, c->n_int));
+    CKF(dalloc(c, &c->u, c->n_dof));
+    CKF(dalloc(c, &c->u_prev, c->n_dof));
+    CKF(dalloc(c, &c->u_it, c->n_dof));
+    CKF(dalloc(c, &c->F, c->n_dof));
+    CKF(dalloc(c, &c->r, c->n_dof));
+    CKF(dalloc(c, &c->f_unit, c->n_dof));
+    CKF(dalloc(c, &c->uD_unit, c->n_dof));
+    CKF(dalloc(c, &c->free_dof, c->n_dof));
+    CKF(dalloc(c, &c->counter, 1));
+    CKF(dalloc(c, &c->err_flag, 1));
+    CKF(dalloc(c, &c->norms, 3));
+    CKF(dalloc(c, &d_dhat, dhat.size()));
+    CKF(dalloc(c, &d_wq, wq.size()));
+    CKF(dalloc(c, &bad, 1));
+    CKF(cudaMallocHost(&c->norms_host, 3 * sizeof(double)));
+    CKF(cudaMallocHost(&c->counter_host, sizeof(unsigned long long)));
+    CKF(cudaMallocHost(&c->err_host, sizeof(int)));
+    for (auto& e : c->ev) CKF(cudaEventCreate(&e));
+    CKF(krylov_alloc(c->kw, c->n_nodes, d, 20000, c->num_sms));
+
+    std::vector<uint8_t> freem(c->n_dof);
+    for (int64_t i = 0; i < c->n_dof; ++i) freem[i] = bc->dirichlet_mask[i] ? 0 : 1;
+    CKF(cudaMemcpyAsync(c->coords, mesh->coords, sizeof(double) * c->n_nodes * d, cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->elem, mesh->elem_nodes, sizeof(int32_t) * c->n_elem * c->n_p, cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->slots, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->row_ptr, row_ptr.data(), sizeof(int32_t) * row_ptr.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->col_idx, col_idx.data(), sizeof(int32_t) * col_idx.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->diag_slot, diag.data(), sizeof(int32_t) * diag.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(d_dhat, dhat.data(), sizeof(double) * dhat.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(d_wq, wq.data(), sizeof(double) * wq.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->free_dof, freem.data(), c->n_dof, cudaMemcpyHostToDevice, s));
+    if (bc->f_ext_unit)
+        CKF(cudaMemcpyAsync(c->f_unit, bc->f_ext_unit, sizeof(double) * c->n_dof, cudaMemcpyHostToDevice, s));
+    else
+        CKF(cudaMemsetAsync(c->f_unit, 0, sizeof(double) * c->n_dof, s));
+    if (bc->u_D_unit)
+        CKF(cudaMemcpyAsync(c->uD_unit, bc->u_D_unit, sizeof(double) * c->n_dof, cudaMemcpyHostToDevice, s));
+    else
+        CKF(cudaMemsetAsync(c->uD_unit, 0, sizeof(double) * c->n_dof, s));
+    CKF(cudaMemsetAsync(c->ep, 0, sizeof(double) * c->n_int * c->n_comp, s));
+    CKF(cudaMemsetAsync(c->hard, 0, sizeof(double) * c->hard_len, s));
+    CKF(cudaMemsetAsync(c->sig, 0, sizeof(double) * c->n_int * c->n_comp, s));
+    CKF(cudaMemsetAsync(c->flag, 0, c->n_int, s));
+    CKF(cudaMemsetAsync(c->u, 0, sizeof(double) * c->n_dof, s));
+    CKF(cudaMemsetAsync(c->u_prev, 0, sizeof(double) * c->n_dof, s));
+    CKF(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+    CKF(cudaMemsetAsync(bad, 0, sizeof(int), s));
+
+    // geometry (Section 6.1) -- cached per point
+    GeomArgs g{};
+    g.n_elem = c->n_elem;
+    g.n_int = c->n_int;
+    g.coords = c->coords;
+    g.elem_nodes = c->elem;
+    g.dhat = d_dhat;
+    g.wq = d_wq;
+    g.dphi = c->dphi;
+    g.wgt = c->wgt;
+    g.bad_count = bad;
+    CKF(launch_geometry(c->eid, g, s));
+    int bad_host = 0;
+    CKF(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKF(cudaStreamSynchronize(s));
+    if (bad_host) {
+        c->err = std::to_string(bad_host) + " integration points with det J <= 0";
+        return fail(EP_ERR_BAD_ELEMENT);
+    }
+    // K_elast (Section 6.3)
+    CKF(cudaMemsetAsync(c->Kel, 0, sizeof(double) * c->nnzb * d * d, s));
+    AsmArgs a{};
+    a.mesh = mesh_dev(c);
+    a.mat = c->mat;
+    a.state = state_dev(c);
+    a.u = c->u;
+    a.F = c->F;
+    a.Kvals = c->Kel;
+    a.mode = ASM_FULL;
+    a.want_K = 1;
+    a.elastic_only = 1;
+    CKF(launch_assemble(c->eid, a, s));
+    CKF(cudaStreamSynchronize(s));
+#undef CKF
+    *out = c;
+    return EP_OK;
+}
+
+ep_status ep_get_info(const void* ctx, ep_info* info) {
+    if (!ctx || !info) return EP_ERR_INVALID_ARG;
+    const Ctx* c = static_cast<const Ctx*>(ctx);
+    info->n_nodes = c->n_nodes;
+    info->n_elem = c->n_elem;
+    info->n_int = c->n_int;
+    info->nnz_blocks = c->nnzb;
+    info->dim = c->dim;
+    info->n_p = c->n_p;
+    info->n_q = c->n_q;
+    info->n_comp = c->n_comp;
+    return EP_OK;
+}
+
+static ep_status field_ptr(Ctx* c, int32_t field, void** p, size_t* bytes, bool writing) {
+    const size_t d2 = (size_t)c->dim * c->dim;
+    switch (field) {
+        case EP_U: *p = c->u; *bytes = sizeof(double) * c->n_dof; return EP_OK;
+        case EP_STRESS: *p = c->sig; *bytes = sizeof(double) * c->n_int * c->n_comp; return EP_OK;
+        case EP_PLASTIC_STRAIN: *p = c->ep; *bytes = sizeof(double) * c->n_int * c->n_comp; return EP_OK;
+        case EP_HARDENING: *p = c->hard; *bytes = sizeof(double) * c->hard_len; return EP_OK;
+        case EP_PLASTIC_FLAG: *p = c->flag; *bytes = c->n_int; return EP_OK;
+    }
+    if (writing) return EP_ERR_INVALID_ARG;
+    switch (field) {
+        case EP_F_INT: *p = c->F; *bytes = sizeof(double) * c->n_dof; return EP_OK;
+        case EP_K_ROW_PTR: *p = c->row_ptr; *bytes = sizeof(int32_t) * (c->n_nodes + 1); return EP_OK;
+        case EP_K_COL_IDX: *p = c->col_idx; *bytes = sizeof(int32_t) * c->nnzb; return EP_OK;
+        case EP_K_VALUES: *p = c->Kt; *bytes = sizeof(double) * c->nnzb * d2; return EP_OK;
+        case EP_K_ELASTIC: *p = c->Kel; *bytes = sizeof(double) * c->nnzb * d2; return EP_OK;
+        case EP_WEIGHT: *p = c->wgt; *bytes = sizeof(double) * c->n_int; return EP_OK;
+        case EP_DPHI: *p = c->dphi; *bytes = sizeof(double) * c->n_int * c->n_p * c->dim; return EP_OK;
+        case EP_SOLUTION: *p = c->kw.x; *bytes = sizeof(double) * c->n_dof; return EP_OK;
+    }
+    return EP_ERR_INVALID_ARG;
+}
+
+ep_status ep_get(void* ctx, int32_t field, void* dst, size_t bytes, int32_t dst_is_device) {
+    if (!ctx || !dst) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    void* src = nullptr;
+    size_t want = 0;
+    if (field_ptr(c, field, &src, &want, false) != EP_OK) {
+        c->err = "ep_get: unknown field";
+        return EP_ERR_INVALID_ARG;
+    }
+    if (bytes != want) {
+        c->err = "ep_get: size mismatch (expected " + std::to_string(want) + " bytes)";
+        return EP_ERR_INVALID_ARG;
+    }
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(dst, src, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return EP_OK;
+}
+
+ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_t src_is_device) {
+    if (!ctx || !src) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    void* dst = nullptr;
+    size_t want = 0;
+    if (field_ptr(c, field, &dst, &want, true) != EP_OK) {
+        c->err = "ep_set: field is not writable";
+        return EP_ERR_INVALID_ARG;
+    }
+    if (bytes != want) {
+        c->err = "ep_set: size mismatch (expected " + std::to_string(want) + " bytes)";
+        return EP_ERR_INVALID_ARG;
+    }
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(dst, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (field == EP_U) c->n_committed = 0;   // no extrapolation history across a reset
+    return EP_OK;
+}
+
+static ep_status load_u(Ctx* c, const double* u, int32_t u_is_device) {
+    CK(cudaMemcpyAsync(c->u_it, u, sizeof(double) * c->n_dof,
+                       u_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    return EP_OK;
+}
+
+ep_status ep_assemble(void* ctx, const double* u, int32_t u_is_device, int32_t split, int64_t* n_plastic) {
+    if (!ctx || !u) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    cudaSetDevice(c->device);
+    ep_status st = load_u(c, u, u_is_device);
+    if (st != EP_OK) return st;
+    CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    st = assemble(c, c->u_it, split != 0, true);
+    if (st != EP_OK) return st;
+    unsigned long long np = 0;
+    bool rm_err = false;
+    st = read_flags(c, &np, &rm_err);
+    if (st != EP_OK) return st;
+    if (n_plastic) *n_plastic = (int64_t)np;
+    if (rm_err) {
+        c->err = "return mapping: apex reached with K*eta*eta_bar + Hc = 0";
+        return EP_ERR_RETURN_MAP;
+    }
+    return EP_OK;
+}
+
+ep_status ep_commit(void* ctx, const double* u, int32_t u_is_device) {
+    if (!ctx || !u) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    cudaSetDevice(c->device);
+    ep_status st = load_u(c, u, u_is_device);
+    if (st != EP_OK) return st;
+    CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+    st = commit(c, c->u_it, nullptr);
+    if (st != EP_OK) return st;
+    CK(cudaMemcpyAsync(c->u, c->u_it, sizeof(double) * c->n_dof, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->n_committed = 0;
+    return EP_OK;
+}
+
+ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const ep_opts* opts, int32_t* iterations,
+                          double* rel_resid) {
+    if (!ctx || !b || !opts) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    if (!c->K_valid) {
+        c->err = "ep_linear_solve: no assembled matrix (call ep_assemble first)";
+        return EP_ERR_STATE;
+    }
+    if (!(opts->krylov_rtol > 0.0) || opts->krylov_maxit <= 0) {
+        c->err = "ep_linear_solve: need krylov_rtol > 0 and krylov_maxit > 0";
+        return EP_ERR_INVALID_ARG;
+    }
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(c->r, b, sizeof(double) * c->n_dof, b_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+    const BsrDev A = bsr_dev(c, c->Kt);
+    CK(krylov_precond(A, c->kw, opts->precond, c->stream));
+    int its = 0, status = 0;
+    double rel = 0.0;
+    CK(krylov_solve(A, c->kw, c->r, krylov_method(c, *opts), opts->krylov_rtol, opts->krylov_maxit, c->stream, &its, &rel,
+                    &status));
+    if (iterations) *iterations = its;
+    if (rel_resid) *rel_resid = rel;
+    if (status != EP_OK) c->err = "Krylov: no convergence within the iteration cap, or breakdown";
+    return (ep_status)status;
+}
+
+ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, const ep_opts* opts,
+                             ep_step_report* reports) {
+    if (!ctx || n_steps < 0 || (n_steps > 0 && !zeta)) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    ep_opts o;
+    if (opts) o = *opts;
+    else ep_default_opts(&o);
+    if (o.precision != EP_FP64) {
+        c->err = "only EP_FP64 is available";
+        return EP_ERR_INVALID_ARG;
+    }
+    if (!(o.newton_rtol > 0.0) || o.newton_maxit < 1 || o.krylov_maxit < 1) return EP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int method = krylov_method(c, o);
+    const bool split = o.split_elastic_cache != 0;
+    const BsrDev A = bsr_dev(c, c->Kt);
+    c->profile = o.profile;
+    c->kw.profile = o.profile;
+    for (int k = 0; k < n_steps; ++k) {
+        const auto t_step0 = std::chrono::steady_clock::now();
+        ep_step_report rep{};
+        float t_asm = 0.f, t_sol = 0.f;
+        c->launches = 0;
+        c->kw.launches = 0;
+        c->kw.spmv_n = 0;
+        c->kw.spmv_ms = 0.0;
+        double t_asm_kernel = 0.0;
+        const double z = zeta[k];
+        // start iterate
+        CK(cudaMemcpyAsync(c->u_it, c->u, sizeof(double) * c->n_dof, cudaMemcpyDeviceToDevice, s));
+        if (o.warm_start == 1 && c->n_committed >= 2 && c->zeta_last != c->zeta_prev) {
+            const double ratio = (z - c->zeta_last) / (c->zeta_last - c->zeta_prev);
+            CK(vec_extrapolate(c->u_it, c->u_prev, ratio, c->n_dof, s));
+            c->launches += 1;
+        }
+        CK(vec_set_dirichlet(c->u_it, c->uD_unit, z, c->free_dof, c->n_dof, s));
+        c->launches += 1;
+        CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+        ep_status st = EP_OK;
+        double rel = 0.0, rnorm_prev = -1.0;
+        int it = 0;
+        bool converged = false;
+        for (;;) {
+            CK(cudaEventRecord(c->ev[0], s));
+            st = assemble(c, c->u_it, split, true);
+            if (st != EP_OK) break;
+            CK(cudaEventRecord(c->ev[1], s));
+            CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, c->n_dof, c->kw.part, c->kw.nparts, c->norms, s));
+            c->launches += 2;
+            rep.n_assemble += 1;
+            CK(cudaMemcpyAsync(c->norms_host, c->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            t_asm += ms;
+            if (c->profile) {
+                CK(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
+                t_asm_kernel += ms;
+            }
+            if (*c->err_host) {
+                c->err = "return mapping: apex reached with K*eta*eta_bar + Hc = 0 (no admissible stress)";
+                st = EP_ERR_RETURN_MAP;
+                break;
+            }
+            const double rnorm = std::sqrt(c->norms_host[0]);
+            const double scale = std::max(std::sqrt(c->norms_host[1]), std::sqrt(c->norms_host[2]));
+            if (!std::isfinite(rnorm) || !std::isfinite(scale)) {
+                c->err = "non-finite residual norm";
+                st = EP_ERR_NAN;
+                break;
+            }
+            rel = scale > 0.0 ? rnorm / scale : rnorm;
+            if (rel <= o.newton_rtol || rnorm == 0.0) {
+                converged = true;
+                break;
+            }
+            if (it >= o.newton_maxit) {
+                st = EP_ERR_NEWTON_NO_CONVERGENCE;
+                c->err = "Newton: no convergence in " + std::to_string(o.newton_maxit) + " iterations";
+                break;
+            }
+            // forcing term
+            double eta;
+            if (o.krylov_rtol > 0.0) eta = o.krylov_rtol;
+            else {
+                const double eta_min = 0.5 * o.newton_rtol * scale / rnorm;
+                const double eta_ew = (rnorm_prev < 0.0) ? 1e-3 : 0.9 * (rnorm / rnorm_prev) * (rnorm / rnorm_prev);
+                eta = std::min(1e-2, std::max(eta_ew, eta_min));
+                eta = std::max(eta, 1e-14);
+            }
+            rnorm_prev = rnorm;
+            CK(cudaEventRecord(c->ev[2], s));
+            CK(krylov_precond(A, c->kw, o.precond, s));
+            c->launches += 1;
+            int kits = 0, kst = 0;
+            double krel = 0.0;
+            CK(krylov_solve(A, c->kw, c->r, method, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+            CK(cudaEventRecord(c->ev[3], s));
+            rep.krylov_its += kits;
+            if (kst == EP_ERR_NAN) {
+                st = EP_ERR_NAN;
+                c->err = "Krylov: non-finite residual";
+                break;
+            }
+            if (kst != EP_OK && !(krel < 0.5)) {
+                // accept a partially converged solve as an inexact Newton step; fail only if it made no progress
+                st = EP_ERR_KRYLOV;
+                c->err = "Krylov: no progress (relative residual " + std::to_string(krel) + ")";
+                break;
+            }
+            CK(vec_axpy(c->u_it, 1.0, c->kw.x, c->n_dof, s));
+            c->launches += 1;
+            CK(cudaEventSynchronize(c->ev[3]));
+            CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+            t_sol += ms;
+            ++it;
+        }
+        rep.newton_its = it;
+        rep.rel_resid = rel;
+        rep.t_assemble_ms = t_asm;
+        rep.t_solve_ms = t_sol;
+        if (converged) {
+            unsigned long long np = 0;
+            st = commit(c, c->u_it, &np);
+            rep.n_plastic = (int64_t)np;
+            if (st == EP_OK) {
+                std::swap(c->u_prev, c->u);     // u_prev <- u_{k-1}
+                std::swap(c->u, c->u_it);       // u <- u_k
+                c->zeta_prev = c->zeta_last;
+                c->zeta_last = z;
+                c->n_committed++;
+            }
+        }
+        CK(cudaStreamSynchronize(s));
+        rep.t_step_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_step0).count();
+        rep.status = st;
+        rep.launches = c->launches + c->kw.launches;
+        rep.n_spmv = c->kw.spmv_n;
+        rep.t_spmv_kernel_ms = c->kw.spmv_ms;
+        rep.t_assemble_kernel_ms = t_asm_kernel;
+        if (reports) reports[k] = rep;
+        if (st != EP_OK) return st;
+    }
+    return EP_OK;
+}
+
+ep_status ep_constitutive(const ep_material* mat, int32_t dim, int64_t n, const double* E, const double* ep_prev,
+                          const double* hard_prev, double* S, double* DS, uint8_t* flag, double* ep_new,
+                          double* hard_new, void* cuda_stream) {
+    if (!mat || (dim != 2 && dim != 3) || n < 0) return EP_ERR_INVALID_ARG;
+    if (n == 0) return EP_OK;
+    if (!E || !ep_prev || !hard_prev || !S || !DS || !flag || !ep_new || !hard_new) return EP_ERR_INVALID_ARG;
+    MatConst m;
+    std::string err;
+    if (!make_matconst(*mat, dim, m, err)) return EP_ERR_INVALID_ARG;
+    cudaError_t e = launch_constitutive(dim, m, n, E, ep_prev, hard_prev, S, DS, flag, ep_new, hard_new,
+                                        static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? EP_OK : EP_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ep.h"
+
+namespace ep {
+
+// ---------------------------------------------------------------------------
+// Element types: (family, dim) -> compile-time sizes.
+// ---------------------------------------------------------------------------
+enum ElemId { P1_2D = 0, P2_2D, Q1_2D, Q2_2D, P1_3D, P2_3D, Q1_3D, Q2_3D, N_ELEM_IDS };
+
+inline int elem_id(int family, int dim) { return (dim == 2 ? 0 : 4) + family; }
+
+template <int ID> struct Elem;
+#define EP_ELEM(ID_, DIM_, NP_, NQ_, EPC_)                                   \
+    template <> struct Elem<ID_> {                                           \
+        static constexpr int ID = ID_, DIM = DIM_, NP = NP_, NQ = NQ_;       \
+        static constexpr int NS = (DIM_ == 2 ? 3 : 6);  /* strain rows */    \
+        static constexpr int NA = (DIM_ == 2 ? 4 : 6);  /* active components */ \
+        static constexpr int EPC = EPC_;                /* elements per CTA */ \
+    };
+EP_ELEM(P1_2D, 2, 3, 1, 128)
+EP_ELEM(P2_2D, 2, 6, 7, 32)
+EP_ELEM(Q1_2D, 2, 4, 4, 64)
+EP_ELEM(Q2_2D, 2, 8, 9, 16)
+EP_ELEM(P1_3D, 3, 4, 1, 64)
+EP_ELEM(P2_3D, 3, 10, 11, 4)
+EP_ELEM(Q1_3D, 3, 8, 8, 8)
+EP_ELEM(Q2_3D, 3, 20, 27, 1)
+#undef EP_ELEM
+
+inline int elem_np(int id) { static const int v[] = {3, 6, 4, 8, 4, 10, 8, 20}; return v[id]; }
+inline int elem_nq(int id) { static const int v[] = {1, 7, 4, 9, 1, 11, 8, 27}; return v[id]; }
+
+// ---------------------------------------------------------------------------
+// Material constants as the kernels use them.
+// ---------------------------------------------------------------------------
+struct MatConst {
+    int model;
+    double K, G;        // bulk and shear moduli
+    double Y, H;        // von Mises yield value and hardening modulus
+    double eta, c, eta_bar, Hc;   // Drucker-Prager
+};
+
+// ---------------------------------------------------------------------------
+// Device-side views passed to kernels.
+// ---------------------------------------------------------------------------
+struct MeshDev {
+    int64_t n_nodes, n_elem, n_int;
+    const int32_t* elem_nodes;  // [n_elem][n_p]
+    const int32_t* slots;       // [n_elem][n_p*n_p], block index of node pair (p, q)
+    const double* dphi;         // [n_int][n_p][dim], physical basis gradients
+    const double* wgt;          // [n_int]
+};
+
+struct StateDev {
+    double* ep;       // [n_comp][n_int]
+    double* hard;     // [n_int] or [n_comp][n_int]
+    double* sig;      // [n_comp][n_int]
+    uint8_t* flag;    // [n_int]
+};
+
+enum AsmMode { ASM_FULL = 0, ASM_DELTA = 1 };
+
+// Launchers defined per element type (asm_<type>.cu).
+struct AsmArgs {
+    MeshDev mesh;
+    MatConst mat;
+    StateDev state;
+    const double* u;           // [n_dof]
+    double* F;                 // [n_dof], accumulated (caller zeroes)
+    double* Kvals;             // [nnzb][dim][dim], accumulated (caller initialises)
+    int mode;                  // AsmMode
+    int want_K;                // 0: F only
+    int elastic_only;          // 1: D = C everywhere (K_elast assembly), u/state ignored
+    unsigned long long* n_plastic;  // device counter (may be null)
+    int* err_flag;             // device error word (return-map failures)
+};
+cudaError_t launch_assemble(int elem_id, const AsmArgs& a, cudaStream_t s);
+
+struct CommitArgs {
+    MeshDev mesh;
+    MatConst mat;
+    StateDev state;            // updated in place
+    const double* u;
+    unsigned long long* n_plastic;
+    int* err_flag;
+};
+cudaError_t launch_commit(int elem_id, const CommitArgs& a, cudaStream_t s);
+
+struct GeomArgs {
+    int64_t n_elem, n_int;
+    const double* coords;      // [n_nodes][dim]
+    const int32_t* elem_nodes;
+    const double* dhat;        // [n_q][n_p][dim] reference gradients
+    const double* wq;          // [n_q]
+    double* dphi;
+    double* wgt;
+    int* bad_count;            // number of points with det J <= 0
+};
+cudaError_t launch_geometry(int elem_id, const GeomArgs& a, cudaStream_t s);
+
+cudaError_t launch_constitutive(int dim, const MatConst& m, int64_t n, const double* E, const double* ep_prev,
+                                const double* hard_prev, double* S, double* DS, uint8_t* flag, double* ep_new,
+                                double* hard_new, cudaStream_t s);
+
+// Host-side reference tables (elements_host.cpp): gradients [n_q][n_p][dim], weights [n_q].
+void reference_tables(int family, int dim, std::vector<double>& dhat, std::vector<double>& wq);
+
+// Host-side pattern construction (pattern_host.cpp).
+// Builds the node-pair pattern (row_ptr [n_nodes+1], col_idx) and the slot map
+// slots [n_elem][n_p*n_p] (block index of each node pair).  Returns false on
+// invalid node indices.
+bool build_pattern(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem, std::vector<int32_t>& row_ptr,
+                   std::vector<int32_t>& col_idx, std::vector<int32_t>& slots, std::string& err);
+
+// ---------------------------------------------------------------------------
+// Krylov solver on the block-CSR matrix (krylov.cu).
+// ---------------------------------------------------------------------------
+struct BsrDev {
+    int64_t n_rows;            // node rows
+    int dim;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const int32_t* diag_slot;  // [n_rows] block index of the diagonal block
+    const double* vals;        // [nnzb][dim][dim]
+    const uint8_t* free_dof;   // [n_rows*dim], 1 = free
+};
+
+// Per-solve scalar record, written by the device, read by the host.
+struct KrylovRec {
+    int its;          // iterations done
+    int done;         // 1 converged, 2 breakdown, 3 iteration cap
+    double rr0;       // ||r_0||^2
+    double rr;        // ||r||^2 of the last iterate
+};
+
+struct KrylovWork {
+    int64_t n;               // vector length (n_rows*dim)
+    int nparts;              // partial-sum slots per reduction
+    int grid, block;         // launch shape of the vector/SpMV kernels
+    double *x, *r, *z, *p, *q, *rhat, *v, *s, *t, *phat, *shat;
+    double* minv;            // preconditioner: [n_rows][dim][dim]
+    double* part;            // [8][nparts] partial sums
+    double* hist;            // [3][maxit+2] rho, alpha, omega per iteration
+    int hist_len;
+    KrylovRec* rec;          // device
+    KrylovRec* rec_host;     // pinned host mirror
+    // instrumentation
+    int profile;             // 1: CUDA events around every SpMV launch
+    int launches;            // kernels launched by the solver (accumulates)
+    int spmv_n;              // SpMV launches that did work (profile = 1)
+    double spmv_ms;          // their summed duration
+    cudaEvent_t ev[2 * 32];
+};
+
+cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms);
+void krylov_free(KrylovWork& w);
+cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s);
+// Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab.
+// Returns cudaSuccess; *status receives EP_OK / EP_ERR_KRYLOV / EP_ERR_NAN.
+cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
+                         cudaStream_t s, int* its, double* relres, int* status);
+
+// Small vector kernels (krylov.cu).
+cudaError_t vec_residual(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof, double* r,
+                         int64_t n, double* part, int nparts, double* out3, cudaStream_t s);
+cudaError_t vec_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);
+cudaError_t vec_set_dirichlet(double* u, const double* uD_unit, double zeta, const uint8_t* free_dof, int64_t n,
+                              cudaStream_t s);
+cudaError_t vec_extrapolate(double* u, const double* u_prev, double ratio, int64_t n, cudaStream_t s);
+cudaError_t vec_mask_copy(double* dst, const double* src, const uint8_t* free_dof, int64_t n, cudaStream_t s);
+
+}  // namespace ep

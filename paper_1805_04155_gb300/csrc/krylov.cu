@@ -1,0 +1,628 @@
+// Preconditioned Krylov solve of eq. (lin_syst) (Section 4) on the block-CSR
+// tangent, restricted to the free DOFs (the K(Q,Q) of Section 5), plus the
+// small vector kernels of the Newton loop.
+//
+// The paper solves this system with MATLAB's sparse direct solver; here it is
+// a hand-written PCG (symmetric tangents: elastic, von Mises, associated
+// Drucker-Prager) or BiCGStab (nonassociated Drucker-Prager), preconditioned
+// by point Jacobi or by the inverse dim x dim diagonal node blocks.
+//
+// Every reduction is deterministic: each CTA writes one partial sum, and
+// every consumer CTA re-reduces all partials in the same fixed order, so all
+// CTAs (and all runs) agree bit for bit and no extra finalising launch is
+// needed.  Iteration scalars (rho, alpha, omega) are kept per iteration in a
+// device array so that no kernel reads a value another CTA of the same launch
+// may be writing.  Kernels exit at once when the device record says the solve
+// has finished, so the host may enqueue iterations in chunks and poll rarely.
+#include <algorithm>
+#include <cmath>
+
+#include "ep_internal.h"
+
+namespace ep {
+
+constexpr int VB = 512;   // threads per CTA of vector and SpMV kernels
+enum { P_RZ = 0, P_RR = 1, P_PQ = 2, P_TS = 3, P_TT = 4, P_N = 8 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Sum over the CTA; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// Sum of n partials in a fixed order; identical in every thread of every CTA.
+__device__ __forceinline__ double sum_partials(const double* part, int n, double* sh) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) sh[0] = v;
+    }
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// y = P A x (P = free-DOF mask), optional partial of dot(dv, y).
+// G lanes share one block row; lanes read consecutive blocks (coalesced).
+// ---------------------------------------------------------------------------
+template <int D, int G>
+__global__ void __launch_bounds__(VB) k_spmv(BsrDev A, const double* __restrict__ x, double* __restrict__ y,
+                                              const double* __restrict__ dv, double* part, const KrylovRec* rec) {
+    __shared__ double sh[32];
+    if (rec && rec->done) return;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = gtid >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int GPW = 32 / G;
+    const int lg = lane % G;
+    double dot = 0.0;
+    for (int64_t rbase = warp * GPW; rbase < A.n_rows; rbase += nwarps * GPW) {
+        const int64_t row = rbase + lane / G;
+        double acc[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) acc[r] = 0.0;
+        if (row < A.n_rows) {
+            const int beg = A.row_ptr[row], end = A.row_ptr[row + 1];
+            for (int k = beg + lg; k < end; k += G) {
+                const int64_t col = A.col_idx[k];
+                const double* blk = A.vals + (int64_t)k * (D * D);
+                double xc[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) xc[c] = x[col * D + c];
+#pragma unroll
+                for (int r = 0; r < D; ++r)
+#pragma unroll
+                    for (int c = 0; c < D; ++c) acc[r] += blk[r * D + c] * xc[c];
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int r = 0; r < D; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
+        if (row < A.n_rows && lg == 0) {
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                const int64_t dof = row * D + r;
+                const double val = A.free_dof[dof] ? acc[r] : 0.0;
+                y[dof] = val;
+                if (dv) dot += dv[dof] * val;
+            }
+        }
+    }
+    if (part) {
+        const double s = block_sum(dot, sh);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// z = M^-1 r for one node block (minv row-major [D][D])
+template <int D>
+__device__ __forceinline__ void apply_minv(const double* __restrict__ minv, const double* __restrict__ r,
+                                           double* __restrict__ z, int64_t node) {
+    const double* m = minv + node * (D * D);
+    double rv[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) rv[c] = r[node * D + c];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += m[i * D + c] * rv[c];
+        z[node * D + i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner: kind 0 point Jacobi, 1 block Jacobi.  Prescribed DOFs get
+// identity rows/columns.  A zero or non-finite pivot also gets identity.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_precond(BsrDev A, double* minv, int kind) {
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= A.n_rows) return;
+    const double* blk = A.vals + (int64_t)A.diag_slot[node] * (D * D);
+    double m[D][D];
+    bool fr[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) fr[r] = A.free_dof[node * D + r] != 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double v = blk[r * D + c];
+            if (!fr[r] || !fr[c] || (kind == 0 && r != c)) v = (r == c) ? 1.0 : 0.0;
+            m[r][c] = v;
+        }
+    double inv[D][D];
+    double det;
+    if (D == 2) {
+        det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+        const double id = 1.0 / det;
+        inv[0][0] = m[1][1] * id;  inv[0][1] = -m[0][1] * id;
+        inv[1][0] = -m[1][0] * id; inv[1][1] = m[0][0] * id;
+    } else {
+        const double c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+        const double c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+        const double c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+        det = m[0][0] * c00 + m[0][1] * c01 + m[0][2] * c02;
+        const double id = 1.0 / det;
+        inv[0][0] = c00 * id;
+        inv[0][1] = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) * id;
+        inv[0][2] = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) * id;
+        inv[1][0] = c01 * id;
+        inv[1][1] = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) * id;
+        inv[1][2] = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) * id;
+        inv[2][0] = c02 * id;
+        inv[2][1] = (m[0][1] * m[2][0] - m[0][0] * m[2][1]) * id;
+        inv[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) * id;
+    }
+    const bool ok = isfinite(det) && det != 0.0;
+    double* out = minv + node * (D * D);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[r * D + c] = ok ? inv[r][c] : (r == c ? 1.0 : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Solver kernels.  `it` is the iteration index supplied by the host.
+// ---------------------------------------------------------------------------
+struct KArgs {
+    int64_t n_rows;
+    const uint8_t* free_dof;
+    const double* minv;
+    double *x, *r, *z, *p, *q, *rhat, *v, *s, *t, *phat, *shat;
+    double* part;       // [P_N][nparts]
+    int nparts;
+    double* h_rho;      // [hist_len]
+    double* h_alpha;
+    double* h_omega;
+    KrylovRec* rec;
+    double rtol2;
+    int maxit;
+};
+
+#define PART(k) (a.part + (int64_t)(k) * a.nparts)
+
+// init: x = 0, r = P b, z = M^-1 r, p = v = 0, rhat = r; partials (rhat or z).r and r.r
+template <int D>
+__global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__ b, int bicg) {
+    __shared__ double sh[32];
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
+         node += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t i = node * D + c;
+            const double ri = a.free_dof[i] ? b[i] : 0.0;
+            a.r[i] = ri;
+            a.x[i] = 0.0;
+            a.p[i] = 0.0;
+            if (bicg) { a.rhat[i] = ri; a.v[i] = 0.0; }
+        }
+        if (!bicg) apply_minv<D>(a.minv, a.r, a.z, node);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t i = node * D + c;
+            s1 += (bicg ? a.rhat[i] : a.z[i]) * a.r[i];
+            s2 += a.r[i] * a.r[i];
+        }
+    }
+    const double b1 = block_sum(s1, sh);
+    const double b2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        PART(P_RZ)[blockIdx.x] = b1;
+        PART(P_RR)[blockIdx.x] = b2;
+        if (blockIdx.x == 0) { a.rec->its = 0; a.rec->done = 0; a.rec->rr0 = 0.0; a.rec->rr = 0.0; }
+    }
+}
+
+// Convergence test at the start of iteration `it`; returns true if the CTA must stop.
+__device__ __forceinline__ bool check_done(const KArgs& a, int it, double rz, double rr, double* sh) {
+    const double rr0 = (it == 0) ? rr : a.rec->rr0;
+    int done = 0;
+    if (!isfinite(rr) || !isfinite(rz)) done = 2;
+    else if (rr <= a.rtol2 * rr0) done = 1;
+    else if (rz == 0.0) done = 2;
+    else if (it >= a.maxit) done = 3;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (it == 0) a.rec->rr0 = rr;
+        a.rec->rr = rr;
+        a.rec->its = it;
+        if (done) a.rec->done = done;
+    }
+    (void)sh;
+    return done != 0;
+}
+
+// CG: p = z + beta p
+template <int D>
+__global__ void __launch_bounds__(VB) k_cg_p(KArgs a, int it) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const double rz = sum_partials(PART(P_RZ), a.nparts, sh);
+    const double rr = sum_partials(PART(P_RR), a.nparts, sh);
+    if (check_done(a, it, rz, rr, sh)) return;
+    const double beta = (it == 0) ? 0.0 : rz / a.h_rho[it - 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.h_rho[it] = rz;
+    const int64_t n = a.n_rows * D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a.p[i] = a.z[i] + beta * a.p[i];
+}
+
+// CG: alpha = rho / (p.q); x += alpha p; r -= alpha q; z = M^-1 r; partials r.z, r.r
+template <int D>
+__global__ void __launch_bounds__(VB) k_cg_update(KArgs a, int it) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const double pq = sum_partials(PART(P_PQ), a.nparts, sh);
+    const double alpha = a.h_rho[it] / pq;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
+         node += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t i = node * D + c;
+            a.x[i] += alpha * a.p[i];
+            a.r[i] -= alpha * a.q[i];
+        }
+        apply_minv<D>(a.minv, a.r, a.z, node);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t i = node * D + c;
+            s1 += a.r[i] * a.z[i];
+            s2 += a.r[i] * a.r[i];
+        }
+    }
+    const double b1 = block_sum(s1, sh);
+    const double b2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        PART(P_RZ)[blockIdx.x] = b1;
+        PART(P_RR)[blockIdx.x] = b2;
+    }
+}
+
+// BiCGStab: p = r + beta (p - omega v); phat = M^-1 p
+template <int D>
+__global__ void __launch_bounds__(VB) k_bicg_p(KArgs a, int it) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const double rho = sum_partials(PART(P_RZ), a.nparts, sh);
+    const double rr = sum_partials(PART(P_RR), a.nparts, sh);
+    if (check_done(a, it, rho, rr, sh)) return;
+    double beta = 0.0, om = 0.0;
+    if (it > 0) {
+        om = a.h_omega[it - 1];
+        if (om == 0.0) {   // t = 0 in the last step: breakdown (convergence was tested above)
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.rec->done = 2;
+            return;
+        }
+        beta = (rho / a.h_rho[it - 1]) * (a.h_alpha[it - 1] / om);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.h_rho[it] = rho;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
+         node += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t i = node * D + c;
+            a.p[i] = a.r[i] + beta * (a.p[i] - om * a.v[i]);
+        }
+        apply_minv<D>(a.minv, a.p, a.phat, node);
+    }
+}
+
+// BiCGStab: alpha = rho / (rhat.v); s = r - alpha v; shat = M^-1 s
+template <int D>
+__global__ void __launch_bounds__(VB) k_bicg_s(KArgs a, int it) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const double rv = sum_partials(PART(P_PQ), a.nparts, sh);
+    if (rv == 0.0 || !isfinite(rv)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.rec->done = 2;
+        return;
+    }
+    const double alpha = a.h_rho[it] / rv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.h_alpha[it] = alpha;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
+         node += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t i = node * D + c;
+            a.s[i] = a.r[i] - alpha * a.v[i];
+        }
+        apply_minv<D>(a.minv, a.s, a.shat, node);
+    }
+}
+
+// BiCGStab: omega = (t.s)/(t.t); x += alpha phat + omega shat; r = s - omega t; partials rhat.r, r.r
+template <int D>
+__global__ void __launch_bounds__(VB) k_bicg_x(KArgs a, int it) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const double ts = sum_partials(PART(P_TS), a.nparts, sh);
+    const double tt = sum_partials(PART(P_TT), a.nparts, sh);
+    const double alpha = a.h_alpha[it];
+    const double om = (tt > 0.0) ? ts / tt : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.h_omega[it] = om;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_rows * D;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        a.x[i] += alpha * a.phat[i] + om * a.shat[i];
+        const double ri = a.s[i] - om * a.t[i];
+        a.r[i] = ri;
+        s1 += a.rhat[i] * ri;
+        s2 += ri * ri;
+    }
+    const double b1 = block_sum(s1, sh);
+    const double b2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        PART(P_RZ)[blockIdx.x] = b1;
+        PART(P_RR)[blockIdx.x] = b2;
+    }
+}
+
+// Two dot partials (t.s and t.t) after the second SpMV of BiCGStab.
+__global__ void __launch_bounds__(VB) k_dot2(KArgs a, int64_t n) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ti = a.t[i];
+        s1 += ti * a.s[i];
+        s2 += ti * ti;
+    }
+    const double b1 = block_sum(s1, sh);
+    const double b2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        PART(P_TS)[blockIdx.x] = b1;
+        PART(P_TT)[blockIdx.x] = b2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms) {
+    w = KrylovWork{};
+    w.n = n_rows * dim;
+    w.block = VB;
+    w.grid = 2 * (num_sms > 0 ? num_sms : 152);
+    w.nparts = w.grid;
+    w.hist_len = maxit_cap + 2;
+    const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(w.n, 1);
+    double** vecs[] = {&w.x, &w.r, &w.z, &w.p, &w.q, &w.rhat, &w.v, &w.s, &w.t, &w.phat, &w.shat};
+    for (double** v : vecs) {
+        cudaError_t e = cudaMalloc(v, vb);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMalloc(&w.minv, sizeof(double) * (size_t)std::max<int64_t>(n_rows, 1) * dim * dim);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.part, sizeof(double) * P_N * w.nparts)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.hist, sizeof(double) * 3 * w.hist_len)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.rec, sizeof(KrylovRec))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&w.rec_host, sizeof(KrylovRec))) != cudaSuccess) return e;
+    for (auto& ev : w.ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+void krylov_free(KrylovWork& w) {
+    double* vecs[] = {w.x, w.r, w.z, w.p, w.q, w.rhat, w.v, w.s, w.t, w.phat, w.shat, w.minv, w.part, w.hist};
+    for (double* v : vecs)
+        if (v) cudaFree(v);
+    if (w.rec) cudaFree(w.rec);
+    if (w.rec_host) cudaFreeHost(w.rec_host);
+    for (auto& ev : w.ev)
+        if (ev) cudaEventDestroy(ev);
+    w = KrylovWork{};
+}
+
+cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s) {
+    const unsigned g = (unsigned)((A.n_rows + 255) / 256);
+    if (g == 0) return cudaSuccess;
+    if (A.dim == 2) k_precond<2><<<g, 256, 0, s>>>(A, w.minv, kind);
+    else k_precond<3><<<g, 256, 0, s>>>(A, w.minv, kind);
+    return cudaGetLastError();
+}
+
+template <int D>
+static void launch_spmv(const BsrDev& A, const double* x, double* y, const double* dv, double* part,
+                        const KrylovRec* rec, int grid, cudaStream_t s) {
+    if (D == 2) k_spmv<2, 4><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
+    else k_spmv<3, 8><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
+}
+
+template <int D>
+static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
+                           cudaStream_t s, int* its, double* relres, int* status) {
+    KArgs a;
+    a.n_rows = A.n_rows;
+    a.free_dof = A.free_dof;
+    a.minv = w.minv;
+    a.x = w.x; a.r = w.r; a.z = w.z; a.p = w.p; a.q = w.q; a.rhat = w.rhat; a.v = w.v; a.s = w.s; a.t = w.t;
+    a.phat = w.phat; a.shat = w.shat;
+    a.part = w.part;
+    a.nparts = w.nparts;
+    if (maxit > w.hist_len - 2) maxit = w.hist_len - 2;
+    a.h_rho = w.hist;
+    a.h_alpha = w.hist + w.hist_len;
+    a.h_omega = w.hist + 2 * w.hist_len;
+    a.rec = w.rec;
+    a.rtol2 = rtol * rtol;
+    a.maxit = maxit;
+    const int grid = w.grid;
+    const bool bicg = (method == 2);
+    k_init<D><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0);
+    w.launches += 1;
+    const int chunk = 16;   // iterations enqueued between two polls of the device record
+    int it = 0;
+    for (;;) {
+        const int first = it;
+        const int stop = std::min(it + chunk, maxit + 1);
+        int nev = 0;
+        for (; it < stop; ++it) {
+            if (!bicg) {
+                k_cg_p<D><<<grid, VB, 0, s>>>(a, it);
+                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                launch_spmv<D>(A, w.p, w.q, w.p, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
+                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                k_cg_update<D><<<grid, VB, 0, s>>>(a, it);
+                w.launches += 3;
+            } else {
+                k_bicg_p<D><<<grid, VB, 0, s>>>(a, it);
+                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                launch_spmv<D>(A, w.phat, w.v, w.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
+                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                k_bicg_s<D><<<grid, VB, 0, s>>>(a, it);
+                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                launch_spmv<D>(A, w.shat, w.t, nullptr, nullptr, w.rec, grid, s);
+                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                k_dot2<<<grid, VB, 0, s>>>(a, w.n);
+                k_bicg_x<D><<<grid, VB, 0, s>>>(a, it);
+                w.launches += 6;
+            }
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(w.rec_host, w.rec, sizeof(KrylovRec), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (w.profile) {
+            // SpMVs of iterations before the converged one did work; later ones exited at once
+            const int done_at = w.rec_host->done ? w.rec_host->its : it;
+            const int per = bicg ? 2 : 1;
+            for (int j = 0; j < nev / 2; ++j) {
+                if (first + j / per >= done_at) break;
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, w.ev[2 * j], w.ev[2 * j + 1]) == cudaSuccess) {
+                    w.spmv_ms += ms;
+                    w.spmv_n += 1;
+                }
+            }
+        }
+        if (w.rec_host->done || it > maxit) break;
+    }
+    const KrylovRec& r = *w.rec_host;
+    *its = r.its;
+    *relres = (r.rr0 > 0.0) ? sqrt(r.rr / r.rr0) : 0.0;
+    if (r.done == 1) *status = EP_OK;
+    else if (!std::isfinite(r.rr)) *status = EP_ERR_NAN;
+    else if (r.done == 2 && r.rr <= rtol * rtol * r.rr0) *status = EP_OK;
+    else *status = EP_ERR_KRYLOV;
+    return cudaSuccess;
+}
+
+cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
+                         cudaStream_t s, int* its, double* relres, int* status) {
+    if (A.dim == 2) return solve_t<2>(A, w, b, method, rtol, maxit, s, its, relres, status);
+    return solve_t<3>(A, w, b, method, rtol, maxit, s, its, relres, status);
+}
+
+// ---------------------------------------------------------------------------
+// Newton-loop vector kernels
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(VB) k_residual(const double* __restrict__ f_unit, double zeta,
+                                                  const double* __restrict__ F, const uint8_t* __restrict__ free_dof,
+                                                  double* __restrict__ r, int64_t n, double* part, int nparts) {
+    __shared__ double sh[32];
+    double s_r = 0.0, s_f = 0.0, s_F = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double fi = f_unit ? zeta * f_unit[i] : 0.0;
+        const double Fi = F[i];
+        const bool fr = free_dof[i] != 0;
+        const double ri = fr ? fi - Fi : 0.0;
+        r[i] = ri;
+        s_r += ri * ri;
+        s_f += fr ? fi * fi : 0.0;
+        s_F += Fi * Fi;
+    }
+    const double a = block_sum(s_r, sh);
+    const double b = block_sum(s_f, sh);
+    const double c = block_sum(s_F, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a;
+        part[nparts + blockIdx.x] = b;
+        part[2 * nparts + blockIdx.x] = c;
+    }
+}
+
+__global__ void k_finalize3(const double* part, int nparts, double* out3) {
+    __shared__ double sh[32];
+    for (int k = 0; k < 3; ++k) {
+        const double v = sum_partials(part + (int64_t)k * nparts, nparts, sh);
+        if (threadIdx.x == 0) out3[k] = v;
+    }
+}
+
+cudaError_t vec_residual(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof, double* r,
+                         int64_t n, double* part, int nparts, double* out3, cudaStream_t s) {
+    k_residual<<<nparts, VB, 0, s>>>(f_unit, zeta, F, free_dof, r, n, part, nparts);
+    k_finalize3<<<1, 32, 0, s>>>(part, nparts, out3);
+    return cudaGetLastError();
+}
+
+__global__ void k_axpy(double* y, double a, const double* x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+__global__ void k_set_dirichlet(double* u, const double* uD, double zeta, const uint8_t* free_dof, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!free_dof[i]) u[i] = uD ? zeta * uD[i] : 0.0;
+}
+
+__global__ void k_extrapolate(double* u, const double* u_prev, double ratio, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += ratio * (u[i] - u_prev[i]);
+}
+
+__global__ void k_mask_copy(double* dst, const double* src, const uint8_t* free_dof, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = free_dof[i] ? src[i] : 0.0;
+}
+
+static unsigned vgrid(int64_t n) {
+    int64_t g = (n + VB - 1) / VB;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 4096));
+}
+
+cudaError_t vec_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s) {
+    k_axpy<<<vgrid(n), VB, 0, s>>>(y, a, x, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_set_dirichlet(double* u, const double* uD_unit, double zeta, const uint8_t* free_dof, int64_t n,
+                              cudaStream_t s) {
+    k_set_dirichlet<<<vgrid(n), VB, 0, s>>>(u, uD_unit, zeta, free_dof, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_extrapolate(double* u, const double* u_prev, double ratio, int64_t n, cudaStream_t s) {
+    k_extrapolate<<<vgrid(n), VB, 0, s>>>(u, u_prev, ratio, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_mask_copy(double* dst, const double* src, const uint8_t* free_dof, int64_t n, cudaStream_t s) {
+    k_mask_copy<<<vgrid(n), VB, 0, s>>>(dst, src, free_dof, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ep

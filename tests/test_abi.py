@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every function include/ep.h declares.
+
+No compute calls: these run on a machine without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "ep.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(ep_[a-z_]+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1805_04155_gb300 import build as b
+    return b.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("ep_create", "ep_destroy", "ep_solve_load_path", "ep_get", "ep_set", "ep_assemble",
+                 "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(libpath):
+    import paper_1805_04155_gb300.ep as ep
+    assert sorted(ep.EXPORTED) == _declared()
+    lib = ep.lib()
+    assert lib.ep_status_str(0) == b"ok"
+    assert lib.ep_status_str(4) == b"element with det J <= 0"
+
+
+def test_struct_layouts_match_header(libpath):
+    """ctypes structures have the C sizes implied by the header's field lists."""
+    import paper_1805_04155_gb300.ep as ep
+    assert ctypes.sizeof(ep.ep_mesh) == 4 + 4 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(ep.ep_material) == 8 + 8 * 8
+    assert ctypes.sizeof(ep.ep_opts) == 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4
+    assert ctypes.sizeof(ep.ep_step_report) == 4 + 4 + 8 + 8 * 4 + 4 * 4 + 8 * 2
+    o = ep.default_opts()   # calls into the library (host only)
+    assert o.newton_rtol == 1e-10 and o.precond == 1 and o.split_elastic_cache == 1
+
+
+def test_create_rejects_bad_input_without_gpu_work(libpath):
+    """Argument validation happens before any CUDA call."""
+    import numpy as np
+    import paper_1805_04155_gb300.ep as ep
+    lib = ep.lib()
+    h = ctypes.c_void_p()
+    coords = np.zeros((3, 2))
+    elem = np.array([[0, 1, 2]], dtype=np.int32)
+    mesh = ep.ep_mesh(4, 0, 3, 1, coords.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      elem.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    mat = ep.ep_material(0, 1.0, 0.3, 0, 0, 0, 0, 0, 0)
+    mask = np.zeros(6, dtype=np.uint8)
+    bc = ep.ep_bc(mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), None, None)
+    st = lib.ep_create(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(mat), ctypes.byref(bc), 0, None)
+    assert st == ep.EP_ERR_INVALID_ARG      # dim = 4
+    assert lib.ep_create(None, None, None, None, 0, None) == ep.EP_ERR_INVALID_ARG
