@@ -95,7 +95,7 @@ typedef struct {
     int32_t precision;           /* ep_precision (EP_FP64 only in this version) */
     double newton_rtol;          /* ||(f - F)_free|| <= rtol * max(||f_free||, ||F||) */
     int32_t newton_maxit;
-    int32_t krylov;              /* 0 auto (CG if the tangent is symmetric, else BiCGStab), 1 CG, 2 BiCGStab */
+    int32_t krylov;              /* 0 auto (CG if the tangent is symmetric, else GMRES), 1 CG, 2 BiCGStab, 3 GMRES(30) */
     double krylov_rtol;          /* > 0: fixed relative tolerance; 0: adaptive forcing term */
     int32_t krylov_maxit;
     int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks) */

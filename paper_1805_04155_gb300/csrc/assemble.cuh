@@ -414,7 +414,7 @@ template <int ID>
 cudaError_t launch_assemble_elem(const AsmArgs& a, cudaStream_t s) {
     if (a.elastic_only) return launch_asm_t<ID, 0, false, false>(a, s);
     switch (a.mat.model) {
-        case 0: return launch_asm_t<ID, 0, false, true>(a, s);
+        case 0: return a.mode == ASM_DELTA ? launch_asm_t<ID, 0, true, true>(a, s) : launch_asm_t<ID, 0, false, true>(a, s);
         case 1: return a.mode == ASM_DELTA ? launch_asm_t<ID, 1, true, true>(a, s) : launch_asm_t<ID, 1, false, true>(a, s);
         case 2: return a.mode == ASM_DELTA ? launch_asm_t<ID, 2, true, true>(a, s) : launch_asm_t<ID, 2, false, true>(a, s);
         case 3: return a.mode == ASM_DELTA ? launch_asm_t<ID, 3, true, true>(a, s) : launch_asm_t<ID, 3, false, true>(a, s);

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -162,6 +163,7 @@ struct Ctx {
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int launches = 0;          // kernels launched (instrumentation)
     int profile = 0;
+    int verbose = 0;           // EP_VERBOSE=1: one line per Newton iteration on stderr
     std::vector<void*> allocs;
 };
 
@@ -272,9 +274,9 @@ static ep_status commit(Ctx* c, const double* u_dev, unsigned long long* n_plast
 }
 
 static int krylov_method(const Ctx* c, const ep_opts& o) {
-    if (o.krylov == 1 || o.krylov == 2) return o.krylov;
+    if (o.krylov >= 1 && o.krylov <= 3) return o.krylov;
     const bool sym = c->mat.model != 3 || (c->mat.eta == c->mat.eta_bar && c->mat.Hc == 0.0);
-    return sym ? 1 : 2;
+    return sym ? 1 : 3;
 }
 
 }  // namespace ep
@@ -356,6 +358,7 @@ ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, con
     };
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (const char* v = std::getenv("EP_VERBOSE")) c->verbose = std::atoi(v);
     if (cudaSetDevice(device) != cudaSuccess) {
         c->err = "cudaSetDevice failed";
         return fail(EP_ERR_CUDA);
@@ -700,6 +703,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             rep.n_assemble += 1;
             CK(cudaMemcpyAsync(c->norms_host, c->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->counter_host, c->counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
@@ -745,9 +749,24 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             c->launches += 1;
             int kits = 0, kst = 0;
             double krel = 0.0;
-            CK(krylov_solve(A, c->kw, c->r, method, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+            // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
+            // nonassociated model
+            const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
+            CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
             CK(cudaEventRecord(c->ev[3], s));
             rep.krylov_its += kits;
+            if (c->verbose)
+                std::fprintf(stderr, "[ep] step %d zeta %.6g newton %d rel %.3e eta %.2e krylov(%s) its %d rel %.3e done %d why %d\n",
+                             k, z, it, rel, eta, m_it == 1 ? "cg" : (m_it == 2 ? "bicgstab" : "gmres"), kits, krel, c->kw.rec_host->done,
+                             c->kw.rec_host->why);
+            if (c->verbose > 1 && kst != EP_OK) {
+                std::vector<double> h(3 * c->kw.hist_len);
+                cudaMemcpy(h.data(), c->kw.hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost);
+                const int n = std::min(kits + 1, c->kw.hist_len);
+                for (int j = std::max(0, n - 6); j < n; ++j)
+                    std::fprintf(stderr, "[ep]   it %d rho %.6e alpha %.6e omega %.6e\n", j, h[j], h[c->kw.hist_len + j],
+                                 h[2 * c->kw.hist_len + j]);
+            }
             if (kst == EP_ERR_NAN) {
                 st = EP_ERR_NAN;
                 c->err = "Krylov: non-finite residual";

@@ -140,6 +140,9 @@ struct KrylovRec {
     int done;         // 1 converged, 2 breakdown, 3 iteration cap
     double rr0;       // ||r_0||^2
     double rr;        // ||r||^2 of the last iterate
+    int why;          // which test ended the solve (diagnostics): 1 converged, 2 non-finite, 3 rho = 0,
+                      // 4 (rhat, v) = 0, 5 omega = 0, 6 iteration cap
+    int pad;
 };
 
 struct KrylovWork {
@@ -148,7 +151,9 @@ struct KrylovWork {
     int grid, block;         // launch shape of the vector/SpMV kernels
     double *x, *r, *z, *p, *q, *rhat, *v, *s, *t, *phat, *shat;
     double* minv;            // preconditioner: [n_rows][dim][dim]
-    double* part;            // [8][nparts] partial sums
+    double* part;            // [max(8, GM_M + 2)][nparts] partial sums
+    double* V;               // GMRES basis [GM_M + 1][n]
+    double* gm;              // GMRES small arrays: H [(GM_M+1) x GM_M], cs, sn, g [GM_M+1]
     double* hist;            // [3][maxit+2] rho, alpha, omega per iteration
     int hist_len;
     KrylovRec* rec;          // device
@@ -161,10 +166,11 @@ struct KrylovWork {
     cudaEvent_t ev[2 * 32];
 };
 
+constexpr int GM_M = 30;     // GMRES restart length
 cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms);
 void krylov_free(KrylovWork& w);
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s);
-// Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab.
+// Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab, 3 GMRES(GM_M).
 // Returns cudaSuccess; *status receives EP_OK / EP_ERR_KRYLOV / EP_ERR_NAN.
 cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
                          cudaStream_t s, int* its, double* relres, int* status);

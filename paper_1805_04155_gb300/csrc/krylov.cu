@@ -200,13 +200,28 @@ struct KArgs {
     KrylovRec* rec;
     double rtol2;
     int maxit;
+    int cold;           // 1 on the first start of a solve (fixes rr0), 0 on restarts
 };
 
 #define PART(k) (a.part + (int64_t)(k) * a.nparts)
 
-// init: x = 0, r = P b, z = M^-1 r, p = v = 0, rhat = r; partials (rhat or z).r and r.r
+// Shadow residual of BiCGStab: a fixed pseudo-random vector on the free DOFs
+// (splitmix64 of the DOF index and a restart counter, mapped to [-1, 1]).
+// r0 itself is a poor choice here: for a traction load it lives on a few
+// boundary DOFs, and (rhat, r) then cancels to zero long before convergence.
+__device__ __forceinline__ double shadow_value(int64_t i, int seed) {
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull * (unsigned long long)(seed + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// init: r = P (b - A x) (warm) or x = 0, r = P b (cold); z = M^-1 r (CG) or
+// rhat = shadow, p = v = 0 (BiCGStab); partials (rhat or z).r and r.r.
+// For the warm start q must hold A x.
 template <int D>
-__global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__ b, int bicg) {
+__global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__ b, int bicg, int warm, int seed) {
     __shared__ double sh[32];
     double s1 = 0.0, s2 = 0.0;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
@@ -214,11 +229,12 @@ __global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
-            const double ri = a.free_dof[i] ? b[i] : 0.0;
+            const bool fr = a.free_dof[i] != 0;
+            const double ri = fr ? (warm ? b[i] - a.q[i] : b[i]) : 0.0;
             a.r[i] = ri;
-            a.x[i] = 0.0;
+            if (!warm) a.x[i] = 0.0;
             a.p[i] = 0.0;
-            if (bicg) { a.rhat[i] = ri; a.v[i] = 0.0; }
+            if (bicg) { a.rhat[i] = fr ? shadow_value(i, seed) : 0.0; a.v[i] = 0.0; }
         }
         if (!bicg) apply_minv<D>(a.minv, a.r, a.z, node);
 #pragma unroll
@@ -233,23 +249,24 @@ __global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__
     if (threadIdx.x == 0) {
         PART(P_RZ)[blockIdx.x] = b1;
         PART(P_RR)[blockIdx.x] = b2;
-        if (blockIdx.x == 0) { a.rec->its = 0; a.rec->done = 0; a.rec->rr0 = 0.0; a.rec->rr = 0.0; }
+        if (blockIdx.x == 0) { a.rec->its = 0; a.rec->done = 0; a.rec->rr = 0.0; a.rec->why = 0; }
     }
 }
 
 // Convergence test at the start of iteration `it`; returns true if the CTA must stop.
 __device__ __forceinline__ bool check_done(const KArgs& a, int it, double rz, double rr, double* sh) {
-    const double rr0 = (it == 0) ? rr : a.rec->rr0;
-    int done = 0;
-    if (!isfinite(rr) || !isfinite(rz)) done = 2;
-    else if (rr <= a.rtol2 * rr0) done = 1;
-    else if (rz == 0.0) done = 2;
-    else if (it >= a.maxit) done = 3;
+    const bool first = (it == 0 && a.cold);
+    const double rr0 = first ? rr : a.rec->rr0;
+    int done = 0, why = 0;
+    if (!isfinite(rr) || !isfinite(rz)) { done = 2; why = 2; }
+    else if (rr <= a.rtol2 * rr0) { done = 1; why = 1; }
+    else if (rz == 0.0) { done = 2; why = 3; }
+    else if (it >= a.maxit) { done = 3; why = 6; }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (it == 0) a.rec->rr0 = rr;
+        if (first) a.rec->rr0 = rr;
         a.rec->rr = rr;
         a.rec->its = it;
-        if (done) a.rec->done = done;
+        if (done) { a.rec->done = done; a.rec->why = why; }
     }
     (void)sh;
     return done != 0;
@@ -314,7 +331,7 @@ __global__ void __launch_bounds__(VB) k_bicg_p(KArgs a, int it) {
     if (it > 0) {
         om = a.h_omega[it - 1];
         if (om == 0.0) {   // t = 0 in the last step: breakdown (convergence was tested above)
-            if (blockIdx.x == 0 && threadIdx.x == 0) a.rec->done = 2;
+            if (blockIdx.x == 0 && threadIdx.x == 0) { a.rec->done = 2; a.rec->why = 5; }
             return;
         }
         beta = (rho / a.h_rho[it - 1]) * (a.h_alpha[it - 1] / om);
@@ -338,7 +355,7 @@ __global__ void __launch_bounds__(VB) k_bicg_s(KArgs a, int it) {
     if (a.rec->done) return;
     const double rv = sum_partials(PART(P_PQ), a.nparts, sh);
     if (rv == 0.0 || !isfinite(rv)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.rec->done = 2;
+        if (blockIdx.x == 0 && threadIdx.x == 0) { a.rec->done = 2; a.rec->why = 4; }
         return;
     }
     const double alpha = a.h_rho[it] / rv;
@@ -417,7 +434,9 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
     }
     cudaError_t e = cudaMalloc(&w.minv, sizeof(double) * (size_t)std::max<int64_t>(n_rows, 1) * dim * dim);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.part, sizeof(double) * P_N * w.nparts)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.part, sizeof(double) * std::max<int>((int)P_N, GM_M + 2) * w.nparts)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.V, vb * (GM_M + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.gm, sizeof(double) * ((GM_M + 1) * GM_M + 3 * (GM_M + 1)))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.hist, sizeof(double) * 3 * w.hist_len)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.rec, sizeof(KrylovRec))) != cudaSuccess) return e;
     if ((e = cudaMallocHost(&w.rec_host, sizeof(KrylovRec))) != cudaSuccess) return e;
@@ -427,7 +446,7 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
 }
 
 void krylov_free(KrylovWork& w) {
-    double* vecs[] = {w.x, w.r, w.z, w.p, w.q, w.rhat, w.v, w.s, w.t, w.phat, w.shat, w.minv, w.part, w.hist};
+    double* vecs[] = {w.x, w.r, w.z, w.p, w.q, w.rhat, w.v, w.s, w.t, w.phat, w.shat, w.minv, w.part, w.hist, w.V, w.gm};
     for (double* v : vecs)
         if (v) cudaFree(v);
     if (w.rec) cudaFree(w.rec);
@@ -472,13 +491,22 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
     a.maxit = maxit;
     const int grid = w.grid;
     const bool bicg = (method == 2);
-    k_init<D><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0);
-    w.launches += 1;
     const int chunk = 16;   // iterations enqueued between two polls of the device record
+    const int max_restarts = bicg ? 8 : 0;
+    int total_its = 0;
+    for (int restart = 0;; ++restart) {
+    a.cold = (restart == 0);
+    a.maxit = maxit - total_its;
+    if (restart > 0) {   // warm restart from the current x after a breakdown
+        launch_spmv<D>(A, w.x, w.q, nullptr, nullptr, nullptr, grid, s);
+        w.launches += 1;
+    }
+    k_init<D><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
+    w.launches += 1;
     int it = 0;
     for (;;) {
         const int first = it;
-        const int stop = std::min(it + chunk, maxit + 1);
+        const int stop = std::min(it + chunk, a.maxit + 1);
         int nev = 0;
         for (; it < stop; ++it) {
             if (!bicg) {
@@ -521,10 +549,14 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
                 }
             }
         }
-        if (w.rec_host->done || it > maxit) break;
+        if (w.rec_host->done || it > a.maxit) break;
+    }
+    total_its += w.rec_host->its;
+    if (w.rec_host->done == 2 && restart < max_restarts && std::isfinite(w.rec_host->rr) && total_its < maxit) continue;
+    break;
     }
     const KrylovRec& r = *w.rec_host;
-    *its = r.its;
+    *its = total_its;
     *relres = (r.rr0 > 0.0) ? sqrt(r.rr / r.rr0) : 0.0;
     if (r.done == 1) *status = EP_OK;
     else if (!std::isfinite(r.rr)) *status = EP_ERR_NAN;
@@ -533,8 +565,283 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
     return cudaSuccess;
 }
 
+
+// ---------------------------------------------------------------------------
+// GMRES(m), right preconditioned: x = x0 + M^-1 V y.  The Hessenberg matrix,
+// the Givens rotations and the residual estimate live in device memory and are
+// updated by thread 0 of CTA 0; every CTA recomputes the reductions it needs
+// from the partial sums, so no launch reads a value written in that launch.
+// ---------------------------------------------------------------------------
+struct GArgs {
+    int64_t n_rows;
+    const uint8_t* free_dof;
+    const double* minv;
+    double* x;
+    double* r;          // r0 of the cycle
+    double* q;          // A x for warm restarts
+    double* z;          // M^-1 v_j
+    double* V;          // [m+1][n]
+    double* H;          // [m+1][m], H[i*m + j]
+    double* cs;
+    double* sn;
+    double* g;          // [m+1]
+    double* part;       // [m+2][nparts]
+    int nparts;
+    KrylovRec* rec;
+    double rtol2;
+    int cold;
+};
+
+#define GPART(k) (a.part + (int64_t)(k) * a.nparts)
+
+// r = P(b - q) (warm) or P b with x = 0 (cold); partial ||r||^2 -> GPART(0)
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_init(GArgs a, const double* __restrict__ b, int warm) {
+    __shared__ double sh[32];
+    double s1 = 0.0;
+    const int64_t n = a.n_rows * D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = a.free_dof[i] ? (warm ? b[i] - a.q[i] : b[i]) : 0.0;
+        a.r[i] = ri;
+        if (!warm) a.x[i] = 0.0;
+        s1 += ri * ri;
+    }
+    const double b1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+        GPART(0)[blockIdx.x] = b1;
+        if (blockIdx.x == 0) { a.rec->done = 0; a.rec->why = 0; }
+    }
+}
+
+// beta = ||r||, v_0 = r / beta, g = (beta, 0, ...); convergence test of the cycle start
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_start(GArgs a) {
+    __shared__ double sh[32];
+    const double rr = sum_partials(GPART(0), a.nparts, sh);
+    const double rr0 = a.cold ? rr : a.rec->rr0;
+    const double beta = sqrt(rr);
+    const bool conv = !(rr > a.rtol2 * rr0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (a.cold) a.rec->rr0 = rr;
+        a.rec->rr = rr;
+        a.rec->its = 0;
+        a.g[0] = beta;
+        for (int i = 1; i <= GM_M; ++i) a.g[i] = 0.0;
+        if (!isfinite(rr)) { a.rec->done = 2; a.rec->why = 2; }
+        else if (conv) { a.rec->done = 1; a.rec->why = 1; }
+    }
+    if (conv || !isfinite(rr)) return;
+    const double ib = 1.0 / beta;
+    const int64_t n = a.n_rows * D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a.V[i] = a.r[i] * ib;
+}
+
+// z = M^-1 v_j
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_prec(GArgs a, int j) {
+    if (a.rec->done) return;
+    const double* v = a.V + (int64_t)j * a.n_rows * D;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
+         node += (int64_t)gridDim.x * blockDim.x)
+        apply_minv<D>(a.minv, v, a.z, node);
+}
+
+// partials of h_i = (w, v_i), i = 0..j, with w = V[j+1]; grid (nparts, j + 1): CTA (b, i) -> GPART(i)[b]
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_dots(GArgs a, int j) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const int i = blockIdx.y;
+    const int64_t n = a.n_rows * D;
+    const double* w = a.V + (int64_t)(j + 1) * n;
+    const double* v = a.V + (int64_t)i * n;
+    double acc = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        acc += w[k] * v[k];
+    const double bsum = block_sum(acc, sh);
+    if (threadIdx.x == 0) GPART(i)[blockIdx.x] = bsum;
+}
+
+// w -= sum_i h_i v_i; partial ||w||^2 -> GPART(GM_M + 1); CTA 0 stores H[:, j]
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_orth(GArgs a, int j) {
+    __shared__ double sh[32];
+    __shared__ double h[GM_M];
+    if (a.rec->done) return;
+    for (int i = 0; i <= j; ++i) {
+        const double v = sum_partials(GPART(i), a.nparts, sh);
+        if (threadIdx.x == 0) h[i] = v;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int i = 0; i <= j; ++i) a.H[i * GM_M + j] = h[i];
+    const int64_t n = a.n_rows * D;
+    double* w = a.V + (int64_t)(j + 1) * n;
+    double s1 = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double wk = w[k];
+        for (int i = 0; i <= j; ++i) wk -= h[i] * a.V[(int64_t)i * n + k];
+        w[k] = wk;
+        s1 += wk * wk;
+    }
+    const double b1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) GPART(GM_M + 1)[blockIdx.x] = b1;
+}
+
+// h_{j+1,j} = ||w||, v_{j+1} = w / h; CTA 0: Givens update and convergence test
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_norm(GArgs a, int j, int it_base, int maxit) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    const double hn = sqrt(sum_partials(GPART(GM_M + 1), a.nparts, sh));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double* H = a.H;
+        H[(j + 1) * GM_M + j] = hn;
+        // apply the previous rotations to column j
+        for (int i = 0; i < j; ++i) {
+            const double t1 = H[i * GM_M + j], t2 = H[(i + 1) * GM_M + j];
+            H[i * GM_M + j] = a.cs[i] * t1 + a.sn[i] * t2;
+            H[(i + 1) * GM_M + j] = -a.sn[i] * t1 + a.cs[i] * t2;
+        }
+        const double h0 = H[j * GM_M + j], h1 = H[(j + 1) * GM_M + j];
+        const double den = hypot(h0, h1);
+        const double c = den > 0.0 ? h0 / den : 1.0, s = den > 0.0 ? h1 / den : 0.0;
+        a.cs[j] = c;
+        a.sn[j] = s;
+        H[j * GM_M + j] = den;
+        H[(j + 1) * GM_M + j] = 0.0;
+        a.g[j + 1] = -s * a.g[j];
+        a.g[j] = c * a.g[j];
+        const double res2 = a.g[j + 1] * a.g[j + 1];
+        a.rec->rr = res2;
+        a.rec->its = j + 1;
+        if (!isfinite(res2) || den == 0.0) { a.rec->done = 2; a.rec->why = isfinite(res2) ? 4 : 2; }
+        else if (res2 <= a.rtol2 * a.rec->rr0 || hn == 0.0) { a.rec->done = 1; a.rec->why = 1; }
+        else if (it_base + j + 1 >= maxit) { a.rec->done = 3; a.rec->why = 6; }
+        else if (j + 1 == GM_M) { a.rec->done = 4; }   // end of the cycle: update and restart
+    }
+    if (hn == 0.0 || !isfinite(hn)) return;
+    const double ih = 1.0 / hn;
+    const int64_t n = a.n_rows * D;
+    double* w = a.V + (int64_t)(j + 1) * n;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        w[k] *= ih;
+}
+
+// x += M^-1 (V_k y), y = R^-1 g (k = its of the cycle); every CTA solves the small triangle itself
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_update(GArgs a, int k) {
+    __shared__ double y[GM_M];
+    if (threadIdx.x == 0) {
+        for (int i = k - 1; i >= 0; --i) {
+            double s = a.g[i];
+            for (int l = i + 1; l < k; ++l) s -= a.H[i * GM_M + l] * y[l];
+            y[i] = s / a.H[i * GM_M + i];
+        }
+    }
+    __syncthreads();
+    const int64_t n = a.n_rows * D;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        double u[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double s = 0.0;
+            for (int i = 0; i < k; ++i) s += y[i] * a.V[(int64_t)i * n + node * D + c];
+            u[c] = s;
+        }
+        const double* m = a.minv + node * (D * D);
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s += m[r * D + c] * u[c];
+            a.x[node * D + r] += s;
+        }
+    }
+}
+
+template <int D>
+static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b, double rtol, int maxit,
+                                 cudaStream_t s, int* its, double* relres, int* status) {
+    GArgs a;
+    a.n_rows = A.n_rows;
+    a.free_dof = A.free_dof;
+    a.minv = w.minv;
+    a.x = w.x;
+    a.r = w.r;
+    a.q = w.q;
+    a.z = w.z;
+    a.V = w.V;
+    a.H = w.gm;
+    a.cs = w.gm + (GM_M + 1) * GM_M;
+    a.sn = a.cs + (GM_M + 1);
+    a.g = a.sn + (GM_M + 1);
+    a.part = w.part;
+    a.nparts = w.nparts;
+    a.rec = w.rec;
+    a.rtol2 = rtol * rtol;
+    const int grid = w.grid;
+    int total = 0;
+    KrylovRec last{};
+    for (int cycle = 0;; ++cycle) {
+        a.cold = (cycle == 0);
+        if (cycle > 0) {
+            launch_spmv<D>(A, w.x, w.q, nullptr, nullptr, nullptr, grid, s);
+            w.launches += 1;
+        }
+        k_gm_init<D><<<grid, VB, 0, s>>>(a, b, cycle > 0 ? 1 : 0);
+        k_gm_start<D><<<grid, VB, 0, s>>>(a);
+        w.launches += 2;
+        int nev = 0;
+        for (int j = 0; j < GM_M; ++j) {
+            k_gm_prec<D><<<grid, VB, 0, s>>>(a, j);
+            if (w.profile) cudaEventRecord(w.ev[nev++], s);
+            launch_spmv<D>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
+            if (w.profile) cudaEventRecord(w.ev[nev++], s);
+            k_gm_dots<D><<<dim3(grid, j + 1), VB, 0, s>>>(a, j);
+            k_gm_orth<D><<<grid, VB, 0, s>>>(a, j);
+            k_gm_norm<D><<<grid, VB, 0, s>>>(a, j, total, maxit);
+            w.launches += 5;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(w.rec_host, w.rec, sizeof(KrylovRec), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        last = *w.rec_host;
+        if (w.profile) {
+            for (int j = 0; j < nev / 2 && j < last.its; ++j) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, w.ev[2 * j], w.ev[2 * j + 1]) == cudaSuccess) {
+                    w.spmv_ms += ms;
+                    w.spmv_n += 1;
+                }
+            }
+        }
+        if (last.its > 0) {
+            k_gm_update<D><<<grid, VB, 0, s>>>(a, last.its);
+            w.launches += 1;
+        }
+        total += last.its;
+        if (last.done != 4) break;           // converged, breakdown, non-finite or cap
+    }
+    *its = total;
+    *relres = last.rr0 > 0.0 ? sqrt(last.rr / last.rr0) : 0.0;
+    if (last.done == 1) *status = EP_OK;
+    else if (!std::isfinite(last.rr)) *status = EP_ERR_NAN;
+    else if (last.rr <= rtol * rtol * last.rr0) *status = EP_OK;
+    else *status = EP_ERR_KRYLOV;
+    return cudaStreamSynchronize(s);
+}
+
 cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
                          cudaStream_t s, int* its, double* relres, int* status) {
+    if (method == 3) {
+        if (A.dim == 2) return solve_gmres_t<2>(A, w, b, rtol, maxit, s, its, relres, status);
+        return solve_gmres_t<3>(A, w, b, rtol, maxit, s, its, relres, status);
+    }
     if (A.dim == 2) return solve_t<2>(A, w, b, method, rtol, maxit, s, its, relres, status);
     return solve_t<3>(A, w, b, method, rtol, maxit, s, its, relres, status);
 }

@@ -118,8 +118,12 @@ def test_constitutive_fuzz(ep, dim, model):
     assert rel_max(hard_new.cpu().numpy(), np.asarray(ref["hard"])) < TOL
 
 
+@pytest.mark.parametrize("method", [1, 2, 3])
 @pytest.mark.parametrize("model,elem,dim", [(VM_ISO, "P2", 2), (DP, "P2", 2), (VM_ISO, "Q1", 3), (DP, "P2", 3)])
-def test_krylov_solve_matches_direct(ep, model, elem, dim):
+def test_krylov_solve_matches_direct(ep, model, elem, dim, method):
+    """CG (symmetric tangents only), BiCGStab and GMRES vs a sparse direct solve."""
+    if method == 1 and model == DP:
+        pytest.skip("CG needs a symmetric tangent")
     import scipy.sparse.linalg as spla
     prob = small_problem(elem, dim, SIZES[(elem, dim)] + 1, model, seed=4)
     u, ep_, hard = fed_iterate(prob, seed=5, dilate=(1.0e-3 if model == DP else 0.0))
@@ -131,7 +135,8 @@ def test_krylov_solve_matches_direct(ep, model, elem, dim):
     free = prob.dirichlet == 0
     b = np.random.default_rng(6).standard_normal(prob.n_dof) * free
     for precond in (0, 1):
-        x, its, rel = ctx.linear_solve(b, ep.default_opts(krylov_rtol=1e-13, krylov_maxit=20000, precond=precond))
+        x, its, rel = ctx.linear_solve(b, ep.default_opts(krylov=method, krylov_rtol=1e-13, krylov_maxit=20000,
+                                                         precond=precond))
         xr = np.zeros(prob.n_dof)
         xr[free] = spla.spsolve(K[free][:, free].tocsc(), b[free])
         assert its > 0 and rel <= 1e-13
@@ -168,7 +173,8 @@ def test_load_path_p2_drucker_prager_column(ep):
     """Plane-strain P2 column, nonassociated DP, to 0.98 of the limit traction (reduced mesh)."""
     from synthetic import p2_plane_dp
     prob = p2_plane_dp(n=12, n_steps=20)
-    reps = _path_parity(ep, prob, 1e-12)
+    # near the limit load the tangent is ill-conditioned: 1e-11 in u needs a 1e-13 residual
+    reps = _path_parity(ep, prob, 1e-13, ep.default_opts(newton_rtol=1e-13, newton_maxit=40))
     assert reps[-1].n_plastic == prob.mesh.n_elem * 7
 
 
@@ -266,10 +272,13 @@ def test_krylov_cap_is_reported(ep):
 
 
 def test_resume_from_saved_state(ep):
-    """Checkpoint after k steps, restore into a fresh context, continue: same result (to FP64 atomics order)."""
+    """Checkpoint after k steps, restore into a fresh context, continue: the same solution.
+
+    FP64 atomics make the summation order, hence the last bits, differ from run to run, so the
+    two runs agree to the accuracy the Newton tolerance fixes (tight here), not bit for bit."""
     from synthetic import p2_plane_dp
     prob = p2_plane_dp(n=6, n_steps=10)
-    opts = ep.default_opts(newton_rtol=1e-12, warm_start=0)
+    opts = ep.default_opts(newton_rtol=1e-13, newton_maxit=40, warm_start=0)
     a = ep.Context.from_problem(prob)
     a.solve_load_path(prob.zeta, opts)
     b = ep.Context.from_problem(prob)
@@ -281,7 +290,7 @@ def test_resume_from_saved_state(ep):
         c.set(f, v)
     c.solve_load_path(prob.zeta[6:], opts)
     for f in (ep.EP_U, ep.EP_STRESS, ep.EP_PLASTIC_STRAIN):
-        assert rel_max(c.get(f), a.get(f)) < 1e-12
+        assert rel_max(c.get(f), a.get(f)) < 1e-11
     assert np.array_equal(a.get(ep.EP_PLASTIC_FLAG), c.get(ep.EP_PLASTIC_FLAG))
     a.close()
     c.close()
