@@ -98,7 +98,8 @@ typedef struct {
     int32_t krylov;              /* 0 auto (CG if the tangent is symmetric, else GMRES), 1 CG, 2 BiCGStab, 3 GMRES(30) */
     double krylov_rtol;          /* > 0: fixed relative tolerance; 0: adaptive forcing term */
     int32_t krylov_maxit;
-    int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks) */
+    int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks), 2 smoothed-aggregation AMG
+                                    (built from K_elast on first use; Chebyshev/block-Jacobi smoothing) */
     int32_t split_elastic_cache; /* 1: K = K_elast + sum over plastic points (eq. (K-split)); 0: K = B^T D B */
     int32_t warm_start;          /* 0: last converged u; 1: linear extrapolation of the last two steps */
     int32_t profile;             /* 1: time the assembly and SpMV kernels with CUDA events (fills t_*_kernel_ms) */
@@ -141,7 +142,7 @@ typedef struct {
     int32_t dim, n_p, n_q, n_comp;
 } ep_info;
 
-/* Fill *opts with defaults (FP64, rtol 1e-10, adaptive Krylov, block Jacobi, split on, no profiling). */
+/* Fill *opts with defaults (FP64, rtol 1e-10, adaptive Krylov, AMG, split on, no profiling). */
 void ep_default_opts(ep_opts* opts);
 
 /*

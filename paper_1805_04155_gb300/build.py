@@ -61,14 +61,14 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     for f in cpp:
         o = os.path.join(obj_dir, f[:-4] + ".o")
         objs.append(o)
-        jobs_list.append(([nvcc, *common, "-x", "c++", "-c", os.path.join(SRC, f), "-o", o], f))
+        jobs_list.append(([nvcc, *common, "-Xcompiler", "-fopenmp", "-x", "c++", "-c", os.path.join(SRC, f), "-o", o], f))
     jobs = jobs or max(2, min(len(jobs_list), os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         for src in ex.map(_compile, jobs_list):
             if verbose:
                 print(f"  compiled {src}", file=sys.stderr)
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xcompiler", "-fopenmp"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking libep.so failed:\n{' '.join(link)}\n{r.stdout}\n{r.stderr}")

@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "amg.h"
 #include "ep_internal.h"
 
 namespace ep {
@@ -164,6 +165,13 @@ struct Ctx {
     int launches = 0;          // kernels launched (instrumentation)
     int profile = 0;
     int verbose = 0;           // EP_VERBOSE=1: one line per Newton iteration on stderr
+    // host copies kept for the AMG setup
+    std::vector<int32_t> h_row_ptr, h_col_idx;
+    std::vector<double> h_coords;
+    std::vector<uint8_t> h_free;
+    AmgDev amg;
+    bool amg_built = false;
+    double amg_setup_ms = 0.0;
     std::vector<void*> allocs;
 };
 
@@ -296,7 +304,7 @@ void ep_default_opts(ep_opts* o) {
     o->krylov = 0;
     o->krylov_rtol = 0.0;
     o->krylov_maxit = 20000;
-    o->precond = 1;
+    o->precond = 2;
     o->split_elastic_cache = 1;
     o->warm_start = 1;
     o->profile = 0;
@@ -337,6 +345,7 @@ ep_status ep_destroy(void* ctx) {
     if (c->err_host) cudaFreeHost(c->err_host);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    amg_free(c->amg);
     cudaSetDevice(prev);
     delete c;
     return EP_OK;
@@ -501,7 +510,34 @@ ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, con
     CKF(launch_assemble(c->eid, a, s));
     CKF(cudaStreamSynchronize(s));
 #undef CKF
+    c->h_row_ptr = std::move(row_ptr);
+    c->h_col_idx = std::move(col_idx);
+    c->h_coords.assign(mesh->coords, mesh->coords + c->n_nodes * d);
+    c->h_free = std::move(freem);
     *out = c;
+    return EP_OK;
+}
+
+// Build the AMG hierarchy from K_elast on first use of preconditioner 2.
+static ep_status ensure_amg(Ctx* c) {
+    if (c->amg_built) return EP_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<double> kel((size_t)c->nnzb * c->dim * c->dim);
+    CK(cudaMemcpyAsync(kel.data(), c->Kel, sizeof(double) * kel.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    AmgInput in{c->dim, c->n_nodes, c->h_row_ptr.data(), c->h_col_idx.data(), kel.data(), c->h_free.data(),
+                c->h_coords.data()};
+    AmgHierarchy H;
+    if (!amg_setup_host(in, H, c->err)) return EP_ERR_STATE;
+    CK(amg_upload(H, c->amg, c->num_sms));
+    c->kw.amg = &c->amg;
+    c->amg_built = true;
+    c->amg_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (c->verbose) {
+        std::fprintf(stderr, "[ep] AMG: %zu levels, setup %.1f ms, sizes", H.levels.size(), c->amg_setup_ms);
+        for (auto& L : H.levels) std::fprintf(stderr, " %lld", (long long)L.n);
+        std::fprintf(stderr, "\n");
+    }
     return EP_OK;
 }
 
@@ -636,6 +672,10 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
         return EP_ERR_INVALID_ARG;
     }
     cudaSetDevice(c->device);
+    if (opts->precond == 2) {
+        ep_status st = ensure_amg(c);
+        if (st != EP_OK) return st;
+    }
     CK(cudaMemcpyAsync(c->r, b, sizeof(double) * c->n_dof, b_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->stream));
     const BsrDev A = bsr_dev(c, c->Kt);
@@ -664,6 +704,10 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     if (!(o.newton_rtol > 0.0) || o.newton_maxit < 1 || o.krylov_maxit < 1) return EP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
+    if (o.precond == 2) {
+        ep_status st = ensure_amg(c);
+        if (st != EP_OK) return st;
+    }
     const int method = krylov_method(c, o);
     const bool split = o.split_elastic_cache != 0;
     const BsrDev A = bsr_dev(c, c->Kt);
@@ -675,6 +719,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         float t_asm = 0.f, t_sol = 0.f;
         c->launches = 0;
         c->kw.launches = 0;
+        c->amg.launches = 0;
         c->kw.spmv_n = 0;
         c->kw.spmv_ms = 0.0;
         double t_asm_kernel = 0.0;
@@ -746,7 +791,6 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             rnorm_prev = rnorm;
             CK(cudaEventRecord(c->ev[2], s));
             CK(krylov_precond(A, c->kw, o.precond, s));
-            c->launches += 1;
             int kits = 0, kst = 0;
             double krel = 0.0;
             // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
@@ -804,7 +848,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         CK(cudaStreamSynchronize(s));
         rep.t_step_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_step0).count();
         rep.status = st;
-        rep.launches = c->launches + c->kw.launches;
+        rep.launches = c->launches + c->kw.launches + c->amg.launches;
         rep.n_spmv = c->kw.spmv_n;
         rep.t_spmv_kernel_ms = c->kw.spmv_ms;
         rep.t_assemble_kernel_ms = t_asm_kernel;

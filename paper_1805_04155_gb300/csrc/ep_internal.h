@@ -145,6 +145,8 @@ struct KrylovRec {
     int pad;
 };
 
+struct AmgDev;
+
 struct KrylovWork {
     int64_t n;               // vector length (n_rows*dim)
     int nparts;              // partial-sum slots per reduction
@@ -158,6 +160,9 @@ struct KrylovWork {
     int hist_len;
     KrylovRec* rec;          // device
     KrylovRec* rec_host;     // pinned host mirror
+    AmgDev* amg;             // AMG hierarchy (precond 2), owned by the context; null if not built
+    int use_amg;             // set by krylov_precond: 1 when the current preconditioner is the AMG V-cycle
+    int gm_m;                // GMRES restart length (<= GM_M)
     // instrumentation
     int profile;             // 1: CUDA events around every SpMV launch
     int launches;            // kernels launched by the solver (accumulates)
@@ -166,7 +171,7 @@ struct KrylovWork {
     cudaEvent_t ev[2 * 32];
 };
 
-constexpr int GM_M = 30;     // GMRES restart length
+constexpr int GM_M = 128;    // largest GMRES restart length (buffers); the run-time length is KrylovWork::gm_m
 cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms);
 void krylov_free(KrylovWork& w);
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s);

@@ -16,7 +16,9 @@
 // has finished, so the host may enqueue iterations in chunks and poll rarely.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
+#include "amg.h"
 #include "ep_internal.h"
 
 namespace ep {
@@ -201,6 +203,7 @@ struct KArgs {
     double rtol2;
     int maxit;
     int cold;           // 1 on the first start of a solve (fixes rr0), 0 on restarts
+    int amg;            // 1: the preconditioner is applied by separate V-cycle launches
 };
 
 #define PART(k) (a.part + (int64_t)(k) * a.nparts)
@@ -236,18 +239,19 @@ __global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__
             a.p[i] = 0.0;
             if (bicg) { a.rhat[i] = fr ? shadow_value(i, seed) : 0.0; a.v[i] = 0.0; }
         }
-        if (!bicg) apply_minv<D>(a.minv, a.r, a.z, node);
+        if (!bicg && !a.amg) apply_minv<D>(a.minv, a.r, a.z, node);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
-            s1 += (bicg ? a.rhat[i] : a.z[i]) * a.r[i];
+            if (bicg) s1 += a.rhat[i] * a.r[i];
+            else if (!a.amg) s1 += a.z[i] * a.r[i];
             s2 += a.r[i] * a.r[i];
         }
     }
     const double b1 = block_sum(s1, sh);
     const double b2 = block_sum(s2, sh);
     if (threadIdx.x == 0) {
-        PART(P_RZ)[blockIdx.x] = b1;
+        if (bicg || !a.amg) PART(P_RZ)[blockIdx.x] = b1;
         PART(P_RR)[blockIdx.x] = b2;
         if (blockIdx.x == 0) { a.rec->its = 0; a.rec->done = 0; a.rec->rr = 0.0; a.rec->why = 0; }
     }
@@ -303,20 +307,32 @@ __global__ void __launch_bounds__(VB) k_cg_update(KArgs a, int it) {
             a.x[i] += alpha * a.p[i];
             a.r[i] -= alpha * a.q[i];
         }
-        apply_minv<D>(a.minv, a.r, a.z, node);
+        if (!a.amg) apply_minv<D>(a.minv, a.r, a.z, node);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
-            s1 += a.r[i] * a.z[i];
+            if (!a.amg) s1 += a.r[i] * a.z[i];
             s2 += a.r[i] * a.r[i];
         }
     }
     const double b1 = block_sum(s1, sh);
     const double b2 = block_sum(s2, sh);
     if (threadIdx.x == 0) {
-        PART(P_RZ)[blockIdx.x] = b1;
+        if (!a.amg) PART(P_RZ)[blockIdx.x] = b1;
         PART(P_RR)[blockIdx.x] = b2;
     }
+}
+
+// partial of (x, y) into PART(slot), skipped once the solve is done
+__global__ void __launch_bounds__(VB) k_dot(KArgs a, const double* __restrict__ x, const double* __restrict__ y,
+                                             int64_t n, int slot) {
+    __shared__ double sh[32];
+    if (a.rec->done) return;
+    double s1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s1 += x[i] * y[i];
+    const double b1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) PART(slot)[blockIdx.x] = b1;
 }
 
 // BiCGStab: p = r + beta (p - omega v); phat = M^-1 p
@@ -344,7 +360,7 @@ __global__ void __launch_bounds__(VB) k_bicg_p(KArgs a, int it) {
             const int64_t i = node * D + c;
             a.p[i] = a.r[i] + beta * (a.p[i] - om * a.v[i]);
         }
-        apply_minv<D>(a.minv, a.p, a.phat, node);
+        if (!a.amg) apply_minv<D>(a.minv, a.p, a.phat, node);
     }
 }
 
@@ -367,7 +383,7 @@ __global__ void __launch_bounds__(VB) k_bicg_s(KArgs a, int it) {
             const int64_t i = node * D + c;
             a.s[i] = a.r[i] - alpha * a.v[i];
         }
-        apply_minv<D>(a.minv, a.s, a.shat, node);
+        if (!a.amg) apply_minv<D>(a.minv, a.s, a.shat, node);
     }
 }
 
@@ -426,6 +442,8 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
     w.grid = 2 * (num_sms > 0 ? num_sms : 152);
     w.nparts = w.grid;
     w.hist_len = maxit_cap + 2;
+    w.gm_m = 30;
+    if (const char* m = std::getenv("EP_GMRES_M")) w.gm_m = std::atoi(m);
     const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(w.n, 1);
     double** vecs[] = {&w.x, &w.r, &w.z, &w.p, &w.q, &w.rhat, &w.v, &w.s, &w.t, &w.phat, &w.shat};
     for (double** v : vecs) {
@@ -459,8 +477,15 @@ void krylov_free(KrylovWork& w) {
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s) {
     const unsigned g = (unsigned)((A.n_rows + 255) / 256);
     if (g == 0) return cudaSuccess;
-    if (A.dim == 2) k_precond<2><<<g, 256, 0, s>>>(A, w.minv, kind);
-    else k_precond<3><<<g, 256, 0, s>>>(A, w.minv, kind);
+    const int bj = (kind == 0) ? 0 : 1;    // the AMG smoother uses the block-Jacobi inverse
+    if (A.dim == 2) k_precond<2><<<g, 256, 0, s>>>(A, w.minv, bj);
+    else k_precond<3><<<g, 256, 0, s>>>(A, w.minv, bj);
+    w.launches += 1;
+    w.use_amg = (kind == 2 && w.amg) ? 1 : 0;
+    if (w.use_amg) {
+        cudaError_t e = amg_refresh(*w.amg, A, w.minv, s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -489,6 +514,7 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
     a.rec = w.rec;
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
+    a.amg = (w.use_amg && w.amg) ? 1 : 0;
     const int grid = w.grid;
     const bool bicg = (method == 2);
     const int chunk = 16;   // iterations enqueued between two polls of the device record
@@ -503,6 +529,11 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
     }
     k_init<D><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
     w.launches += 1;
+    if (a.amg && !bicg) {   // z = M^-1 r0, then (r, z)
+        amg_apply(*w.amg, A, w.minv, w.r, w.z, w.rec, s);
+        k_dot<<<grid, VB, 0, s>>>(a, w.r, w.z, w.n, P_RZ);
+        w.launches += 1;
+    }
     int it = 0;
     for (;;) {
         const int first = it;
@@ -516,12 +547,19 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
                 k_cg_update<D><<<grid, VB, 0, s>>>(a, it);
                 w.launches += 3;
+                if (a.amg) {
+                    amg_apply(*w.amg, A, w.minv, w.r, w.z, w.rec, s);
+                    k_dot<<<grid, VB, 0, s>>>(a, w.r, w.z, w.n, P_RZ);
+                    w.launches += 1;
+                }
             } else {
                 k_bicg_p<D><<<grid, VB, 0, s>>>(a, it);
+                if (a.amg) amg_apply(*w.amg, A, w.minv, w.p, w.phat, w.rec, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D>(A, w.phat, w.v, w.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
                 k_bicg_s<D><<<grid, VB, 0, s>>>(a, it);
+                if (a.amg) amg_apply(*w.amg, A, w.minv, w.s, w.shat, w.rec, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D>(A, w.shat, w.t, nullptr, nullptr, w.rec, grid, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
@@ -590,6 +628,7 @@ struct GArgs {
     KrylovRec* rec;
     double rtol2;
     int cold;
+    int m;              // restart length
 };
 
 #define GPART(k) (a.part + (int64_t)(k) * a.nparts)
@@ -626,7 +665,7 @@ __global__ void __launch_bounds__(VB) k_gm_start(GArgs a) {
         a.rec->rr = rr;
         a.rec->its = 0;
         a.g[0] = beta;
-        for (int i = 1; i <= GM_M; ++i) a.g[i] = 0.0;
+        for (int i = 1; i <= a.m; ++i) a.g[i] = 0.0;
         if (!isfinite(rr)) { a.rec->done = 2; a.rec->why = 2; }
         else if (conv) { a.rec->done = 1; a.rec->why = 1; }
     }
@@ -719,7 +758,7 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs a, int j, int it_base, int
         if (!isfinite(res2) || den == 0.0) { a.rec->done = 2; a.rec->why = isfinite(res2) ? 4 : 2; }
         else if (res2 <= a.rtol2 * a.rec->rr0 || hn == 0.0) { a.rec->done = 1; a.rec->why = 1; }
         else if (it_base + j + 1 >= maxit) { a.rec->done = 3; a.rec->why = 6; }
-        else if (j + 1 == GM_M) { a.rec->done = 4; }   // end of the cycle: update and restart
+        else if (j + 1 == a.m) { a.rec->done = 4; }   // end of the cycle: update and restart
     }
     if (hn == 0.0 || !isfinite(hn)) return;
     const double ih = 1.0 / hn;
@@ -762,6 +801,31 @@ __global__ void __launch_bounds__(VB) k_gm_update(GArgs a, int k) {
     }
 }
 
+// u = V_k y (y = R^-1 g solved redundantly by every CTA)
+template <int D>
+__global__ void __launch_bounds__(VB) k_gm_combine(GArgs a, int k, double* __restrict__ u) {
+    __shared__ double y[GM_M];
+    if (threadIdx.x == 0) {
+        for (int i = k - 1; i >= 0; --i) {
+            double s = a.g[i];
+            for (int l = i + 1; l < k; ++l) s -= a.H[i * GM_M + l] * y[l];
+            y[i] = s / a.H[i * GM_M + i];
+        }
+    }
+    __syncthreads();
+    const int64_t n = a.n_rows * D;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += y[i] * a.V[(int64_t)i * n + t];
+        u[t] = s;
+    }
+}
+
+__global__ void k_axpy_plain(double* __restrict__ x, const double* __restrict__ z, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += z[i];
+}
+
 template <int D>
 static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b, double rtol, int maxit,
                                  cudaStream_t s, int* its, double* relres, int* status) {
@@ -782,7 +846,9 @@ static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b
     a.nparts = w.nparts;
     a.rec = w.rec;
     a.rtol2 = rtol * rtol;
+    a.m = std::max(2, std::min(GM_M, w.gm_m > 0 ? w.gm_m : 30));
     const int grid = w.grid;
+    const bool use_amg = w.use_amg && w.amg;
     int total = 0;
     KrylovRec last{};
     for (int cycle = 0;; ++cycle) {
@@ -795,11 +861,13 @@ static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b
         k_gm_start<D><<<grid, VB, 0, s>>>(a);
         w.launches += 2;
         int nev = 0;
-        for (int j = 0; j < GM_M; ++j) {
-            k_gm_prec<D><<<grid, VB, 0, s>>>(a, j);
-            if (w.profile) cudaEventRecord(w.ev[nev++], s);
+        for (int j = 0; j < a.m; ++j) {
+            if (use_amg) amg_apply(*w.amg, A, w.minv, a.V + (int64_t)j * w.n, a.z, w.rec, s);
+            else k_gm_prec<D><<<grid, VB, 0, s>>>(a, j);
+            const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
+            if (ev_ok) cudaEventRecord(w.ev[nev++], s);
             launch_spmv<D>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
-            if (w.profile) cudaEventRecord(w.ev[nev++], s);
+            if (ev_ok) cudaEventRecord(w.ev[nev++], s);
             k_gm_dots<D><<<dim3(grid, j + 1), VB, 0, s>>>(a, j);
             k_gm_orth<D><<<grid, VB, 0, s>>>(a, j);
             k_gm_norm<D><<<grid, VB, 0, s>>>(a, j, total, maxit);
@@ -821,8 +889,15 @@ static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b
             }
         }
         if (last.its > 0) {
-            k_gm_update<D><<<grid, VB, 0, s>>>(a, last.its);
-            w.launches += 1;
+            if (use_amg) {
+                k_gm_combine<D><<<grid, VB, 0, s>>>(a, last.its, w.q);
+                amg_apply(*w.amg, A, w.minv, w.q, w.z, nullptr, s);
+                k_axpy_plain<<<grid, VB, 0, s>>>(w.x, w.z, w.n);
+                w.launches += 2;
+            } else {
+                k_gm_update<D><<<grid, VB, 0, s>>>(a, last.its);
+                w.launches += 1;
+            }
         }
         total += last.its;
         if (last.done != 4) break;           // converged, breakdown, non-finite or cap

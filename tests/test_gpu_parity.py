@@ -134,7 +134,7 @@ def test_krylov_solve_matches_direct(ep, model, elem, dim, method):
     K = ctx.K_csr()
     free = prob.dirichlet == 0
     b = np.random.default_rng(6).standard_normal(prob.n_dof) * free
-    for precond in (0, 1):
+    for precond in (0, 1, 2):
         x, its, rel = ctx.linear_solve(b, ep.default_opts(krylov=method, krylov_rtol=1e-13, krylov_maxit=20000,
                                                          precond=precond))
         xr = np.zeros(prob.n_dof)
@@ -266,7 +266,7 @@ def test_krylov_cap_is_reported(ep):
     ctx.assemble(np.zeros(prob.n_dof))
     b = np.ones(prob.n_dof) * (prob.dirichlet == 0)
     with pytest.raises(ep.EPError) as e:
-        ctx.linear_solve(b, ep.default_opts(krylov_rtol=1e-14, krylov_maxit=2))
+        ctx.linear_solve(b, ep.default_opts(krylov_rtol=1e-14, krylov_maxit=2, precond=1))
     assert e.value.status == ep.EP_ERR_KRYLOV
     ctx.close()
 
