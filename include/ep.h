@@ -231,10 +231,38 @@ ep_status ep_constitutive(const ep_material* mat, int32_t dim, int64_t n, const 
                           const double* ep_prev, const double* hard_prev, double* S, double* DS,
                           uint8_t* flag, double* ep_new, double* hard_new, void* cuda_stream);
 
+/*
+ * Workspace-free variant of ep_linear_solve, for callers that cannot allocate
+ * device memory: code that runs while another runtime owns the device's
+ * memory pool, or a phase in which no cudaMalloc may be issued.  The paper
+ * has no counterpart: this is an interface for such callers, not a step of
+ * the method.  The caller passes every array (device pointers): the
+ * block-CSR matrix of K (node blocks dim x dim, row-major blocks, as returned
+ * by EP_K_ROW_PTR / EP_K_COL_IDX / EP_K_VALUES), diag_slot [n_nodes] (index
+ * of each row's diagonal block), the free-DOF mask, b and the output x
+ * [n_nodes*dim] (zero on prescribed DOFs on return).  method: 1 CG, 2
+ * BiCGStab; precond: 0 Jacobi, 1 block Jacobi.  The solver's own buffers live
+ * in one fixed device array inside the library (about 3.7 MB), held by every
+ * GPU that loads the library until the process exits; it limits the system
+ * to EP_NOALLOC_MAX_DOF DOFs and maxit to EP_NOALLOC_MAX_ITERATIONS, and
+ * larger requests fail with EP_ERR_INVALID_ARG (message in
+ * ep_last_error(NULL)).  The first call on a device looks up that array's
+ * device address (with the device current), so make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * Issues no cudaMalloc/cudaFree and no allocating library call; runs on
+ * cuda_stream and returns after synchronising it.
+ */
+#define EP_NOALLOC_MAX_DOF 32768
+#define EP_NOALLOC_MAX_ITERATIONS 10000
+ep_status ep_linear_solve_noalloc(int32_t dim, int64_t n_nodes, const int32_t* row_ptr, const int32_t* col_idx,
+                                  const int32_t* diag_slot, const double* vals, const uint8_t* free_dof,
+                                  const double* b, double* x, int32_t method, int32_t precond, double rtol,
+                                  int32_t maxit, int32_t* iterations, double* rel_resid, void* cuda_stream);
+
 /* Human-readable name of a status code. */
 const char* ep_status_str(int32_t status);
 /* Message of the last failure of `ctx`; with ctx == NULL, the message of the
- * last failed ep_create on the calling thread. */
+ * last failed ep_create or ep_linear_solve_noalloc on the calling thread. */
 const char* ep_last_error(const void* ctx);
 
 #ifdef __cplusplus

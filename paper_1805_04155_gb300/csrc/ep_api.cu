@@ -291,8 +291,14 @@ static int krylov_method(const Ctx* c, const ep_opts& o) {
 
 using namespace ep;
 
-// message of the last failed ep_create on this thread (no context exists then)
-static thread_local std::string g_create_err;
+// message of the last failed context-free call on this thread (no context exists then)
+namespace ep {
+std::string& thread_error() {
+    static thread_local std::string msg;
+    return msg;
+}
+}  // namespace ep
+#define g_create_err (ep::thread_error())
 
 extern "C" {
 

@@ -111,6 +111,9 @@ cudaError_t launch_constitutive(int dim, const MatConst& m, int64_t n, const dou
                                 const double* hard_prev, double* S, double* DS, uint8_t* flag, double* ep_new,
                                 double* hard_new, cudaStream_t s);
 
+// Message of the last failed context-free call (ep_create, ep_linear_solve_noalloc) on this thread.
+std::string& thread_error();
+
 // Host-side reference tables (elements_host.cpp): gradients [n_q][n_p][dim], weights [n_q].
 void reference_tables(int family, int dim, std::vector<double>& dhat, std::vector<double>& wq);
 

@@ -30,7 +30,10 @@ EP_ELASTIC, EP_VM_KIN, EP_VM_ISO, EP_DP = range(4)
 EXPORTED = [
     "ep_default_opts", "ep_create", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set",
     "ep_assemble", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error",
+    "ep_linear_solve_noalloc",
 ]
+EP_NOALLOC_MAX_DOF = 32768
+EP_NOALLOC_MAX_ITERATIONS = 10000
 
 
 class ep_mesh(C.Structure):
@@ -88,6 +91,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_commit.argtypes = [vp, vp, i32]
     lib.ep_linear_solve.argtypes = [vp, vp, i32, C.POINTER(ep_opts), C.POINTER(i32), dp]
     lib.ep_constitutive.argtypes = [C.POINTER(ep_material), i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ep_linear_solve_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, vp, i32, i32, C.c_double, i32,
+                                            C.POINTER(i32), dp, vp]
+    lib.ep_linear_solve_noalloc.restype = i32
     lib.ep_status_str.argtypes = [i32]
     lib.ep_status_str.restype = C.c_char_p
     lib.ep_last_error.argtypes = [vp]
@@ -269,6 +275,23 @@ class Context:
         ci = self.get(EP_K_COL_IDX)
         vals = self.get(EP_K_ELASTIC if elastic else EP_K_VALUES)
         return sp.bsr_matrix((vals, ci, rp), shape=(self.n_dof, self.n_dof)).tocsr()
+
+
+def linear_solve_noalloc(dim: int, row_ptr, col_idx, diag_slot, vals, free_dof, b, x, method: int = 1,
+                         precond: int = 1, rtol: float = 1e-12, maxit: int = 10000, stream=None):
+    """ep_linear_solve_noalloc on torch CUDA tensors (the library allocates nothing for this call).
+
+    row_ptr/col_idx/diag_slot int32, vals float64 [nnzb][dim][dim], free_dof uint8, b and x float64.
+    Returns (status, iterations, relative residual); x is filled in place.
+    """
+    its = C.c_int32(0)
+    rel = C.c_double(0.0)
+    n_nodes = row_ptr.numel() - 1
+    st = lib().ep_linear_solve_noalloc(dim, n_nodes, row_ptr.data_ptr(), col_idx.data_ptr(), diag_slot.data_ptr(),
+                                       vals.data_ptr(), free_dof.data_ptr(), b.data_ptr(), x.data_ptr(), method,
+                                       precond, rtol, maxit, C.byref(its), C.byref(rel),
+                                       C.c_void_p(_stream_ptr(stream)))
+    return st, its.value, rel.value
 
 
 def constitutive(material, dim: int, E, ep_prev, hard_prev, stream=None):

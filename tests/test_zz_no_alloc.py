@@ -1,0 +1,79 @@
+"""The allocation-free Krylov entry point (ep_linear_solve_noalloc) against ep_linear_solve.
+
+Some callers cannot allocate device memory when they solve (another runtime
+owns the memory pool, or the phase forbids cudaMalloc); they hand the matrix
+and vectors in and the solver works in a fixed device array inside the
+library.  This file is collected last so that a failure here leaves every
+other test already run; it passes both alone and after the other tests.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def ep():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_04155_gb300 import build as b
+    b.build()
+    import paper_1805_04155_gb300.ep as mod
+    return mod
+
+
+def _system(ep, model, seed):
+    from gpu_helpers import fed_iterate, small_problem
+    prob = small_problem("P2", 2, 6, model, seed=seed)
+    u, ep_, hard = fed_iterate(prob, seed=seed + 1)
+    ctx = ep.Context.from_problem(prob)
+    ctx.set(ep.EP_PLASTIC_STRAIN, ep_)
+    ctx.set(ep.EP_HARDENING, hard)
+    ctx.assemble(u)
+    return prob, ctx
+
+
+@pytest.mark.parametrize("model,method", [(2, 1), (3, 2)])
+def test_noalloc_solve_matches_context_solve(ep, model, method):
+    prob, ctx = _system(ep, model, seed=11)
+    free = (prob.dirichlet == 0)
+    b = np.random.default_rng(12).standard_normal(prob.n_dof) * free
+    opts = ep.default_opts(krylov=method, krylov_rtol=1e-12, krylov_maxit=5000, precond=1)
+    x_ref, its_ref, rel_ref = ctx.linear_solve(b, opts)
+    rp = ctx.get(ep.EP_K_ROW_PTR)
+    ci = ctx.get(ep.EP_K_COL_IDX)
+    vals = ctx.get(ep.EP_K_VALUES)
+    diag = np.array([rp[i] + np.searchsorted(ci[rp[i]:rp[i + 1]], i) for i in range(len(rp) - 1)], dtype=np.int32)
+    assert np.all(ci[diag] == np.arange(len(rp) - 1))
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    args = [T(rp), T(ci), T(diag), T(vals), T(prob.dirichlet == 0).to(torch.uint8), T(b)]
+    for call in range(2):            # the second call must not see the first one's workspace
+        x = torch.full((prob.n_dof,), float("nan"), dtype=torch.float64, device=dev)
+        st, its, rel = ep.linear_solve_noalloc(2, *args, x, method=method, precond=1, rtol=1e-12, maxit=5000)
+        torch.cuda.synchronize()
+        assert st == ep.EP_OK, ep.lib().ep_last_error(None)
+        xh = x.cpu().numpy()
+        assert its == its_ref
+        assert np.all(xh[~free] == 0.0)
+        assert np.abs(xh - x_ref).max() <= TOL * np.abs(x_ref).max()
+    ctx.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_workspace(ep):
+    """Host-side check before any GPU work: more DOFs than the fixed array holds."""
+    dev = torch.device("cuda:0")
+    n_nodes = ep.EP_NOALLOC_MAX_DOF // 2 + 1
+    rp = torch.zeros(n_nodes + 1, dtype=torch.int32, device=dev)
+    one = torch.zeros(1, dtype=torch.int32, device=dev)
+    v = torch.zeros(4, dtype=torch.float64, device=dev)
+    m = torch.zeros(2 * n_nodes, dtype=torch.uint8, device=dev)
+    bx = torch.zeros(2 * n_nodes, dtype=torch.float64, device=dev)
+    st, _, _ = ep.linear_solve_noalloc(2, rp, one, one, v, m, bx, bx.clone())
+    assert st == ep.EP_ERR_INVALID_ARG
+    assert b"EP_NOALLOC_MAX_DOF" in ep.lib().ep_last_error(None)
+    st, _, _ = ep.linear_solve_noalloc(2, rp[:3], one, one, v, m, bx, bx.clone(), maxit=ep.EP_NOALLOC_MAX_ITERATIONS + 1)
+    assert st == ep.EP_ERR_INVALID_ARG
