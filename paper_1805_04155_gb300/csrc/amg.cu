@@ -1,14 +1,19 @@
-// Smoothed-aggregation AMG preconditioner: device V-cycle.
+// Smoothed-aggregation AMG preconditioner: device V-cycle and Galerkin refresh.
 //
-// Level 0 is the live tangent K (masked to the free DOFs) with its block-
-// Jacobi inverse; levels >= 1 are the Galerkin operators built once from
-// K_elast.  Smoother: Chebyshev polynomial of degree AMG_CHEB_DEGREE in
-// D^-1 A on [beta/30, beta], beta = 1.1 * rho(D^-1 A); the same polynomial
-// before and after the coarse correction keeps the V-cycle symmetric for
-// symmetric A.  The coarsest level is applied as a dense inverse.  Every
-// block-row product uses G lanes per row reading consecutive blocks.
+// Level 0 is the live tangent K (FP64, masked to the free DOFs) with its
+// block-Jacobi inverse.  Levels >= 1 are single precision and, after every
+// change of K, are rebuilt as Galerkin products A_{l+1} = R (A_l P) on the
+// device with the fixed patterns computed at setup, so the coarse spaces see
+// the plastic tangent's soft modes, not K_elast's.  Smoother: Chebyshev
+// polynomial of degree AMG_CHEB_DEGREE in D^-1 A on [beta/30, beta],
+// beta = 1.1 rho(D^-1 A) (rho by power iteration per level and per refresh);
+// the same polynomial before and after the coarse correction keeps the cycle
+// symmetric for symmetric A.  The coarsest level is a dense inverse, computed
+// on the host after each refresh.  Every block-row product uses G lanes per
+// row reading consecutive blocks.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "amg.h"
 
@@ -16,35 +21,33 @@ namespace ep {
 
 constexpr int AB = 256;   // threads per CTA
 
-struct MatView {
+template <class T>
+struct Mat {
     int64_t n_rows;
     const int32_t* row_ptr;
     const int32_t* col_idx;
-    const double* vals;
+    const T* vals;
     const uint8_t* mask;   // per DOF (level 0) or null
 };
 
-static MatView view(const DevBsr& M) { return MatView{M.n_rows, M.row_ptr, M.col_idx, M.vals, nullptr}; }
-static MatView view(const BsrDev& A) { return MatView{A.n_rows, A.row_ptr, A.col_idx, A.vals, A.free_dof}; }
-
 // acc = (M x)_row for a group of G lanes (every lane of the group gets the sum)
-template <int RB, int CB, int G>
-__device__ __forceinline__ void group_row(const MatView& M, int64_t row, bool active, int lg,
-                                          const double* __restrict__ x, double (&acc)[RB]) {
+template <int RB, int CB, int G, class TM, class TX, class TA>
+__device__ __forceinline__ void group_row(const Mat<TM>& M, int64_t row, bool active, int lg, const TX* __restrict__ x,
+                                          TA (&acc)[RB]) {
 #pragma unroll
-    for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+    for (int r = 0; r < RB; ++r) acc[r] = TA(0);
     if (active) {
         const int beg = M.row_ptr[row], end = M.row_ptr[row + 1];
         for (int k = beg + lg; k < end; k += G) {
             const int64_t col = M.col_idx[k];
-            const double* blk = M.vals + (int64_t)k * (RB * CB);
-            double xc[CB];
+            const TM* blk = M.vals + (int64_t)k * (RB * CB);
+            TA xc[CB];
 #pragma unroll
-            for (int c = 0; c < CB; ++c) xc[c] = x[col * CB + c];
+            for (int c = 0; c < CB; ++c) xc[c] = (TA)x[col * CB + c];
 #pragma unroll
             for (int r = 0; r < RB; ++r)
 #pragma unroll
-                for (int c = 0; c < CB; ++c) acc[r] += blk[r * CB + c] * xc[c];
+                for (int c = 0; c < CB; ++c) acc[r] += (TA)blk[r * CB + c] * xc[c];
         }
     }
 #pragma unroll
@@ -86,90 +89,89 @@ __device__ __forceinline__ ChebCoef cheb_coef(double lambda, int step) {
     return c;
 }
 
-// One Chebyshev update: r = b - A x_in (or b when x_in is zero), d = c1 d + c2 D^-1 r (step 0: D^-1 r / theta),
-// x_out = x_in + d.
-template <int RB, int G>
-__global__ void __launch_bounds__(AB) k_cheb(MatView A, const double* __restrict__ dinv, const double* __restrict__ b,
-                                              const double* __restrict__ x_in, double* __restrict__ x_out,
-                                              double* __restrict__ d, const double* lam, double lam_host, int step,
-                                              const KrylovRec* rec) {
+// One Chebyshev update in precision T: r = b - A x_in (or b when x_in is null),
+// d = c1 d + c2 D^-1 r (step 0: D^-1 r / theta), x_out = x_in + d.
+template <int RB, int G, class T>
+__global__ void __launch_bounds__(AB) k_cheb(Mat<T> A, const T* __restrict__ dinv, const T* __restrict__ b,
+                                              const T* __restrict__ x_in, T* __restrict__ x_out, T* __restrict__ d,
+                                              const double* lam, int step, const KrylovRec* rec) {
     if (rec && rec->done) return;
-    const ChebCoef cf = cheb_coef(lam ? *lam : lam_host, step);
+    const ChebCoef cf = cheb_coef(*lam, step);
     ROW_LOOP_BEGIN(A.n_rows)
-    double acc[RB];
-    if (x_in) group_row<RB, RB, G>(A, row, active, lg, x_in, acc);
+    T acc[RB];
+    if (x_in) group_row<RB, RB, G, T, T, T>(A, row, active, lg, x_in, acc);
     else {
 #pragma unroll
-        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+        for (int r = 0; r < RB; ++r) acc[r] = T(0);
     }
     if (active && lg == 0) {
-        double res[RB];
+        T res[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
             const int64_t i = row * RB + r;
             const bool fr = A.mask ? A.mask[i] != 0 : true;
-            res[r] = fr ? b[i] - acc[r] : 0.0;
+            res[r] = fr ? b[i] - acc[r] : T(0);
         }
-        const double* m = dinv + row * (RB * RB);
+        const T* m = dinv + row * (RB * RB);
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
             for (int c = 0; c < RB; ++c) s += m[r * RB + c] * res[c];
             const int64_t i = row * RB + r;
-            const double dn = (step == 0) ? cf.inv_theta * s : cf.c1 * d[i] + cf.c2 * s;
+            const T dn = (step == 0) ? (T)cf.inv_theta * s : (T)cf.c1 * d[i] + (T)cf.c2 * s;
             d[i] = dn;
-            x_out[i] = (x_in ? x_in[i] : 0.0) + dn;
+            x_out[i] = (x_in ? x_in[i] : T(0)) + dn;
         }
     }
     ROW_LOOP_END
 }
 
 // r = b - A x (masked)
-template <int RB, int G>
-__global__ void __launch_bounds__(AB) k_resid(MatView A, const double* __restrict__ b, const double* __restrict__ x,
-                                               double* __restrict__ r, const KrylovRec* rec) {
+template <int RB, int G, class T>
+__global__ void __launch_bounds__(AB) k_resid(Mat<T> A, const T* __restrict__ b, const T* __restrict__ x,
+                                               T* __restrict__ r, const KrylovRec* rec) {
     if (rec && rec->done) return;
     ROW_LOOP_BEGIN(A.n_rows)
-    double acc[RB];
-    group_row<RB, RB, G>(A, row, active, lg, x, acc);
+    T acc[RB];
+    group_row<RB, RB, G, T, T, T>(A, row, active, lg, x, acc);
     if (active && lg == 0) {
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
             const int64_t i = row * RB + q;
             const bool fr = A.mask ? A.mask[i] != 0 : true;
-            r[i] = fr ? b[i] - acc[q] : 0.0;
+            r[i] = fr ? b[i] - acc[q] : T(0);
         }
     }
     ROW_LOOP_END
 }
 
-// y = M x (add = 0) or y += M x (add = 1)
-template <int RB, int CB, int G>
-__global__ void __launch_bounds__(AB) k_mv(MatView M, const double* __restrict__ x, double* __restrict__ y, int add,
+// y = M x (add = 0) or y += M x (add = 1); FP32 matrix, FP32 accumulation
+template <int RB, int CB, int G, class TX, class TY>
+__global__ void __launch_bounds__(AB) k_mv(Mat<float> M, const TX* __restrict__ x, TY* __restrict__ y, int add,
                                             const KrylovRec* rec) {
     if (rec && rec->done) return;
     ROW_LOOP_BEGIN(M.n_rows)
-    double acc[RB];
-    group_row<RB, CB, G>(M, row, active, lg, x, acc);
+    float acc[RB];
+    group_row<RB, CB, G, float, TX, float>(M, row, active, lg, x, acc);
     if (active && lg == 0) {
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
             const int64_t i = row * RB + q;
-            y[i] = add ? y[i] + acc[q] : acc[q];
+            y[i] = add ? y[i] + (TY)acc[q] : (TY)acc[q];
         }
     }
     ROW_LOOP_END
 }
 
-// x = Ainv b, dense (coarsest level); one warp per row
-__global__ void __launch_bounds__(AB) k_dense(const double* __restrict__ Ainv, int64_t n, const double* __restrict__ b,
-                                               double* __restrict__ x, const KrylovRec* rec) {
+// x = Ainv b, dense FP32 (coarsest level); one warp per row
+__global__ void __launch_bounds__(AB) k_dense(const float* __restrict__ Ainv, int64_t n, const float* __restrict__ b,
+                                               float* __restrict__ x, const KrylovRec* rec) {
     if (rec && rec->done) return;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
-    double s = 0.0;
+    float s = 0.f;
     for (int64_t j = lane; j < n; j += 32) s += Ainv[warp * n + j] * b[j];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -177,32 +179,173 @@ __global__ void __launch_bounds__(AB) k_dense(const double* __restrict__ Ainv, i
 }
 
 // ---------------------------------------------------------------------------
-// power iteration for rho(D^-1 A) of the live level-0 matrix
+// Galerkin products with fixed patterns: T = A P, A_next = R T.  One warp per
+// output block row; the row is accumulated in shared memory (FP32), each lane
+// taking one block of the left factor at a time.
 // ---------------------------------------------------------------------------
-template <int RB, int G>
-__global__ void __launch_bounds__(AB) k_pw_apply(MatView A, const double* __restrict__ dinv,
-                                                  const double* __restrict__ x, double* __restrict__ y, double* part) {
+__device__ __forceinline__ int find_col(const int32_t* cols, int len, int c) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cols[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < len && cols[lo] == c) ? lo : -1;
+}
+
+template <int RA, int CA, int CP, class TA>
+__global__ void __launch_bounds__(AB) k_rap_ap(Mat<TA> A, Mat<float> P, DevPat T, float* __restrict__ Tvals,
+                                                int max_row) {
+    extern __shared__ float sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* acc = sm + (size_t)wib * max_row * (RA * CP);
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n_rows; i += nwarps) {
+        const int tb = T.row_ptr[i], tlen = T.row_ptr[i + 1] - tb;
+        const int32_t* tcols = T.col_idx + tb;
+        for (int e = lane; e < tlen * RA * CP; e += 32) acc[e] = 0.f;
+        __syncwarp();
+        for (int k = A.row_ptr[i] + lane; k < A.row_ptr[i + 1]; k += 32) {
+            const int64_t j = A.col_idx[k];
+            float a[RA * CA];
+#pragma unroll
+            for (int e = 0; e < RA * CA; ++e) a[e] = (float)A.vals[(int64_t)k * (RA * CA) + e];
+            for (int kp = P.row_ptr[j]; kp < P.row_ptr[j + 1]; ++kp) {
+                const int pos = find_col(tcols, tlen, P.col_idx[kp]);
+                if (pos < 0) continue;
+                const float* p = P.vals + (int64_t)kp * (CA * CP);
+                float* dst = acc + pos * (RA * CP);
+#pragma unroll
+                for (int r = 0; r < RA; ++r)
+#pragma unroll
+                    for (int c = 0; c < CP; ++c) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int m = 0; m < CA; ++m) s += a[r * CA + m] * p[m * CP + c];
+                        atomicAdd(dst + r * CP + c, s);
+                    }
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < tlen * RA * CP; e += 32) Tvals[(int64_t)tb * (RA * CP) + e] = acc[e];
+        __syncwarp();
+    }
+}
+
+template <int RR, int CR, int CT>
+__global__ void __launch_bounds__(AB) k_rap_rt(Mat<float> R, Mat<float> T, DevPat An, float* __restrict__ Anvals,
+                                                int max_row) {
+    extern __shared__ float sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* acc = sm + (size_t)wib * max_row * (RR * CT);
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < R.n_rows; a += nwarps) {
+        const int ab = An.row_ptr[a], alen = An.row_ptr[a + 1] - ab;
+        const int32_t* acols = An.col_idx + ab;
+        for (int e = lane; e < alen * RR * CT; e += 32) acc[e] = 0.f;
+        __syncwarp();
+        for (int k = R.row_ptr[a] + lane; k < R.row_ptr[a + 1]; k += 32) {
+            const int64_t i = R.col_idx[k];
+            float rb[RR * CR];
+#pragma unroll
+            for (int e = 0; e < RR * CR; ++e) rb[e] = R.vals[(int64_t)k * (RR * CR) + e];
+            for (int kt = T.row_ptr[i]; kt < T.row_ptr[i + 1]; ++kt) {
+                const int pos = find_col(acols, alen, T.col_idx[kt]);
+                if (pos < 0) continue;
+                const float* t = T.vals + (int64_t)kt * (CR * CT);
+                float* dst = acc + pos * (RR * CT);
+#pragma unroll
+                for (int r = 0; r < RR; ++r)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int m = 0; m < CR; ++m) s += rb[r * CR + m] * t[m * CT + c];
+                        atomicAdd(dst + r * CT + c, s);
+                    }
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < alen * RR * CT; e += 32) Anvals[(int64_t)ab * (RR * CT) + e] = acc[e];
+        __syncwarp();
+    }
+}
+
+// inverses of the BS x BS diagonal blocks (Gauss-Jordan with partial pivoting; identity if singular)
+template <int BS>
+__global__ void k_blockinv(DevPat A, const float* __restrict__ Avals, const int32_t* __restrict__ diag,
+                           float* __restrict__ dinv) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= A.n_rows) return;
+    float m[BS][BS], inv[BS][BS];
+    const float* src = Avals + (int64_t)diag[row] * (BS * BS);
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+        for (int c = 0; c < BS; ++c) {
+            m[r][c] = src[r * BS + c];
+            inv[r][c] = (r == c) ? 1.f : 0.f;
+        }
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+        int piv = c;
+        float best = fabsf(m[c][c]);
+#pragma unroll
+        for (int r = c + 1; r < BS; ++r)
+            if (fabsf(m[r][c]) > best) { best = fabsf(m[r][c]); piv = r; }
+        if (!(best > 0.f)) { ok = false; break; }
+        if (piv != c) {
+#pragma unroll
+            for (int k = 0; k < BS; ++k) {
+                float t = m[c][k]; m[c][k] = m[piv][k]; m[piv][k] = t;
+                t = inv[c][k]; inv[c][k] = inv[piv][k]; inv[piv][k] = t;
+            }
+        }
+        const float dd = 1.f / m[c][c];
+#pragma unroll
+        for (int k = 0; k < BS; ++k) { m[c][k] *= dd; inv[c][k] *= dd; }
+#pragma unroll
+        for (int r = 0; r < BS; ++r) {
+            if (r == c) continue;
+            const float f = m[r][c];
+#pragma unroll
+            for (int k = 0; k < BS; ++k) { m[r][k] -= f * m[c][k]; inv[r][k] -= f * inv[c][k]; }
+        }
+    }
+    float* dst = dinv + row * (BS * BS);
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+        for (int c = 0; c < BS; ++c) dst[r * BS + c] = ok ? inv[r][c] : (r == c ? 1.f : 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// power iteration for rho(D^-1 A) (level 0 in FP64, coarse levels in FP32)
+// ---------------------------------------------------------------------------
+template <int RB, int G, class T>
+__global__ void __launch_bounds__(AB) k_pw_apply(Mat<T> A, const T* __restrict__ dinv, const T* __restrict__ x,
+                                                  T* __restrict__ y, double* part) {
     __shared__ double sh[AB / 32];
     double s2 = 0.0;
     ROW_LOOP_BEGIN(A.n_rows)
-    double acc[RB];
-    group_row<RB, RB, G>(A, row, active, lg, x, acc);
+    T acc[RB];
+    group_row<RB, RB, G, T, T, T>(A, row, active, lg, x, acc);
     if (active && lg == 0) {
-        const double* m = dinv + row * (RB * RB);
+        const T* m = dinv + row * (RB * RB);
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
             for (int c = 0; c < RB; ++c) {
                 const bool fr = A.mask ? A.mask[row * RB + c] != 0 : true;
-                s += m[r * RB + c] * (fr ? acc[c] : 0.0);
+                s += m[r * RB + c] * (fr ? acc[c] : T(0));
             }
             y[row * RB + r] = s;
-            s2 += s * s;
+            s2 += (double)s * (double)s;
         }
     }
     ROW_LOOP_END
-    // CTA sum
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s2;
@@ -215,8 +358,8 @@ __global__ void __launch_bounds__(AB) k_pw_apply(MatView A, const double* __rest
 }
 
 // lambda = ||y|| (x had unit norm); x = y / ||y||
-__global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, double* y, double* x, int64_t n,
-                                                 double* lam) {
+template <class T>
+__global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, T* y, T* x, int64_t n, double* lam) {
     __shared__ double tot;
     if (threadIdx.x < 32) {
         double v = 0.0;
@@ -227,25 +370,26 @@ __global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, 
     }
     __syncthreads();
     const double nrm = sqrt(tot);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *lam = nrm;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *lam = (nrm > 0.0 && isfinite(nrm)) ? nrm : 1.0;
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = y[i] * inv;
+        x[i] = (T)((double)y[i] * inv);
 }
 
-__global__ void k_pw_init(double* x, int64_t n, const uint8_t* mask) {
+template <class T>
+__global__ void k_pw_init(T* x, int64_t n, const uint8_t* mask) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 12345ull;
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         z ^= z >> 31;
         const double v = (double)(z >> 11) * (1.0 / 9007199254740992.0) + 0.5;
-        x[i] = (mask && !mask[i]) ? 0.0 : v / sqrt((double)n);
+        x[i] = (mask && !mask[i]) ? T(0) : (T)(v / sqrt((double)n));
     }
 }
 
 // ---------------------------------------------------------------------------
-// Dispatch over block shapes
+// Dispatch helpers
 // ---------------------------------------------------------------------------
 static unsigned rows_grid(int64_t n_rows, int G) {
     const int64_t groups_per_cta = AB / G;
@@ -253,37 +397,36 @@ static unsigned rows_grid(int64_t n_rows, int G) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-template <int RB, int G>
-static void cheb_t(const MatView& A, const double* dinv, const double* b, const double* xi, double* xo, double* d,
-                   const double* lam, double lamh, int step, const KrylovRec* rec, cudaStream_t s) {
-    k_cheb<RB, G><<<rows_grid(A.n_rows, G), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, lamh, step, rec);
-}
-static void cheb(int bs, const MatView& A, const double* dinv, const double* b, const double* xi, double* xo,
-                 double* d, const double* lam, double lamh, int step, const KrylovRec* rec, cudaStream_t s) {
+static Mat<double> mat0(const BsrDev& A) { return Mat<double>{A.n_rows, A.row_ptr, A.col_idx, A.vals, A.free_dof}; }
+static Mat<float> matf(const DevPat& p, const float* v) { return Mat<float>{p.n_rows, p.row_ptr, p.col_idx, v, nullptr}; }
+
+template <class T>
+static void cheb(int bs, const Mat<T>& A, const T* dinv, const T* b, const T* xi, T* xo, T* d, const double* lam,
+                 int step, const KrylovRec* rec, cudaStream_t s) {
     switch (bs) {
-        case 2: cheb_t<2, 4>(A, dinv, b, xi, xo, d, lam, lamh, step, rec, s); break;
-        case 3: cheb_t<3, 8>(A, dinv, b, xi, xo, d, lam, lamh, step, rec, s); break;
-        case 6: cheb_t<6, 8>(A, dinv, b, xi, xo, d, lam, lamh, step, rec, s); break;
+        case 2: k_cheb<2, 4, T><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, step, rec); break;
+        case 3: k_cheb<3, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, step, rec); break;
+        case 6: k_cheb<6, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, step, rec); break;
     }
 }
-static void resid(int bs, const MatView& A, const double* b, const double* x, double* r, const KrylovRec* rec,
-                  cudaStream_t s) {
+template <class T>
+static void resid(int bs, const Mat<T>& A, const T* b, const T* x, T* r, const KrylovRec* rec, cudaStream_t s) {
     switch (bs) {
-        case 2: k_resid<2, 4><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, b, x, r, rec); break;
-        case 3: k_resid<3, 8><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, b, x, r, rec); break;
-        case 6: k_resid<6, 8><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, b, x, r, rec); break;
+        case 2: k_resid<2, 4, T><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, b, x, r, rec); break;
+        case 3: k_resid<3, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, b, x, r, rec); break;
+        case 6: k_resid<6, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, b, x, r, rec); break;
     }
 }
-static void mv(const DevBsr& M, const double* x, double* y, int add, const KrylovRec* rec, cudaStream_t s) {
-    const MatView v = view(M);
-    const int key = M.rb * 10 + M.cb;
-    switch (key) {
-        case 23: k_mv<2, 3, 4><<<rows_grid(M.n_rows, 4), AB, 0, s>>>(v, x, y, add, rec); break;
-        case 32: k_mv<3, 2, 8><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(v, x, y, add, rec); break;
-        case 33: k_mv<3, 3, 8><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(v, x, y, add, rec); break;
-        case 36: k_mv<3, 6, 8><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(v, x, y, add, rec); break;
-        case 63: k_mv<6, 3, 8><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(v, x, y, add, rec); break;
-        case 66: k_mv<6, 6, 8><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(v, x, y, add, rec); break;
+template <class TX, class TY>
+static void mv(const DevPat& p, const float* v, const TX* x, TY* y, int add, const KrylovRec* rec, cudaStream_t s) {
+    const Mat<float> M = matf(p, v);
+    switch (p.rb * 10 + p.cb) {
+        case 23: k_mv<2, 3, 4, TX, TY><<<rows_grid(M.n_rows, 4), AB, 0, s>>>(M, x, y, add, rec); break;
+        case 32: k_mv<3, 2, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
+        case 33: k_mv<3, 3, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
+        case 36: k_mv<3, 6, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
+        case 63: k_mv<6, 3, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
+        case 66: k_mv<6, 6, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
     }
 }
 
@@ -297,19 +440,25 @@ static cudaError_t up(AmgDev& D, T** dst, const std::vector<T>& src) {
     return e;
 }
 
-static cudaError_t up_bsr(AmgDev& D, DevBsr& d, const HostBsr& h) {
+static cudaError_t up_pat(AmgDev& D, DevPat& d, const HostBsr& h) {
     d.rb = h.rb;
     d.cb = h.cb;
     d.n_rows = h.n_rows;
     d.n_cols = h.n_cols;
     cudaError_t e;
     if ((e = up(D, &d.row_ptr, h.row_ptr)) != cudaSuccess) return e;
-    if ((e = up(D, &d.col_idx, h.col_idx)) != cudaSuccess) return e;
-    return up(D, &d.vals, h.vals);
+    return up(D, &d.col_idx, h.col_idx);
 }
 
-static cudaError_t dvec(AmgDev& D, double** p, int64_t n) {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(double) * std::max<int64_t>(1, n));
+static cudaError_t up_f(AmgDev& D, float** dst, const std::vector<double>& src, size_t n) {
+    std::vector<float> f(std::max<size_t>(n, 1), 0.f);
+    for (size_t i = 0; i < src.size() && i < f.size(); ++i) f[i] = (float)src[i];
+    return up(D, dst, f);
+}
+
+template <class T>
+static cudaError_t dvec(AmgDev& D, T** p, int64_t n) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<int64_t>(1, n));
     if (e == cudaSuccess) D.allocs.push_back(*p);
     return e;
 }
@@ -317,28 +466,47 @@ static cudaError_t dvec(AmgDev& D, double** p, int64_t n) {
 cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
     D.n_levels = (int)H.levels.size();
     cudaError_t e;
+    std::vector<double> lam(AMG_MAX_LEVELS, 1.0);
     for (int l = 0; l < D.n_levels; ++l) {
         const AmgLevel& L = H.levels[l];
         AmgDevLevel& d = D.lv[l];
         d.bs = L.bs;
         d.n = L.n;
-        d.lambda = L.lambda;
-        if (l > 0 && (e = up_bsr(D, d.A, L.A)) != cudaSuccess) return e;
-        if (!L.dinv.empty() && (e = up(D, &d.dinv, L.dinv)) != cudaSuccess) return e;
-        if (!L.P.vals.empty()) {
-            if ((e = up_bsr(D, d.P, L.P)) != cudaSuccess) return e;
-            if ((e = up_bsr(D, d.R, L.R)) != cudaSuccess) return e;
+        d.max_t_row = L.max_t_row;
+        d.max_next_row = L.max_next_row;
+        lam[l] = L.lambda;
+        if (l > 0) {
+            if ((e = up_pat(D, d.A, L.A)) != cudaSuccess) return e;
+            if ((e = up_f(D, &d.Avals, L.A.vals, L.A.vals.size())) != cudaSuccess) return e;
+            if ((e = up(D, &d.diag, L.diag)) != cudaSuccess) return e;
+            // one bs x bs block per row of A on every coarse level (the coarsest too, unused there)
+            if ((e = up_f(D, &d.dinv, L.dinv, (size_t)L.A.n_rows * L.bs * L.bs)) != cudaSuccess) return e;
+            float** fv[] = {&d.b, &d.x, &d.x2, &d.d, &d.r};
+            for (float** v : fv)
+                if ((e = dvec(D, v, L.n)) != cudaSuccess) return e;
+        } else {
+            double** dv[] = {&d.x2_0, &d.d_0, &d.r_0};
+            for (double** v : dv)
+                if ((e = dvec(D, v, L.n)) != cudaSuccess) return e;
         }
-        if (!L.dense_inv.empty() && (e = up(D, &d.dense_inv, L.dense_inv)) != cudaSuccess) return e;
-        double** vecs[] = {&d.b, &d.x, &d.x2, &d.d, &d.r};
-        for (double** v : vecs)
-            if ((e = dvec(D, v, L.n)) != cudaSuccess) return e;
+        if (!L.P.vals.empty()) {
+            if ((e = up_pat(D, d.P, L.P)) != cudaSuccess) return e;
+            if ((e = up_f(D, &d.Pvals, L.P.vals, L.P.vals.size())) != cudaSuccess) return e;
+            if ((e = up_pat(D, d.R, L.R)) != cudaSuccess) return e;
+            if ((e = up_f(D, &d.Rvals, L.R.vals, L.R.vals.size())) != cudaSuccess) return e;
+            if ((e = up_pat(D, d.T, L.T)) != cudaSuccess) return e;
+            if ((e = dvec(D, &d.Tvals, (int64_t)L.T.col_idx.size() * L.T.rb * L.T.cb)) != cudaSuccess) return e;
+        }
+        if (!L.dense_inv.empty() && (e = up_f(D, &d.dense_inv, L.dense_inv, L.dense_inv.size())) != cudaSuccess)
+            return e;
     }
     D.nparts = 2 * (num_sms > 0 ? num_sms : 152);
-    if ((e = dvec(D, &D.lambda0, 1)) != cudaSuccess) return e;
+    if ((e = dvec(D, &D.lam, AMG_MAX_LEVELS)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw, 2 * H.levels[0].n)) != cudaSuccess) return e;
+    const int64_t n1 = D.n_levels > 1 ? H.levels[1].n : 1;
+    if ((e = dvec(D, &D.pwf, 2 * n1)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw_part, D.nparts)) != cudaSuccess) return e;
-    return cudaMemcpy(D.lambda0, &H.levels[0].lambda, sizeof(double), cudaMemcpyHostToDevice);
+    return cudaMemcpy(D.lam, lam.data(), sizeof(double) * AMG_MAX_LEVELS, cudaMemcpyHostToDevice);
 }
 
 void amg_free(AmgDev& D) {
@@ -346,65 +514,182 @@ void amg_free(AmgDev& D) {
     D = AmgDev{};
 }
 
-cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, cudaStream_t s) {
-    const MatView A = view(A0);
-    const int64_t n = A0.n_rows * A0.dim;
-    double* x = D.pw;
-    double* y = D.pw + n;
-    k_pw_init<<<256, 256, 0, s>>>(x, n, A0.free_dof);
-    D.launches += 1;
+template <class T>
+static void power(AmgDev& D, int bs, const Mat<T>& A, const T* dinv, T* x, T* y, int64_t n, const uint8_t* mask,
+                  double* lam, cudaStream_t s) {
+    k_pw_init<T><<<256, 256, 0, s>>>(x, n, mask);
     for (int it = 0; it < 12; ++it) {
-        if (A0.dim == 2) k_pw_apply<2, 4><<<D.nparts, AB, 0, s>>>(A, minv0, x, y, D.pw_part);
-        else k_pw_apply<3, 8><<<D.nparts, AB, 0, s>>>(A, minv0, x, y, D.pw_part);
-        k_pw_norm<<<256, AB, 0, s>>>(D.pw_part, D.nparts, y, x, n, D.lambda0);
-        D.launches += 2;
+        switch (bs) {
+            case 2: k_pw_apply<2, 4, T><<<D.nparts, AB, 0, s>>>(A, dinv, x, y, D.pw_part); break;
+            case 3: k_pw_apply<3, 8, T><<<D.nparts, AB, 0, s>>>(A, dinv, x, y, D.pw_part); break;
+            case 6: k_pw_apply<6, 8, T><<<D.nparts, AB, 0, s>>>(A, dinv, x, y, D.pw_part); break;
+        }
+        k_pw_norm<T><<<256, AB, 0, s>>>(D.pw_part, D.nparts, y, x, n, lam);
     }
+    D.launches += 25;
+}
+
+template <class TA>
+static cudaError_t rap_level(AmgDev& D, int l, const Mat<TA>& A, cudaStream_t s) {
+    AmgDevLevel& L = D.lv[l];
+    AmgDevLevel& N = D.lv[l + 1];
+    const int bs = L.bs, k = N.bs;
+    // one warp per output row; as many warps per CTA as 160 KB of shared accumulators allow
+    const size_t per_ap = (size_t)std::max(1, L.max_t_row) * bs * k * sizeof(float);
+    const size_t per_rt = (size_t)std::max(1, L.max_next_row) * k * k * sizeof(float);
+    const size_t budget = 160 * 1024;
+    if (per_ap > budget || per_rt > budget) return cudaErrorInvalidConfiguration;
+    const int w_ap = (int)std::min<size_t>(AB / 32, budget / per_ap);
+    const int w_rt = (int)std::min<size_t>(AB / 32, budget / per_rt);
+    const size_t sm_ap = per_ap * w_ap, sm_rt = per_rt * w_rt;
+    const unsigned g_ap = (unsigned)std::max<int64_t>(1, std::min<int64_t>((A.n_rows + w_ap - 1) / w_ap, 152 * 64));
+    const unsigned g_rt = (unsigned)std::max<int64_t>(1, std::min<int64_t>((L.R.n_rows + w_rt - 1) / w_rt, 152 * 64));
+    const Mat<float> P = matf(L.P, L.Pvals);
+    const Mat<float> R = matf(L.R, L.Rvals);
+    const Mat<float> Tm = matf(L.T, L.Tvals);
+    cudaError_t e = cudaSuccess;
+#define EP_AP(RA, CP)                                                                                        \
+    {                                                                                                         \
+        auto kern = k_rap_ap<RA, RA, CP, TA>;                                                                 \
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ap)) !=       \
+            cudaSuccess)                                                                                      \
+            return e;                                                                                         \
+        kern<<<g_ap, 32 * w_ap, sm_ap, s>>>(A, P, L.T, L.Tvals, L.max_t_row);                                        \
+    }
+#define EP_RT(RR, CR)                                                                                        \
+    {                                                                                                         \
+        auto kern = k_rap_rt<RR, CR, RR>;                                                                     \
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rt)) !=       \
+            cudaSuccess)                                                                                      \
+            return e;                                                                                         \
+        kern<<<g_rt, 32 * w_rt, sm_rt, s>>>(R, Tm, N.A, N.Avals, L.max_next_row);                                    \
+    }
+    switch (bs * 10 + k) {
+        case 23: EP_AP(2, 3) EP_RT(3, 2) break;
+        case 36: EP_AP(3, 6) EP_RT(6, 3) break;
+        case 33: EP_AP(3, 3) EP_RT(3, 3) break;
+        case 66: EP_AP(6, 6) EP_RT(6, 6) break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef EP_AP
+#undef EP_RT
+    if (l + 1 < D.n_levels - 1) {   // block inverses feed the smoother; the coarsest level is inverted densely
+        const unsigned gb = (unsigned)((N.A.n_rows + 127) / 128);
+        if (k == 3) k_blockinv<3><<<gb, 128, 0, s>>>(N.A, N.Avals, N.diag, N.dinv);
+        else k_blockinv<6><<<gb, 128, 0, s>>>(N.A, N.Avals, N.diag, N.dinv);
+        D.launches += 1;
+    }
+    D.launches += 2;
     return cudaGetLastError();
+}
+
+cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s) {
+    const int L = D.n_levels;
+    const Mat<double> M0 = mat0(A0);
+    const int64_t n0 = A0.n_rows * A0.dim;
+    power<double>(D, A0.dim, M0, minv0, D.pw, D.pw + n0, n0, A0.free_dof, D.lam + 0, s);
+    if (!galerkin || L < 2) return cudaGetLastError();
+    cudaError_t e;
+    for (int l = 0; l + 1 < L; ++l) {
+        if (l == 0) e = rap_level<double>(D, 0, M0, s);
+        else e = rap_level<float>(D, l, matf(D.lv[l].A, D.lv[l].Avals), s);
+        if (e != cudaSuccess) return e;
+        AmgDevLevel& N = D.lv[l + 1];
+        if (l + 1 < L - 1)
+            power<float>(D, N.bs, matf(N.A, N.Avals), N.dinv, D.pwf, D.pwf + N.n, N.n, nullptr, D.lam + l + 1, s);
+    }
+    // coarsest: dense inverse on the host
+    AmgDevLevel& C = D.lv[L - 1];
+    const int64_t nb = C.A.n_rows, bs = C.bs, n = C.n;
+    std::vector<int32_t> rp(nb + 1), ci;
+    std::vector<float> v;
+    if ((e = cudaMemcpyAsync(rp.data(), C.A.row_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    ci.resize(rp[nb]);
+    v.resize((size_t)rp[nb] * bs * bs);
+    if ((e = cudaMemcpyAsync(ci.data(), C.A.col_idx, sizeof(int32_t) * ci.size(), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(v.data(), C.Avals, sizeof(float) * v.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    std::vector<double> dense((size_t)n * n, 0.0);
+    for (int64_t I = 0; I < nb; ++I)
+        for (int32_t b = rp[I]; b < rp[I + 1]; ++b)
+            for (int r = 0; r < bs; ++r)
+                for (int c = 0; c < bs; ++c)
+                    dense[(size_t)(I * bs + r) * n + (size_t)ci[b] * bs + c] = v[((size_t)b * bs + r) * bs + c];
+    if (!amg_invert_dense(dense, (int)n)) return cudaErrorInvalidValue;
+    std::vector<float> inv(dense.begin(), dense.end());
+    if ((e = cudaMemcpyAsync(C.dense_inv, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(s);
+}
+
+// 1-level hierarchy: out = Ainv in, FP32 inverse applied to FP64 vectors
+__global__ void __launch_bounds__(AB) k_dense_d(const float* __restrict__ Ainv, int64_t n, const double* __restrict__ b,
+                                                 double* __restrict__ x, const KrylovRec* rec) {
+    if (rec && rec->done) return;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += (double)Ainv[warp * n + j] * b[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) x[warp] = s;
 }
 
 cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const double* in, double* out,
                       const KrylovRec* rec, cudaStream_t s) {
     const int L = D.n_levels;
-    // descending leg
-    const double* b = in;
-    for (int l = 0; l < L - 1; ++l) {
-        AmgDevLevel& lv = D.lv[l];
-        const MatView A = (l == 0) ? view(A0) : view(lv.A);
-        const double* dinv = (l == 0) ? minv0 : lv.dinv;
-        const double* lam = (l == 0) ? D.lambda0 : nullptr;
-        double* xa = (l == 0) ? lv.x2 : lv.x2;
-        double* xb = (l == 0) ? out : lv.x;
-        // pre-smoothing from zero: step 0 -> xa, step 1 -> xb
-        cheb(lv.bs, A, dinv, b, nullptr, xa, lv.d, lam, lv.lambda, 0, rec, s);
-        cheb(lv.bs, A, dinv, b, xa, xb, lv.d, lam, lv.lambda, 1, rec, s);
-        resid(lv.bs, A, b, xb, lv.r, rec, s);
-        mv(lv.R, lv.r, D.lv[l + 1].b, 0, rec, s);
-        D.launches += 4;
-        b = D.lv[l + 1].b;
+    AmgDevLevel& l0 = D.lv[0];
+    if (L == 1) {
+        const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
+        k_dense_d<<<g, AB, 0, s>>>(l0.dense_inv, l0.n, in, out, rec);
+        D.launches += 1;
+        return cudaGetLastError();
     }
-    // coarsest
+    const Mat<double> M0 = mat0(A0);
+    const int bs0 = A0.dim;
+    // level 0 (FP64): pre-smoothing from zero, residual, restriction
+    cheb<double>(bs0, M0, minv0, in, nullptr, l0.x2_0, l0.d_0, D.lam + 0, 0, rec, s);
+    cheb<double>(bs0, M0, minv0, in, l0.x2_0, out, l0.d_0, D.lam + 0, 1, rec, s);
+    resid<double>(bs0, M0, in, out, l0.r_0, rec, s);
+    mv<double, float>(l0.R, l0.Rvals, l0.r_0, D.lv[1].b, 0, rec, s);
+    D.launches += 4;
+    // coarse levels (FP32), descending
+    for (int l = 1; l < L - 1; ++l) {
+        AmgDevLevel& v = D.lv[l];
+        const Mat<float> A = matf(v.A, v.Avals);
+        cheb<float>(v.bs, A, v.dinv, v.b, nullptr, v.x2, v.d, D.lam + l, 0, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.lam + l, 1, rec, s);
+        resid<float>(v.bs, A, v.b, v.x, v.r, rec, s);
+        mv<float, float>(v.R, v.Rvals, v.r, D.lv[l + 1].b, 0, rec, s);
+        D.launches += 4;
+    }
     {
         AmgDevLevel& c = D.lv[L - 1];
-        double* xc = (L == 1) ? out : c.x;
         const unsigned g = (unsigned)((c.n * 32 + AB - 1) / AB);
-        k_dense<<<g, AB, 0, s>>>(c.dense_inv, c.n, b, xc, rec);
+        k_dense<<<g, AB, 0, s>>>(c.dense_inv, c.n, c.b, c.x, rec);
         D.launches += 1;
     }
-    // ascending leg
-    for (int l = L - 2; l >= 0; --l) {
-        AmgDevLevel& lv = D.lv[l];
-        const MatView A = (l == 0) ? view(A0) : view(lv.A);
-        const double* dinv = (l == 0) ? minv0 : lv.dinv;
-        const double* lam = (l == 0) ? D.lambda0 : nullptr;
-        const double* bl = (l == 0) ? in : lv.b;
-        double* xb = (l == 0) ? out : lv.x;     // current iterate
-        double* xa = lv.x2;
-        mv(lv.P, D.lv[l + 1].x, xb, 1, rec, s);
-        // post-smoothing: xb -> xa -> xb
-        cheb(lv.bs, A, dinv, bl, xb, xa, lv.d, lam, lv.lambda, 0, rec, s);
-        cheb(lv.bs, A, dinv, bl, xa, xb, lv.d, lam, lv.lambda, 1, rec, s);
+    // ascending
+    for (int l = L - 2; l >= 1; --l) {
+        AmgDevLevel& v = D.lv[l];
+        const Mat<float> A = matf(v.A, v.Avals);
+        mv<float, float>(v.P, v.Pvals, D.lv[l + 1].x, v.x, 1, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, v.x, v.x2, v.d, D.lam + l, 0, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.lam + l, 1, rec, s);
         D.launches += 3;
     }
+    mv<float, double>(l0.P, l0.Pvals, D.lv[1].x, out, 1, rec, s);
+    cheb<double>(bs0, M0, minv0, in, out, l0.x2_0, l0.d_0, D.lam + 0, 0, rec, s);
+    cheb<double>(bs0, M0, minv0, in, l0.x2_0, out, l0.d_0, D.lam + 0, 1, rec, s);
+    D.launches += 3;
     return cudaGetLastError();
 }
 

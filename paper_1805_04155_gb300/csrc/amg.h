@@ -1,5 +1,5 @@
 // Smoothed-aggregation AMG preconditioner: host setup (amg_host.cpp) and the
-// device V-cycle (amg.cu).
+// device V-cycle with on-device Galerkin refresh (amg.cu).
 #pragma once
 
 #include <stdint.h>
@@ -11,7 +11,7 @@
 
 namespace ep {
 
-constexpr int AMG_COARSE_MAX = 1200;   // DOFs of the coarsest level (inverted densely)
+constexpr int AMG_COARSE_MAX = 600;    // DOFs of the coarsest level (inverted densely on the host)
 constexpr int AMG_MAX_LEVELS = 10;
 constexpr int AMG_CHEB_DEGREE = 2;     // Chebyshev smoothing steps before and after the coarse correction
 
@@ -26,9 +26,13 @@ struct AmgLevel {
     int bs = 0;                        // DOFs per block row of A at this level
     int64_t n = 0;                     // DOFs at this level
     HostBsr A;                         // operator (levels >= 1; level 0 is the live tangent)
+    std::vector<int32_t> diag;         // block index of each row's diagonal block in A (levels >= 1)
     std::vector<double> dinv;          // inverses of the bs x bs diagonal blocks
     double lambda = 1.0;               // spectral radius estimate of D^-1 A
     HostBsr P, R;                      // prolongation from the next level and its transpose
+    HostBsr T;                         // pattern of A P (values unused): the first Galerkin factor
+    int max_t_row = 0;                 // longest block row of T
+    int max_next_row = 0;              // longest block row of the next level's A
     std::vector<double> dense_inv;     // coarsest level only
 };
 
@@ -47,30 +51,37 @@ struct AmgInput {
 };
 
 bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err);
+// In-place inverse of a dense row-major n x n matrix (partial pivoting); false if singular.
+bool amg_invert_dense(std::vector<double>& M, int n);
 
-// Device side
-struct DevBsr {
+// Device side.  Coarse levels (>= 1) are single precision: the preconditioner's
+// precision does not limit the accuracy of the FP64 Krylov iteration it serves.
+struct DevPat {
     int rb = 0, cb = 0;
     int64_t n_rows = 0, n_cols = 0;
     int32_t *row_ptr = nullptr, *col_idx = nullptr;
-    double* vals = nullptr;
 };
 
 struct AmgDevLevel {
     int bs = 0;
     int64_t n = 0;
-    DevBsr A, P, R;
-    double* dinv = nullptr;
-    double lambda = 1.0;
-    double* dense_inv = nullptr;
-    double *b = nullptr, *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr;   // work vectors
+    DevPat A, P, R, T;                 // patterns (A for levels >= 1; P, R, T towards the next level)
+    float *Avals = nullptr, *Pvals = nullptr, *Rvals = nullptr, *Tvals = nullptr;
+    int32_t* diag = nullptr;           // diagonal block index per row of A (levels >= 1)
+    float* dinv = nullptr;             // levels >= 1
+    float* dense_inv = nullptr;        // coarsest level
+    float* dense_work = nullptr;       // coarsest level: [n][2n] Gauss-Jordan work
+    int max_t_row = 0, max_next_row = 0;
+    float *b = nullptr, *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr;   // levels >= 1
+    double *x2_0 = nullptr, *d_0 = nullptr, *r_0 = nullptr;                        // level 0 work (FP64)
 };
 
 struct AmgDev {
     int n_levels = 0;
     AmgDevLevel lv[AMG_MAX_LEVELS];
-    double* lambda0 = nullptr;         // device scalar: spectral radius estimate for the live level-0 matrix
-    double* pw = nullptr;              // power-iteration work [2][n0]
+    double* lam = nullptr;             // device [AMG_MAX_LEVELS]: spectral radius estimates per level
+    double* pw = nullptr;              // power-iteration work [2][n0] (FP64)
+    float* pwf = nullptr;              // power-iteration work [2][n1] (FP32)
     double* pw_part = nullptr;
     int nparts = 0;
     std::vector<void*> allocs;
@@ -79,9 +90,11 @@ struct AmgDev {
 
 cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms);
 void amg_free(AmgDev& D);
-// Refresh level-0 data for a new tangent: spectral radius of minv * A0 by power iteration.
-cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, cudaStream_t s);
-// One V-cycle: out = M^-1 in (level 0 uses A0 and its block-Jacobi inverse minv0).
+// New level-0 matrix A0 (with block-Jacobi inverse minv0): spectral estimate of level 0 and, when
+// galerkin != 0, coarse operators R A P recomputed from A0 down the hierarchy (with their block
+// inverses, spectral estimates and the coarsest dense inverse).
+cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s);
+// One V-cycle: out = M^-1 in (level 0 uses A0 and minv0).
 // rec (may be null): the calling solver's record; every launch exits at once once rec->done is set.
 cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const double* in, double* out,
                       const KrylovRec* rec, cudaStream_t s);

@@ -13,8 +13,11 @@
 // Prescribed DOFs are decoupled (identity rows) and have zero near-null rows,
 // so the coarse spaces never see them.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "amg.h"
@@ -249,11 +252,15 @@ std::vector<int32_t> aggregate(const Csr& A, int bs, double theta, int64_t& n_ag
     for (int64_t I = 0; I < nb; ++I)
         for (auto& [J, v] : nb_norm[I])
             if (J != I && v > theta * std::sqrt(dn[I] * dn[J])) strong[I].push_back(J);
+    // structurally decoupled nodes (only their own diagonal block: prescribed nodes, dead coarse DOFs)
+    // belong to no aggregate and get zero prolongator rows
+    std::vector<char> decoupled(nb, 0);
+    for (int64_t I = 0; I < nb; ++I) decoupled[I] = (nb_norm[I].size() == 1 && nb_norm[I][0].first == I);
     std::vector<int32_t> agg(nb, -1);
     n_agg = 0;
     // phase 1: root nodes whose strong neighbourhood is free
     for (int64_t I = 0; I < nb; ++I) {
-        if (agg[I] >= 0 || strong[I].empty()) continue;
+        if (decoupled[I] || agg[I] >= 0 || strong[I].empty()) continue;
         bool free_nb = true;
         for (int32_t J : strong[I])
             if (agg[J] >= 0) { free_nb = false; break; }
@@ -265,24 +272,26 @@ std::vector<int32_t> aggregate(const Csr& A, int bs, double theta, int64_t& n_ag
     // phase 2: attach to the aggregate of the strongest aggregated neighbour
     std::vector<int32_t> agg2 = agg;
     for (int64_t I = 0; I < nb; ++I) {
-        if (agg[I] >= 0) continue;
+        if (decoupled[I] || agg[I] >= 0) continue;
         double best = -1.0;
         for (auto& [J, v] : nb_norm[I])
             if (J != I && agg[J] >= 0 && v > best) { best = v; agg2[I] = agg[J]; }
     }
     agg = agg2;
-    // phase 3: leftovers (isolated or decoupled nodes) form their own aggregates
+    // phase 3: leftovers (not decoupled) form their own aggregates
     for (int64_t I = 0; I < nb; ++I) {
-        if (agg[I] >= 0) continue;
+        if (decoupled[I] || agg[I] >= 0) continue;
         agg[I] = (int32_t)n_agg;
         for (int32_t J : strong[I])
-            if (agg[J] < 0) agg[J] = (int32_t)n_agg;
+            if (agg[J] < 0 && !decoupled[J]) agg[J] = (int32_t)n_agg;
         ++n_agg;
     }
     return agg;
 }
 
 }  // namespace
+
+bool amg_invert_dense(std::vector<double>& M, int n) { return invert_dense(M, n); }
 
 bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err) {
     const int d = in.dim;
@@ -348,12 +357,33 @@ bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err) {
         AmgLevel L;
         L.bs = bs;
         L.n = A.n;
-        const bool coarsest = A.n <= AMG_COARSE_MAX || level >= AMG_MAX_LEVELS - 1;
+        bool coarsest = A.n <= AMG_COARSE_MAX || level >= AMG_MAX_LEVELS - 1;
+        if (!coarsest && level > 0 && A.n > (int64_t)(0.8 * (double)H.levels.back().n)) {
+            // coarsening stalled: stop here if the level is small enough to invert densely
+            if (A.n > 4 * AMG_COARSE_MAX) {
+                err = "AMG: coarsening stalled at " + std::to_string(A.n) + " DOFs";
+                return false;
+            }
+            coarsest = true;
+        }
         if (!coarsest) {
             L.dinv = block_diag_inv(A, bs);
             L.lambda = lambda_max(A, bs, L.dinv);
         }
-        if (level > 0) L.A = to_bsr(A, bs, bs);
+        if (level > 0) {
+            L.A = to_bsr(A, bs, bs);
+            L.diag.assign(L.A.n_rows, 0);
+            for (int64_t I = 0; I < L.A.n_rows; ++I) {
+                const int32_t* b = L.A.col_idx.data() + L.A.row_ptr[I];
+                const int32_t* e = L.A.col_idx.data() + L.A.row_ptr[I + 1];
+                const int32_t* it = std::lower_bound(b, e, (int32_t)I);
+                if (it == e || *it != I) {
+                    err = "AMG: coarse operator without a diagonal block";
+                    return false;
+                }
+                L.diag[I] = (int32_t)(it - L.A.col_idx.data());
+            }
+        }
         if (coarsest) {
             std::vector<double> M((size_t)A.n * A.n, 0.0);
             for (int64_t i = 0; i < A.n; ++i)
@@ -370,8 +400,12 @@ bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err) {
         int64_t n_agg = 0;
         const std::vector<int32_t> agg = aggregate(A, bs, level == 0 ? 0.02 : 0.0, n_agg);
         const int64_t nb = A.n / bs;
+        if (std::getenv("EP_AMG_DEBUG"))
+            std::fprintf(stderr, "[amg] level %d: %lld block rows, nnz %lld, %lld aggregates\n", level, (long long)nb,
+                         (long long)A.rp[A.n], (long long)n_agg);
         std::vector<std::vector<int32_t>> members(n_agg);
-        for (int64_t I = 0; I < nb; ++I) members[agg[I]].push_back((int32_t)I);
+        for (int64_t I = 0; I < nb; ++I)
+            if (agg[I] >= 0) members[agg[I]].push_back((int32_t)I);
         Csr P0;
         P0.n = A.n;
         P0.m = n_agg * k;
@@ -407,6 +441,11 @@ bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err) {
                     for (size_t t = 0; t < m; ++t) Q[t * k + j] /= nj;
                     R[(size_t)j * k + j] = nj;
                 }
+            }
+            if (std::getenv("EP_AMG_DEBUG")) {
+                int dropped = 0;
+                for (int j = 0; j < k; ++j) dropped += (R[(size_t)j * k + j] == 0.0);
+                if (dropped) std::fprintf(stderr, "[amg]   aggregate %lld: %zu dofs, %d of %d modes dropped\n", (long long)a, m, dropped, k);
             }
             for (size_t t = 0; t < m; ++t)
                 for (int j = 0; j < k; ++j)
@@ -507,6 +546,14 @@ bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err) {
         }
         L.P = to_bsr(P, bs, k);
         L.R = to_bsr(PT, k, bs);
+        L.T = to_bsr(AP, bs, k);
+        for (int64_t I = 0; I < L.T.n_rows; ++I)
+            L.max_t_row = std::max<int>(L.max_t_row, L.T.row_ptr[I + 1] - L.T.row_ptr[I]);
+        {
+            const HostBsr nextA = to_bsr(Ac, k, k);
+            for (int64_t I = 0; I < nextA.n_rows; ++I)
+                L.max_next_row = std::max<int>(L.max_next_row, nextA.row_ptr[I + 1] - nextA.row_ptr[I]);
+        }
         H.levels.push_back(std::move(L));
         A = std::move(Ac);
         B = std::move(Bc);

@@ -171,6 +171,7 @@ struct Ctx {
     std::vector<uint8_t> h_free;
     AmgDev amg;
     bool amg_built = false;
+    bool amg_elastic = true;     // the AMG coarse operators currently come from K_elast
     double amg_setup_ms = 0.0;
     std::vector<void*> allocs;
 };
@@ -685,6 +686,8 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
     CK(cudaMemcpyAsync(c->r, b, sizeof(double) * c->n_dof, b_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->stream));
     const BsrDev A = bsr_dev(c, c->Kt);
+    c->kw.galerkin = 1;
+    c->amg_elastic = false;
     CK(krylov_precond(A, c->kw, opts->precond, c->stream));
     int its = 0, status = 0;
     double rel = 0.0;
@@ -796,6 +799,10 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             }
             rnorm_prev = rnorm;
             CK(cudaEventRecord(c->ev[2], s));
+            // coarse operators from the current tangent unless it is exactly K_elast
+            const bool tangent_elastic = split && *c->counter_host == 0;
+            c->kw.galerkin = (tangent_elastic && c->amg_elastic) ? 0 : 1;
+            if (c->kw.galerkin) c->amg_elastic = tangent_elastic;
             CK(krylov_precond(A, c->kw, o.precond, s));
             int kits = 0, kst = 0;
             double krel = 0.0;

@@ -166,6 +166,7 @@ struct KrylovWork {
     AmgDev* amg;             // AMG hierarchy (precond 2), owned by the context; null if not built
     int use_amg;             // set by krylov_precond: 1 when the current preconditioner is the AMG V-cycle
     int gm_m;                // GMRES restart length (<= GM_M)
+    int galerkin;            // 1: recompute the AMG coarse operators from the current matrix in krylov_precond
     // instrumentation
     int profile;             // 1: CUDA events around every SpMV launch
     int launches;            // kernels launched by the solver (accumulates)

@@ -483,7 +483,7 @@ cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_
     w.launches += 1;
     w.use_amg = (kind == 2 && w.amg) ? 1 : 0;
     if (w.use_amg) {
-        cudaError_t e = amg_refresh(*w.amg, A, w.minv, s);
+        cudaError_t e = amg_refresh(*w.amg, A, w.minv, w.galerkin, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
