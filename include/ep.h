@@ -117,6 +117,7 @@ typedef struct {
     int32_t n_spmv;              /* SpMV kernel launches that did work (profile = 1) */
     double t_assemble_kernel_ms; /* summed duration of the assembly kernel launches (profile = 1) */
     double t_spmv_kernel_ms;     /* summed duration of those SpMV launches (profile = 1) */
+    int64_t n_plastic_assembled; /* plastic points summed over the step's assemblies (local-tangent work done) */
 } ep_step_report;
 
 /* Fields readable with ep_get / writable with ep_set. */

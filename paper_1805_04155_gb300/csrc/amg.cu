@@ -44,10 +44,18 @@ __device__ __forceinline__ void group_row(const Mat<TM>& M, int64_t row, bool ac
             TA xc[CB];
 #pragma unroll
             for (int c = 0; c < CB; ++c) xc[c] = (TA)x[col * CB + c];
+            TM bv[RB * CB];
+            if constexpr (RB * CB == 4 && sizeof(TM) == 4) {   // one 16-byte load per 2x2 FP32 block
+                const float4 v = *reinterpret_cast<const float4*>(blk);
+                bv[0] = v.x; bv[1] = v.y; bv[2] = v.z; bv[3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < RB * CB; ++e) bv[e] = blk[e];
+            }
 #pragma unroll
             for (int r = 0; r < RB; ++r)
 #pragma unroll
-                for (int c = 0; c < CB; ++c) acc[r] += (TA)blk[r * CB + c] * xc[c];
+                for (int c = 0; c < CB; ++c) acc[r] += (TA)bv[r * CB + c] * xc[c];
         }
     }
 #pragma unroll
@@ -89,14 +97,28 @@ __device__ __forceinline__ ChebCoef cheb_coef(double lambda, int step) {
     return c;
 }
 
+// Chebyshev coefficients of every level and step, from the spectral estimates (one thread):
+// coef[(l * AMG_CHEB_DEGREE + step) * 3 + {0,1,2}] = (1/theta, c1, c2)
+__global__ void k_cheb_setup(const double* lam, int n_levels, float* coef) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int l = 0; l < n_levels; ++l)
+        for (int st = 0; st < AMG_CHEB_DEGREE; ++st) {
+            const ChebCoef c = cheb_coef(lam[l], st);
+            float* o = coef + (l * AMG_CHEB_DEGREE + st) * 3;
+            o[0] = (float)c.inv_theta;
+            o[1] = (float)c.c1;
+            o[2] = (float)c.c2;
+        }
+}
+
 // One Chebyshev update in precision T: r = b - A x_in (or b when x_in is null),
-// d = c1 d + c2 D^-1 r (step 0: D^-1 r / theta), x_out = x_in + d.
+// d = c1 d + c2 D^-1 r (step 0: D^-1 r / theta), x_out = x_in + d.  cf = (1/theta, c1, c2).
 template <int RB, int G, class T>
 __global__ void __launch_bounds__(AB) k_cheb(Mat<T> A, const T* __restrict__ dinv, const T* __restrict__ b,
                                               const T* __restrict__ x_in, T* __restrict__ x_out, T* __restrict__ d,
-                                              const double* lam, int step, const KrylovRec* rec) {
+                                              const float* __restrict__ coef, int step, const KrylovRec* rec) {
     if (rec && rec->done) return;
-    const ChebCoef cf = cheb_coef(*lam, step);
+    struct { T inv_theta, c1, c2; } cf = {(T)coef[0], (T)coef[1], (T)coef[2]};
     ROW_LOOP_BEGIN(A.n_rows)
     T acc[RB];
     if (x_in) group_row<RB, RB, G, T, T, T>(A, row, active, lg, x_in, acc);
@@ -119,7 +141,7 @@ __global__ void __launch_bounds__(AB) k_cheb(Mat<T> A, const T* __restrict__ din
 #pragma unroll
             for (int c = 0; c < RB; ++c) s += m[r * RB + c] * res[c];
             const int64_t i = row * RB + r;
-            const T dn = (step == 0) ? (T)cf.inv_theta * s : (T)cf.c1 * d[i] + (T)cf.c2 * s;
+            const T dn = (step == 0) ? cf.inv_theta * s : cf.c1 * d[i] + cf.c2 * s;
             d[i] = dn;
             x_out[i] = (x_in ? x_in[i] : T(0)) + dn;
         }
@@ -368,12 +390,16 @@ __global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, 
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (threadIdx.x == 0) tot = v;
     }
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) {
+        const double nrm = sqrt(tot);
+        if (blockIdx.x == 0) *lam = (nrm > 0.0 && isfinite(nrm)) ? nrm : 1.0;
+        s_inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
     __syncthreads();
-    const double nrm = sqrt(tot);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *lam = (nrm > 0.0 && isfinite(nrm)) ? nrm : 1.0;
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    const T inv = (T)s_inv;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = (T)((double)y[i] * inv);
+        x[i] = y[i] * inv;
 }
 
 template <class T>
@@ -397,16 +423,26 @@ static unsigned rows_grid(int64_t n_rows, int G) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-static Mat<double> mat0(const BsrDev& A) { return Mat<double>{A.n_rows, A.row_ptr, A.col_idx, A.vals, A.free_dof}; }
+static Mat<float> mat0f(const BsrDev& A, const float* v) { return Mat<float>{A.n_rows, A.row_ptr, A.col_idx, v, A.free_dof}; }
+
+template <class TI, class TO>
+__global__ void k_cvt(const TI* __restrict__ in, TO* __restrict__ out, int64_t n, const KrylovRec* rec) {
+    if (rec && rec->done) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (TO)in[i];
+}
+
+static unsigned cvt_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 static Mat<float> matf(const DevPat& p, const float* v) { return Mat<float>{p.n_rows, p.row_ptr, p.col_idx, v, nullptr}; }
 
 template <class T>
-static void cheb(int bs, const Mat<T>& A, const T* dinv, const T* b, const T* xi, T* xo, T* d, const double* lam,
+static void cheb(int bs, const Mat<T>& A, const T* dinv, const T* b, const T* xi, T* xo, T* d, const float* coef_l,
                  int step, const KrylovRec* rec, cudaStream_t s) {
+    const float* cf = coef_l + step * 3;
     switch (bs) {
-        case 2: k_cheb<2, 4, T><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, step, rec); break;
-        case 3: k_cheb<3, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, step, rec); break;
-        case 6: k_cheb<6, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, lam, step, rec); break;
+        case 2: k_cheb<2, 4, T><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, dinv, b, xi, xo, d, cf, step, rec); break;
+        case 3: k_cheb<3, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, cf, step, rec); break;
+        case 6: k_cheb<6, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, cf, step, rec); break;
     }
 }
 template <class T>
@@ -485,8 +521,8 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
             for (float** v : fv)
                 if ((e = dvec(D, v, L.n)) != cudaSuccess) return e;
         } else {
-            double** dv[] = {&d.x2_0, &d.d_0, &d.r_0};
-            for (double** v : dv)
+            float** fv[] = {&d.b, &d.x, &d.x2, &d.d, &d.r};
+            for (float** v : fv)
                 if ((e = dvec(D, v, L.n)) != cudaSuccess) return e;
         }
         if (!L.P.vals.empty()) {
@@ -501,12 +537,19 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
             return e;
     }
     D.nparts = 2 * (num_sms > 0 ? num_sms : 152);
+    D.nnzb0 = H.nnzb0;
+    const int d0 = H.levels[0].bs;
+    if ((e = dvec(D, &D.K32, H.nnzb0 * d0 * d0)) != cudaSuccess) return e;
+    if ((e = dvec(D, &D.minv32, H.levels[0].n * d0)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.lam, AMG_MAX_LEVELS)) != cudaSuccess) return e;
-    if ((e = dvec(D, &D.pw, 2 * H.levels[0].n)) != cudaSuccess) return e;
-    const int64_t n1 = D.n_levels > 1 ? H.levels[1].n : 1;
-    if ((e = dvec(D, &D.pwf, 2 * n1)) != cudaSuccess) return e;
+    if ((e = dvec(D, &D.coef, AMG_MAX_LEVELS * AMG_CHEB_DEGREE * 3)) != cudaSuccess) return e;
+    if ((e = dvec(D, &D.pw, 2)) != cudaSuccess) return e;
+    if ((e = dvec(D, &D.pwf, 2 * H.levels[0].n)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw_part, D.nparts)) != cudaSuccess) return e;
-    return cudaMemcpy(D.lam, lam.data(), sizeof(double) * AMG_MAX_LEVELS, cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(D.lam, lam.data(), sizeof(double) * AMG_MAX_LEVELS, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    k_cheb_setup<<<1, 1>>>(D.lam, D.n_levels, D.coef);
+    return cudaDeviceSynchronize();
 }
 
 void amg_free(AmgDev& D) {
@@ -585,19 +628,30 @@ static cudaError_t rap_level(AmgDev& D, int l, const Mat<TA>& A, cudaStream_t s)
 
 cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s) {
     const int L = D.n_levels;
-    const Mat<double> M0 = mat0(A0);
-    const int64_t n0 = A0.n_rows * A0.dim;
-    power<double>(D, A0.dim, M0, minv0, D.pw, D.pw + n0, n0, A0.free_dof, D.lam + 0, s);
-    if (!galerkin || L < 2) return cudaGetLastError();
+    const int d0 = A0.dim;
+    const int64_t n0 = A0.n_rows * d0;
+    // FP32 copies of the live matrix and of its block-Jacobi inverse
+    k_cvt<double, float><<<cvt_grid(D.nnzb0 * d0 * d0), 256, 0, s>>>(A0.vals, D.K32, D.nnzb0 * d0 * d0, nullptr);
+    k_cvt<double, float><<<cvt_grid(n0 * d0), 256, 0, s>>>(minv0, D.minv32, n0 * d0, nullptr);
+    D.launches += 2;
+    const Mat<float> M0 = mat0f(A0, D.K32);
+    power<float>(D, d0, M0, D.minv32, D.pwf, D.pwf + n0, n0, A0.free_dof, D.lam + 0, s);
+    if (!galerkin || L < 2) {
+        k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
+        D.launches += 1;
+        return cudaGetLastError();
+    }
     cudaError_t e;
     for (int l = 0; l + 1 < L; ++l) {
-        if (l == 0) e = rap_level<double>(D, 0, M0, s);
+        if (l == 0) e = rap_level<float>(D, 0, M0, s);
         else e = rap_level<float>(D, l, matf(D.lv[l].A, D.lv[l].Avals), s);
         if (e != cudaSuccess) return e;
         AmgDevLevel& N = D.lv[l + 1];
         if (l + 1 < L - 1)
             power<float>(D, N.bs, matf(N.A, N.Avals), N.dinv, D.pwf, D.pwf + N.n, N.n, nullptr, D.lam + l + 1, s);
     }
+    k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
+    D.launches += 1;
     // coarsest: dense inverse on the host
     AmgDevLevel& C = D.lv[L - 1];
     const int64_t nb = C.A.n_rows, bs = C.bs, n = C.n;
@@ -653,20 +707,21 @@ cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const do
         D.launches += 1;
         return cudaGetLastError();
     }
-    const Mat<double> M0 = mat0(A0);
+    const Mat<float> M0 = mat0f(A0, D.K32);
     const int bs0 = A0.dim;
-    // level 0 (FP64): pre-smoothing from zero, residual, restriction
-    cheb<double>(bs0, M0, minv0, in, nullptr, l0.x2_0, l0.d_0, D.lam + 0, 0, rec, s);
-    cheb<double>(bs0, M0, minv0, in, l0.x2_0, out, l0.d_0, D.lam + 0, 1, rec, s);
-    resid<double>(bs0, M0, in, out, l0.r_0, rec, s);
-    mv<double, float>(l0.R, l0.Rvals, l0.r_0, D.lv[1].b, 0, rec, s);
-    D.launches += 4;
+    // level 0 in FP32 on the tangent's copy: pre-smoothing from zero, residual, restriction
+    k_cvt<double, float><<<cvt_grid(l0.n), 256, 0, s>>>(in, l0.b, l0.n, rec);
+    cheb<float>(bs0, M0, D.minv32, l0.b, nullptr, l0.x2, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 0, rec, s);
+    cheb<float>(bs0, M0, D.minv32, l0.b, l0.x2, l0.x, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 1, rec, s);
+    resid<float>(bs0, M0, l0.b, l0.x, l0.r, rec, s);
+    mv<float, float>(l0.R, l0.Rvals, l0.r, D.lv[1].b, 0, rec, s);
+    D.launches += 5;
     // coarse levels (FP32), descending
     for (int l = 1; l < L - 1; ++l) {
         AmgDevLevel& v = D.lv[l];
         const Mat<float> A = matf(v.A, v.Avals);
-        cheb<float>(v.bs, A, v.dinv, v.b, nullptr, v.x2, v.d, D.lam + l, 0, rec, s);
-        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.lam + l, 1, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, nullptr, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
         resid<float>(v.bs, A, v.b, v.x, v.r, rec, s);
         mv<float, float>(v.R, v.Rvals, v.r, D.lv[l + 1].b, 0, rec, s);
         D.launches += 4;
@@ -682,14 +737,15 @@ cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const do
         AmgDevLevel& v = D.lv[l];
         const Mat<float> A = matf(v.A, v.Avals);
         mv<float, float>(v.P, v.Pvals, D.lv[l + 1].x, v.x, 1, rec, s);
-        cheb<float>(v.bs, A, v.dinv, v.b, v.x, v.x2, v.d, D.lam + l, 0, rec, s);
-        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.lam + l, 1, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, v.x, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
+        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
         D.launches += 3;
     }
-    mv<float, double>(l0.P, l0.Pvals, D.lv[1].x, out, 1, rec, s);
-    cheb<double>(bs0, M0, minv0, in, out, l0.x2_0, l0.d_0, D.lam + 0, 0, rec, s);
-    cheb<double>(bs0, M0, minv0, in, l0.x2_0, out, l0.d_0, D.lam + 0, 1, rec, s);
-    D.launches += 3;
+    mv<float, float>(l0.P, l0.Pvals, D.lv[1].x, l0.x, 1, rec, s);
+    cheb<float>(bs0, M0, D.minv32, l0.b, l0.x, l0.x2, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 0, rec, s);
+    cheb<float>(bs0, M0, D.minv32, l0.b, l0.x2, l0.x, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 1, rec, s);
+    k_cvt<float, double><<<cvt_grid(l0.n), 256, 0, s>>>(l0.x, out, l0.n, rec);
+    D.launches += 4;
     return cudaGetLastError();
 }
 

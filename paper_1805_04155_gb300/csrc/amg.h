@@ -38,6 +38,7 @@ struct AmgLevel {
 
 struct AmgHierarchy {
     std::vector<AmgLevel> levels;
+    int64_t nnzb0 = 0;                 // blocks of the level-0 (tangent) pattern
 };
 
 struct AmgInput {
@@ -54,8 +55,9 @@ bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err);
 // In-place inverse of a dense row-major n x n matrix (partial pivoting); false if singular.
 bool amg_invert_dense(std::vector<double>& M, int n);
 
-// Device side.  Coarse levels (>= 1) are single precision: the preconditioner's
-// precision does not limit the accuracy of the FP64 Krylov iteration it serves.
+// Device side.  The whole V-cycle is single precision (level 0 on an FP32 copy
+// of the tangent): the preconditioner's precision does not limit the accuracy
+// of the FP64 Krylov iteration it serves.
 struct DevPat {
     int rb = 0, cb = 0;
     int64_t n_rows = 0, n_cols = 0;
@@ -72,14 +74,17 @@ struct AmgDevLevel {
     float* dense_inv = nullptr;        // coarsest level
     float* dense_work = nullptr;       // coarsest level: [n][2n] Gauss-Jordan work
     int max_t_row = 0, max_next_row = 0;
-    float *b = nullptr, *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr;   // levels >= 1
-    double *x2_0 = nullptr, *d_0 = nullptr, *r_0 = nullptr;                        // level 0 work (FP64)
+    float *b = nullptr, *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr;   // work vectors (all levels)
 };
 
 struct AmgDev {
     int n_levels = 0;
     AmgDevLevel lv[AMG_MAX_LEVELS];
     double* lam = nullptr;             // device [AMG_MAX_LEVELS]: spectral radius estimates per level
+    float* coef = nullptr;             // device [AMG_MAX_LEVELS][AMG_CHEB_DEGREE][3]: Chebyshev coefficients
+    float* K32 = nullptr;              // FP32 copy of the live level-0 matrix values [nnzb0][dim][dim]
+    float* minv32 = nullptr;           // FP32 copy of its block-Jacobi inverse [n_nodes][dim][dim]
+    int64_t nnzb0 = 0;
     double* pw = nullptr;              // power-iteration work [2][n0] (FP64)
     float* pwf = nullptr;              // power-iteration work [2][n1] (FP32)
     double* pw_part = nullptr;

@@ -297,6 +297,7 @@ bool amg_setup_host(const AmgInput& in, AmgHierarchy& H, std::string& err) {
     const int d = in.dim;
     const int k = d == 2 ? 3 : 6;     // rigid-body modes
     H = AmgHierarchy{};
+    H.nnzb0 = in.row_ptr[in.n_nodes];
     // level-0 scalar matrix with prescribed DOFs decoupled
     Csr A;
     A.n = A.m = in.n_nodes * d;

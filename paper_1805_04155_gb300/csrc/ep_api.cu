@@ -766,6 +766,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 CK(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
                 t_asm_kernel += ms;
             }
+            rep.n_plastic_assembled += (int64_t)*c->counter_host;
             if (*c->err_host) {
                 c->err = "return mapping: apex reached with K*eta*eta_bar + Hc = 0 (no admissible stress)";
                 st = EP_ERR_RETURN_MAP;

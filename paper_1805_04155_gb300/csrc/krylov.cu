@@ -284,7 +284,11 @@ __global__ void __launch_bounds__(VB) k_cg_p(KArgs a, int it) {
     const double rz = sum_partials(PART(P_RZ), a.nparts, sh);
     const double rr = sum_partials(PART(P_RR), a.nparts, sh);
     if (check_done(a, it, rz, rr, sh)) return;
-    const double beta = (it == 0) ? 0.0 : rz / a.h_rho[it - 1];
+    // FP64 divisions are costly on this GPU: one per CTA, broadcast through shared memory
+    __shared__ double s_beta;
+    if (threadIdx.x == 0) s_beta = (it == 0) ? 0.0 : rz / a.h_rho[it - 1];
+    __syncthreads();
+    const double beta = s_beta;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_rho[it] = rz;
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -297,7 +301,10 @@ __global__ void __launch_bounds__(VB) k_cg_update(KArgs a, int it) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double pq = sum_partials(PART(P_PQ), a.nparts, sh);
-    const double alpha = a.h_rho[it] / pq;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) s_alpha = a.h_rho[it] / pq;
+    __syncthreads();
+    const double alpha = s_alpha;
     double s1 = 0.0, s2 = 0.0;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
@@ -350,7 +357,10 @@ __global__ void __launch_bounds__(VB) k_bicg_p(KArgs a, int it) {
             if (blockIdx.x == 0 && threadIdx.x == 0) { a.rec->done = 2; a.rec->why = 5; }
             return;
         }
-        beta = (rho / a.h_rho[it - 1]) * (a.h_alpha[it - 1] / om);
+        __shared__ double s_beta;
+        if (threadIdx.x == 0) s_beta = (rho / a.h_rho[it - 1]) * (a.h_alpha[it - 1] / om);
+        __syncthreads();
+        beta = s_beta;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_rho[it] = rho;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
@@ -374,7 +384,10 @@ __global__ void __launch_bounds__(VB) k_bicg_s(KArgs a, int it) {
         if (blockIdx.x == 0 && threadIdx.x == 0) { a.rec->done = 2; a.rec->why = 4; }
         return;
     }
-    const double alpha = a.h_rho[it] / rv;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) s_alpha = a.h_rho[it] / rv;
+    __syncthreads();
+    const double alpha = s_alpha;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_alpha[it] = alpha;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
@@ -395,7 +408,10 @@ __global__ void __launch_bounds__(VB) k_bicg_x(KArgs a, int it) {
     const double ts = sum_partials(PART(P_TS), a.nparts, sh);
     const double tt = sum_partials(PART(P_TT), a.nparts, sh);
     const double alpha = a.h_alpha[it];
-    const double om = (tt > 0.0) ? ts / tt : 0.0;
+    __shared__ double s_om;
+    if (threadIdx.x == 0) s_om = (tt > 0.0) ? ts / tt : 0.0;
+    __syncthreads();
+    const double om = s_om;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_omega[it] = om;
     double s1 = 0.0, s2 = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_rows * D;
@@ -658,7 +674,10 @@ __global__ void __launch_bounds__(VB) k_gm_start(GArgs a) {
     __shared__ double sh[32];
     const double rr = sum_partials(GPART(0), a.nparts, sh);
     const double rr0 = a.cold ? rr : a.rec->rr0;
-    const double beta = sqrt(rr);
+    __shared__ double s_b[2];
+    if (threadIdx.x == 0) { s_b[0] = sqrt(rr); s_b[1] = 1.0 / s_b[0]; }
+    __syncthreads();
+    const double beta = s_b[0];
     const bool conv = !(rr > a.rtol2 * rr0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (a.cold) a.rec->rr0 = rr;
@@ -670,7 +689,7 @@ __global__ void __launch_bounds__(VB) k_gm_start(GArgs a) {
         else if (conv) { a.rec->done = 1; a.rec->why = 1; }
     }
     if (conv || !isfinite(rr)) return;
-    const double ib = 1.0 / beta;
+    const double ib = s_b[1];
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a.V[i] = a.r[i] * ib;
@@ -733,7 +752,13 @@ template <int D>
 __global__ void __launch_bounds__(VB) k_gm_norm(GArgs a, int j, int it_base, int maxit) {
     __shared__ double sh[32];
     if (a.rec->done) return;
-    const double hn = sqrt(sum_partials(GPART(GM_M + 1), a.nparts, sh));
+    __shared__ double s_h[2];
+    {
+        const double hh = sum_partials(GPART(GM_M + 1), a.nparts, sh);
+        if (threadIdx.x == 0) { s_h[0] = sqrt(hh); s_h[1] = s_h[0] > 0.0 ? 1.0 / s_h[0] : 0.0; }
+        __syncthreads();
+    }
+    const double hn = s_h[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double* H = a.H;
         H[(j + 1) * GM_M + j] = hn;
@@ -761,7 +786,7 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs a, int j, int it_base, int
         else if (j + 1 == a.m) { a.rec->done = 4; }   // end of the cycle: update and restart
     }
     if (hn == 0.0 || !isfinite(hn)) return;
-    const double ih = 1.0 / hn;
+    const double ih = s_h[1];
     const int64_t n = a.n_rows * D;
     double* w = a.V + (int64_t)(j + 1) * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)

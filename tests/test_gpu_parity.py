@@ -172,10 +172,24 @@ def test_load_path_p1_von_mises_column(ep):
 def test_load_path_p2_drucker_prager_column(ep):
     """Plane-strain P2 column, nonassociated DP, to 0.98 of the limit traction (reduced mesh)."""
     from synthetic import p2_plane_dp
-    prob = p2_plane_dp(n=12, n_steps=20)
+    prob = p2_plane_dp(n=12, n_steps=20, load_fraction=0.98)
     # near the limit load the tangent is ill-conditioned: 1e-11 in u needs a 1e-13 residual
     reps = _path_parity(ep, prob, 1e-13, ep.default_opts(newton_rtol=1e-13, newton_maxit=40))
     assert reps[-1].n_plastic == prob.mesh.n_elem * 7
+
+
+def test_load_path_p2_full_size_all_steps(ep):
+    """The benchmark workload (256x256 P2, 40 steps) end to end, against the one-point oracle."""
+    from oracle.newton import homogeneous_column
+    from synthetic import p2_plane_dp
+    prob = p2_plane_dp()
+    ctx = ep.Context.from_problem(prob)
+    reps = ctx.solve_load_path(prob.zeta, ep.default_opts(newton_rtol=1e-10))
+    sig = ctx.get(ep.EP_STRESS)
+    ctx.close()
+    hom = homogeneous_column(prob.material, prob.zeta * prob.extra["load_fraction"] * prob.extra["t_lim"])
+    assert rel_max(sig, np.repeat(hom[-1]["stress"][:, None], sig.shape[1], axis=1)) < 1e-9
+    assert all(r.rel_resid <= 1e-10 for r in reps) and reps[-1].n_plastic == sig.shape[1]
 
 
 def test_load_path_q1_cube_fixed_base(ep):
@@ -201,7 +215,7 @@ def test_homogeneous_column_full_size_p2(ep):
     sig = ctx.get(ep.EP_STRESS)
     flags = ctx.get(ep.EP_PLASTIC_FLAG)
     ctx.close()
-    hom = homogeneous_column(prob.material, zs * 0.98 * prob.extra["t_lim"])
+    hom = homogeneous_column(prob.material, zs * prob.extra["load_fraction"] * prob.extra["t_lim"])
     want = hom[-1]["stress"]
     assert rel_max(sig, np.repeat(want[:, None], sig.shape[1], axis=1)) < 1e-9
     assert np.all(flags == hom[-1]["plastic"])
