@@ -10,7 +10,11 @@ K = 40 times exactly one full 40-step load path.
 value = integration points assembled per second over the timed region
         (n_int x assemblies / elapsed), i.e. the rate at which the solver
         drives every integration point through return mapping + tangent
-        assembly, Krylov and update included.
+        assembly, Krylov and update included, for the primary precision
+        (--precision, default mixed: FP32 tangent and inner Krylov, FP64
+        return mapping, residual and update).  The other precision runs the
+        same load path after it ("compare": value, load-path time, Newton and
+        Krylov iterations, and the difference of the final displacements).
 roofline: the dominant kernel of the step (measured with CUDA events around
         every launch inside the timed region, on the context's stream).
 e2e:    the same metric through the C ABI with host buffers: each step
@@ -125,20 +129,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _spmv_bytes(info, dim):
-    """Algorithmic bytes of one masked block-CSR SpMV: values + column indices + row pointers +
-    x read once + y written once + free mask."""
+def _spmv_bytes(info, dim, vb=8):
+    """Algorithmic bytes of one masked block-CSR SpMV with vb-byte values and vectors: values +
+    column indices + row pointers + x read once + y written once + free mask."""
     nnzb, n_rows = info.nnz_blocks, info.n_nodes
     n = n_rows * dim
-    return nnzb * (dim * dim * 8 + 4) + (n_rows + 1) * 4 + n * 8 * 2 + n
+    return nnzb * (dim * dim * vb + 4) + (n_rows + 1) * 4 + n * vb * 2 + n
 
 
-def _assembly_bytes(info, dim, n_p, n_comp):
-    """Algorithmic bytes of one fused assembly launch (split or full form): cached gradients and
-    weights, connectivity, slot map, displacement gather, state read, F and K block updates."""
+def _assembly_bytes(info, dim, n_p, n_comp, kb=8):
+    """Algorithmic bytes of one fused assembly launch (split or full form) with kb-byte K values:
+    cached gradients and weights, connectivity, slot map, displacement gather, state read, F and K
+    block updates (K read and written once)."""
     n_int, n_e = info.n_int, info.n_elem
     return (n_int * (n_p * dim + 1) * 8 + n_e * n_p * 4 + n_e * n_p * n_p * 4 + n_e * n_p * dim * 8
-            + n_int * (n_comp + 1) * 8 + info.n_nodes * dim * 8 * 2 + info.nnz_blocks * dim * dim * 8 * 2)
+            + n_int * (n_comp + 1) * 8 + info.n_nodes * dim * 8 * 2 + info.nnz_blocks * dim * dim * kb * 2)
 
 
 def _tangent_flops_per_point(dim, n_p, sym):
@@ -149,6 +154,12 @@ def _tangent_flops_per_point(dim, n_p, sym):
     h = n_p * ns * dim * fm * 2
     nb = n_p * (n_p + 1) // 2 if sym else n_p * n_p
     return h + nb * dim * dim * fm * 2
+
+
+def _return_map_flops(model):
+    """FP64 FLOPs of the return mapping per point (trial state, yield test, correction), counted
+    from the closed forms of Section 2 (no division; one reciprocal square root counted as 10)."""
+    return {0: 30, 1: 110, 2: 100, 3: 120}.get(model, 120)
 
 
 def _base_flops_per_point(dim, n_p):
@@ -232,6 +243,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="cells per side (0: the workload's full size)")
     ap.add_argument("--skip", type=int, default=0,
                     help="run the first S load steps untimed before the timed region (bounded profiling)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the load path in the other precision")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -256,7 +269,7 @@ def main():
     ctx = ep.Context.from_problem(prob, device=local, stream=stream)
     info = ctx.info
     n_path = len(prob.zeta)
-    opts = ep.default_opts(newton_rtol=prob.newton_rtol, profile=1)
+    prec_of = {"mixed": ep.EP_MIXED, "fp64": ep.EP_FP64}
     zeros = {f: np.zeros(*ctx.field_shape(f)) for f in (ep.EP_U, ep.EP_PLASTIC_STRAIN, ep.EP_HARDENING,
                                                           ep.EP_STRESS, ep.EP_PLASTIC_FLAG)}
 
@@ -264,16 +277,15 @@ def main():
         for f, v in zeros.items():
             ctx.set(f, v)
 
-    # warm-up: first W load steps, then back to the virgin state
-    for j in range(args.warmup):
-        ctx.solve_load_path([prob.zeta[j % n_path]], opts)
-    reset()
+    def opts_for(prec):
+        return ep.default_opts(newton_rtol=prob.newton_rtol, profile=1, precision=prec_of[prec])
 
-    def timed(e2e: bool):
+    def timed(prec, e2e: bool, steps: int, skip: int):
+        opts = opts_for(prec)
         reps = []
         u_host = np.empty(ctx.n_dof) if e2e else None
         zbuf = np.empty(1)
-        for j in range(args.skip):
+        for j in range(skip):
             zbuf[0] = prob.zeta[j % n_path]
             ctx.solve_load_path(zbuf, opts)
         if world > 1:
@@ -283,10 +295,10 @@ def main():
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t_wall0 = time.perf_counter()
         ev0.record(stream)
-        for j in range(args.steps):
-            if j > 0 and (j + args.skip) % n_path == 0:
+        for j in range(steps):
+            if j > 0 and (j + skip) % n_path == 0:
                 reset()
-            zbuf[0] = prob.zeta[(j + args.skip) % n_path]
+            zbuf[0] = prob.zeta[(j + skip) % n_path]
             reps.extend(ctx.solve_load_path(zbuf, opts))
             if e2e:
                 ctx.get(ep.EP_U, out=u_host)
@@ -299,27 +311,61 @@ def main():
         wall = time.perf_counter() - t_wall0
         return ms, wall, reps
 
+    def max_over_ranks(ms):
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    prec = args.precision
+    other = "fp64" if prec == "mixed" else "mixed"
+    # warm-up: first W load steps in each precision used, then back to the virgin state
+    for p_ in ([prec] if args.no_compare else [prec, other]):
+        for j in range(args.warmup):
+            ctx.solve_load_path([prob.zeta[j % n_path]], opts_for(p_))
+        reset()
+
     clocks = Clocks(local)
-    ms, wall, reps = timed(False)
+    ms, wall, reps = timed(prec, False, args.steps, args.skip)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
+    ends_on_path_end = (args.skip + args.steps) % n_path == 0
+    u_primary = ctx.get(ep.EP_U) if ends_on_path_end else None
     assemblies = sum(r.n_assemble for r in reps)
     n_int = info.n_int
     value = world * n_int * assemblies / (ms / 1e3) / 1e9
 
+    compare = None
+    if not args.no_compare:
+        reset()
+        ms_o, _, reps_o = timed(other, False, n_path, 0)
+        ms_o = max_over_ranks(ms_o)
+        a_o = sum(r.n_assemble for r in reps_o)
+        u_o = ctx.get(ep.EP_U)
+        compare = {"precision": other, "value": world * n_int * a_o / (ms_o / 1e3) / 1e9, "unit": UNIT,
+                   "load_path_s": ms_o / 1e3, "newton_its": int(sum(r.newton_its for r in reps_o)),
+                   "krylov_its": int(sum(r.krylov_its for r in reps_o)),
+                   "max_rel_resid": max(r.rel_resid for r in reps_o),
+                   "assembly_avg_us": 1e3 * sum(r.t_assemble_kernel_ms for r in reps_o) / max(1, a_o),
+                   "spmv_avg_us": 1e3 * sum(r.t_spmv_kernel_ms for r in reps_o) / max(1, sum(r.n_spmv for r in reps_o))}
+        if u_primary is not None:
+            compare["u_rel_diff"] = float(np.linalg.norm(u_primary - u_o) / max(np.linalg.norm(u_o), 1e-300))
+        # the primary precision's load path time over one full path, for the side-by-side
+        compare["primary_load_path_s"] = ms / 1e3 * n_path / args.steps
+
     e2e = None
     if not args.no_e2e:
         reset()
-        ms_e2e, _, reps_e2e = timed(True)
+        ms_e2e, _, reps_e2e = timed(prec, True, args.steps, args.skip)
+        ms_e2e = max_over_ranks(ms_e2e)
         a2 = sum(r.n_assemble for r in reps_e2e)
         e2e = {"value": world * n_int * a2 / (ms_e2e / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8,
                "d2h_bytes_per_step": int(ctx.n_dof * 8)}
 
     # roofline of the dominant kernel (the SpMV inside the Krylov solves, or the assembly)
     dim = info.dim
+    f32 = prec == "mixed"
     peaks, peaks_kind = _peaks()
     t_spmv = sum(r.t_spmv_kernel_ms for r in reps)
     n_spmv = sum(r.n_spmv for r in reps)
@@ -329,36 +375,45 @@ def main():
     roof_spmv = roof_asm = None
     if n_spmv:
         dur = t_spmv / n_spmv / 1e3
-        by = _spmv_bytes(info, dim)
+        by = _spmv_bytes(info, dim, 4 if f32 else 8)
         gbs = by / dur / 1e9
         fl = 2.0 * info.nnz_blocks * dim * dim / dur / 1e12
         roof_spmv = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": "k_spmv (masked block-CSR, FP64)", "launches": n_spmv, "avg_us": dur * 1e6,
-                     "bytes_per_launch": by, "fp64_tflops": fl, "fp64_frac": fl / FP64_PEAK_TFLOPS,
+                     "kernel": f"k_spmv (masked block-CSR, {'FP32' if f32 else 'FP64'})", "launches": n_spmv,
+                     "avg_us": dur * 1e6, "bytes_per_launch": by, "tflops": fl,
                      "peak_source": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)", "share_of_step": t_spmv / ms}
+        if not f32:
+            roof_spmv["fp64_frac"] = fl / FP64_PEAK_TFLOPS
     if assemblies:
         dur = t_asmk / assemblies / 1e3
-        flops_per_launch = (plastic_assembled * _tangent_flops_per_point(dim, info.n_p, sym)
-                            + assemblies * n_int * _base_flops_per_point(dim, info.n_p)) / assemblies
-        fl = flops_per_launch / dur / 1e12
-        by = _assembly_bytes(info, dim, info.n_p, info.n_comp)
-        roof_asm = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": fl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_assemble (fused, FP64)",
-                    "launches": assemblies, "avg_us": dur * 1e6, "flops_per_launch": flops_per_launch,
+        tan = plastic_assembled * _tangent_flops_per_point(dim, info.n_p, sym) / assemblies
+        base = n_int * (_base_flops_per_point(dim, info.n_p) + _return_map_flops(prob.material.model))
+        fp64_flops = base + (0 if f32 else tan)
+        by = _assembly_bytes(info, dim, info.n_p, info.n_comp, 4 if f32 else 8)
+        gbs = by / dur / 1e9
+        roof_asm = {"bound": "hbm" if f32 else "alu", "kernel": f"k_assemble (fused, tangent {'FP32' if f32 else 'FP64'})",
+                    "launches": assemblies, "avg_us": dur * 1e6, "traffic": None,
+                    "bytes_per_launch": by, "fp64_flops_per_launch": fp64_flops,
+                    "fp32_flops_per_launch": tan if f32 else 0.0,
                     "plastic_fraction": plastic_assembled / max(1, assemblies * n_int),
-                    "hbm_gbs": by / dur / 1e9,
-                    "hbm_frac": by / dur / 1e9 / peaks["hbm_gbs"],
-                    "assembled_gpts_s": n_int / dur / 1e9,
-                    "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
-                    "share_of_step": t_asmk / ms}
+                    "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
+                    "fp64_tflops": fp64_flops / dur / 1e12, "fp64_frac": fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS,
+                    "assembled_gpts_s": n_int / dur / 1e9, "share_of_step": t_asmk / ms,
+                    "peak_source": (f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)" if f32 else
+                                    "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)")}
+        if f32:
+            roof_asm.update({"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]})
+        else:
+            roof_asm.update({"achieved": fp64_flops / dur / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS})
     dominant = roof_spmv if (roof_spmv and t_spmv >= t_asmk) else roof_asm
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if f32 else "f64", "data": "synthetic",
             "config": _workload_config(args.workload, prob, {
-                "n_int": n_int, "parallelism": "replicas" if world > 1 else "single GPU",
+                "n_int": n_int, "parallelism": "replicas" if world > 1 else "single GPU", "precision": prec,
                 "krylov": "GMRES(30)" if prob.material.model == 3 and prob.material.psi != prob.material.phi
                 else "CG", "precond": "smoothed-aggregation AMG, FP32 V-cycle, Galerkin from the tangent",
                 "split_elastic_cache": True, "skip": args.skip}),
@@ -369,6 +424,8 @@ def main():
             "n_plastic_final": int(reps[-1].n_plastic) if reps else 0,
             "max_rel_resid": max(r.rel_resid for r in reps) if reps else None,
             "wall_s": wall}
+    if compare:
+        line["compare"] = compare
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline and world == 1:

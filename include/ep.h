@@ -64,6 +64,16 @@ typedef enum {
     EP_DP = 3         /* Drucker-Prager; nonassociated (psi != phi) and cohesion hardening Hc optional */
 } ep_model;
 
+/*
+ * Arithmetic of a solve.  EP_FP64: every step in FP64.  EP_MIXED: strains, the
+ * return mapping (yield test and plastic multiplier), the internal forces F,
+ * the Newton residual and its norms and the update of u stay FP64; the
+ * tangent D_p is rounded to FP32 per point and the local element matrices,
+ * their assembly into K and the inner Krylov solve (vectors, SpMV,
+ * preconditioner) run in FP32.  Newton on the FP64 residual is the outer
+ * refinement, so the load path still reaches newton_rtol; the inner relative
+ * tolerance is not taken below 1e-5.
+ */
 typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
 
 /* Mesh (Section 6: ELEM and COORD).  Host pointers, copied by ep_create. */
@@ -92,7 +102,7 @@ typedef struct {
 } ep_bc;
 
 typedef struct {
-    int32_t precision;           /* ep_precision (EP_FP64 only in this version) */
+    int32_t precision;           /* ep_precision */
     double newton_rtol;          /* ||(f - F)_free|| <= rtol * max(||f_free||, ||F||) */
     int32_t newton_maxit;
     int32_t krylov;              /* 0 auto (CG if the tangent is symmetric, else GMRES), 1 CG, 2 BiCGStab, 3 GMRES(30) */
@@ -134,7 +144,9 @@ typedef enum {
     EP_K_ELASTIC = 9,        /* double [nnz_blocks][dim][dim], K_elast (read only) */
     EP_WEIGHT = 10,          /* double [n_int], |det J| w_q (Section 6.3, WEIGHT) (read only) */
     EP_DPHI = 11,            /* double [n_int][n_p][dim], physical basis gradients (Section 6.1, DPhi) (read only) */
-    EP_SOLUTION = 12         /* double [n_nodes*dim], x of the last ep_linear_solve (read only) */
+    EP_SOLUTION = 12,        /* double [n_nodes*dim], x of the last ep_linear_solve (read only) */
+    EP_K_VALUES_F32 = 13     /* float [nnz_blocks][dim][dim], K of the last EP_MIXED assembly (read only;
+                                EP_ERR_STATE before the first one) */
 } ep_field;
 
 /* Sizes of a context: n_int, n_comp, nnz_blocks, n_p, n_q. */
@@ -200,6 +212,15 @@ ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_
 ep_status ep_assemble(void* ctx, const double* u, int32_t u_is_device, int32_t split, int64_t* n_plastic);
 
 /*
+ * ep_assemble with the tangent's precision chosen (ep_precision): EP_FP64 is
+ * ep_assemble; EP_MIXED computes strains, return mapping and F in FP64 as
+ * ep_assemble does and forms the tangent in FP32 into EP_K_VALUES_F32 (the
+ * split path starts from K_elast rounded to FP32).
+ */
+ep_status ep_assemble_prec(void* ctx, const double* u, int32_t u_is_device, int32_t split, int32_t precision,
+                           int64_t* n_plastic);
+
+/*
  * Commit the state at displacement u (host or device): evaluate the return
  * mapping at every point and store sigma_k, eps^p_k, the hardening variable
  * and the plastic flags (Sections 2.2, 2.3, the T_other updates) as the new
@@ -211,7 +232,9 @@ ep_status ep_commit(void* ctx, const double* u, int32_t u_is_device);
  * Solve K x = b on the free DOFs with the matrix of the last ep_assemble
  * (eq. (lin_syst)); b is a host or device array [n_nodes*dim] (prescribed
  * entries ignored), x is kept as EP_SOLUTION (zero on prescribed DOFs).  Uses
- * opts->krylov, krylov_rtol (must be > 0 here), krylov_maxit, precond.
+ * opts->krylov, krylov_rtol (must be > 0 here), krylov_maxit, precond and
+ * precision: EP_MIXED solves with the FP32 matrix of the last EP_MIXED
+ * assembly in FP32 arithmetic (b rounded to FP32, x returned as double).
  * *iterations and *rel_resid (may be NULL) receive the iteration count and
  * the final ||b - K x|| / ||b|| on the free DOFs.
  */

@@ -1,7 +1,8 @@
 // Smoothed-aggregation AMG preconditioner: device V-cycle and Galerkin refresh.
 //
-// Level 0 is the live tangent K (FP64, masked to the free DOFs) with its
-// block-Jacobi inverse.  Levels >= 1 are single precision and, after every
+// Level 0 is the live tangent K (masked to the free DOFs) with its
+// block-Jacobi inverse, in FP32: a rounded copy for the FP64 path, the FP32
+// tangent itself for the mixed path.  Levels >= 1 are single precision and, after every
 // change of K, are rebuilt as Galerkin products A_{l+1} = R (A_l P) on the
 // device with the fixed patterns computed at setup, so the coarse spaces see
 // the plastic tangent's soft modes, not K_elast's.  Smoother: Chebyshev
@@ -423,7 +424,8 @@ static unsigned rows_grid(int64_t n_rows, int G) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-static Mat<float> mat0f(const BsrDev& A, const float* v) { return Mat<float>{A.n_rows, A.row_ptr, A.col_idx, v, A.free_dof}; }
+template <class T>
+static Mat<float> mat0f(const BsrT<T>& A, const float* v) { return Mat<float>{A.n_rows, A.row_ptr, A.col_idx, v, A.free_dof}; }
 
 template <class TI, class TO>
 __global__ void k_cvt(const TI* __restrict__ in, TO* __restrict__ out, int64_t n, const KrylovRec* rec) {
@@ -538,9 +540,6 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
     }
     D.nparts = 2 * (num_sms > 0 ? num_sms : 152);
     D.nnzb0 = H.nnzb0;
-    const int d0 = H.levels[0].bs;
-    if ((e = dvec(D, &D.K32, H.nnzb0 * d0 * d0)) != cudaSuccess) return e;
-    if ((e = dvec(D, &D.minv32, H.levels[0].n * d0)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.lam, AMG_MAX_LEVELS)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.coef, AMG_MAX_LEVELS * AMG_CHEB_DEGREE * 3)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw, 2)) != cudaSuccess) return e;
@@ -626,16 +625,14 @@ static cudaError_t rap_level(AmgDev& D, int l, const Mat<TA>& A, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s) {
+// Common part of the refresh: level 0 is (A0's pattern, D.K0, D.minv0).
+template <class T>
+static cudaError_t refresh_core(AmgDev& D, const BsrT<T>& A0, int galerkin, cudaStream_t s) {
     const int L = D.n_levels;
     const int d0 = A0.dim;
     const int64_t n0 = A0.n_rows * d0;
-    // FP32 copies of the live matrix and of its block-Jacobi inverse
-    k_cvt<double, float><<<cvt_grid(D.nnzb0 * d0 * d0), 256, 0, s>>>(A0.vals, D.K32, D.nnzb0 * d0 * d0, nullptr);
-    k_cvt<double, float><<<cvt_grid(n0 * d0), 256, 0, s>>>(minv0, D.minv32, n0 * d0, nullptr);
-    D.launches += 2;
-    const Mat<float> M0 = mat0f(A0, D.K32);
-    power<float>(D, d0, M0, D.minv32, D.pwf, D.pwf + n0, n0, A0.free_dof, D.lam + 0, s);
+    const Mat<float> M0 = mat0f(A0, D.K0);
+    power<float>(D, d0, M0, D.minv0, D.pwf, D.pwf + n0, n0, A0.free_dof, D.lam + 0, s);
     if (!galerkin || L < 2) {
         k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
         D.launches += 1;
@@ -683,6 +680,28 @@ cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int ga
     return cudaStreamSynchronize(s);
 }
 
+cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s) {
+    const int d0 = A0.dim;
+    const int64_t n0 = A0.n_rows * d0;
+    cudaError_t e;
+    if (!D.K32) {   // FP32 copies of the live matrix and of its block-Jacobi inverse, on first FP64 use
+        if ((e = dvec(D, &D.K32, D.nnzb0 * d0 * d0)) != cudaSuccess) return e;
+        if ((e = dvec(D, &D.minv32, n0 * d0)) != cudaSuccess) return e;
+    }
+    k_cvt<double, float><<<cvt_grid(D.nnzb0 * d0 * d0), 256, 0, s>>>(A0.vals, D.K32, D.nnzb0 * d0 * d0, nullptr);
+    k_cvt<double, float><<<cvt_grid(n0 * d0), 256, 0, s>>>(minv0, D.minv32, n0 * d0, nullptr);
+    D.launches += 2;
+    D.K0 = D.K32;
+    D.minv0 = D.minv32;
+    return refresh_core(D, A0, galerkin, s);
+}
+
+cudaError_t amg_refresh(AmgDev& D, const BsrF& A0, const float* minv0, int galerkin, cudaStream_t s) {
+    D.K0 = A0.vals;
+    D.minv0 = minv0;
+    return refresh_core(D, A0, galerkin, s);
+}
+
 // 1-level hierarchy: out = Ainv in, FP32 inverse applied to FP64 vectors
 __global__ void __launch_bounds__(AB) k_dense_d(const float* __restrict__ Ainv, int64_t n, const double* __restrict__ b,
                                                  double* __restrict__ x, const KrylovRec* rec) {
@@ -697,25 +716,21 @@ __global__ void __launch_bounds__(AB) k_dense_d(const float* __restrict__ Ainv, 
     if (lane == 0) x[warp] = s;
 }
 
-cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const double* in, double* out,
-                      const KrylovRec* rec, cudaStream_t s) {
+// The V-cycle on FP32 vectors: x0 = M^-1 b0 (b0 and x0 distinct; level-0 work vectors x2, d, r).
+template <class T>
+static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* x0, const KrylovRec* rec,
+                          cudaStream_t s) {
     const int L = D.n_levels;
     AmgDevLevel& l0 = D.lv[0];
-    if (L == 1) {
-        const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
-        k_dense_d<<<g, AB, 0, s>>>(l0.dense_inv, l0.n, in, out, rec);
-        D.launches += 1;
-        return cudaGetLastError();
-    }
-    const Mat<float> M0 = mat0f(A0, D.K32);
+    const Mat<float> M0 = mat0f(A0, D.K0);
     const int bs0 = A0.dim;
-    // level 0 in FP32 on the tangent's copy: pre-smoothing from zero, residual, restriction
-    k_cvt<double, float><<<cvt_grid(l0.n), 256, 0, s>>>(in, l0.b, l0.n, rec);
-    cheb<float>(bs0, M0, D.minv32, l0.b, nullptr, l0.x2, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 0, rec, s);
-    cheb<float>(bs0, M0, D.minv32, l0.b, l0.x2, l0.x, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 1, rec, s);
-    resid<float>(bs0, M0, l0.b, l0.x, l0.r, rec, s);
+    const float* cf0 = D.coef;
+    // level 0: pre-smoothing from zero, residual, restriction
+    cheb<float>(bs0, M0, D.minv0, b0, nullptr, l0.x2, l0.d, cf0, 0, rec, s);
+    cheb<float>(bs0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
+    resid<float>(bs0, M0, b0, x0, l0.r, rec, s);
     mv<float, float>(l0.R, l0.Rvals, l0.r, D.lv[1].b, 0, rec, s);
-    D.launches += 5;
+    D.launches += 4;
     // coarse levels (FP32), descending
     for (int l = 1; l < L - 1; ++l) {
         AmgDevLevel& v = D.lv[l];
@@ -741,12 +756,39 @@ cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const do
         cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
         D.launches += 3;
     }
-    mv<float, float>(l0.P, l0.Pvals, D.lv[1].x, l0.x, 1, rec, s);
-    cheb<float>(bs0, M0, D.minv32, l0.b, l0.x, l0.x2, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 0, rec, s);
-    cheb<float>(bs0, M0, D.minv32, l0.b, l0.x2, l0.x, l0.d, D.coef + (0) * AMG_CHEB_DEGREE * 3, 1, rec, s);
-    k_cvt<float, double><<<cvt_grid(l0.n), 256, 0, s>>>(l0.x, out, l0.n, rec);
-    D.launches += 4;
+    mv<float, float>(l0.P, l0.Pvals, D.lv[1].x, x0, 1, rec, s);
+    cheb<float>(bs0, M0, D.minv0, b0, x0, l0.x2, l0.d, cf0, 0, rec, s);
+    cheb<float>(bs0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
+    D.launches += 3;
     return cudaGetLastError();
+}
+
+cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* in, double* out, const KrylovRec* rec,
+                      cudaStream_t s) {
+    AmgDevLevel& l0 = D.lv[0];
+    if (D.n_levels == 1) {
+        const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
+        k_dense_d<<<g, AB, 0, s>>>(l0.dense_inv, l0.n, in, out, rec);
+        D.launches += 1;
+        return cudaGetLastError();
+    }
+    k_cvt<double, float><<<cvt_grid(l0.n), 256, 0, s>>>(in, l0.b, l0.n, rec);
+    cudaError_t e = vcycle(D, A0, l0.b, l0.x, rec, s);
+    k_cvt<float, double><<<cvt_grid(l0.n), 256, 0, s>>>(l0.x, out, l0.n, rec);
+    D.launches += 2;
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t amg_apply(AmgDev& D, const BsrF& A0, const float* in, float* out, const KrylovRec* rec,
+                      cudaStream_t s) {
+    AmgDevLevel& l0 = D.lv[0];
+    if (D.n_levels == 1) {
+        const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
+        k_dense<<<g, AB, 0, s>>>(l0.dense_inv, l0.n, in, out, rec);
+        D.launches += 1;
+        return cudaGetLastError();
+    }
+    return vcycle(D, A0, in, out, rec, s);
 }
 
 }  // namespace ep

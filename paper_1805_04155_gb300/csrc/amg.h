@@ -82,8 +82,10 @@ struct AmgDev {
     AmgDevLevel lv[AMG_MAX_LEVELS];
     double* lam = nullptr;             // device [AMG_MAX_LEVELS]: spectral radius estimates per level
     float* coef = nullptr;             // device [AMG_MAX_LEVELS][AMG_CHEB_DEGREE][3]: Chebyshev coefficients
-    float* K32 = nullptr;              // FP32 copy of the live level-0 matrix values [nnzb0][dim][dim]
-    float* minv32 = nullptr;           // FP32 copy of its block-Jacobi inverse [n_nodes][dim][dim]
+    float* K32 = nullptr;              // FP64 path: FP32 copy of the live level-0 matrix values [nnzb0][dim][dim]
+    float* minv32 = nullptr;           // FP64 path: FP32 copy of its block-Jacobi inverse [n_nodes][dim][dim]
+    const float* K0 = nullptr;         // level-0 values of the V-cycle (K32, or the mixed path's FP32 tangent)
+    const float* minv0 = nullptr;      // their block-Jacobi inverse
     int64_t nnzb0 = 0;
     double* pw = nullptr;              // power-iteration work [2][n0] (FP64)
     float* pwf = nullptr;              // power-iteration work [2][n1] (FP32)
@@ -97,11 +99,17 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms);
 void amg_free(AmgDev& D);
 // New level-0 matrix A0 (with block-Jacobi inverse minv0): spectral estimate of level 0 and, when
 // galerkin != 0, coarse operators R A P recomputed from A0 down the hierarchy (with their block
-// inverses, spectral estimates and the coarsest dense inverse).
+// inverses, spectral estimates and the coarsest dense inverse).  The FP64 overload first rounds A0
+// and minv0 to FP32 copies; the FP32 overload (mixed path) uses the given arrays, which must stay
+// valid until the next refresh.
 cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s);
-// One V-cycle: out = M^-1 in (level 0 uses A0 and minv0).
+cudaError_t amg_refresh(AmgDev& D, const BsrF& A0, const float* minv0, int galerkin, cudaStream_t s);
+// One V-cycle: out = M^-1 in (level 0 uses the operator of the last refresh; A0 gives its pattern
+// and free-DOF mask).
 // rec (may be null): the calling solver's record; every launch exits at once once rec->done is set.
-cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* minv0, const double* in, double* out,
-                      const KrylovRec* rec, cudaStream_t s);
+cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* in, double* out, const KrylovRec* rec,
+                      cudaStream_t s);
+cudaError_t amg_apply(AmgDev& D, const BsrF& A0, const float* in, float* out, const KrylovRec* rec,
+                      cudaStream_t s);
 
 }  // namespace ep

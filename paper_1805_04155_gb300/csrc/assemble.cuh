@@ -29,19 +29,25 @@ namespace ep {
 
 constexpr int ASM_THREADS = 256;
 
-template <int ID>
+template <int ID, class KT>
 struct AsmShape {
     using ET = Elem<ID>;
     static constexpr int D = ET::DIM, NP = ET::NP, NQ = ET::NQ, NS = ET::NS, NA = ET::NA, EPC = ET::EPC;
     static constexpr int NIP = EPC * NQ;
+    static constexpr bool F32 = sizeof(KT) == 4;
+    // FP64 region: displacements, gradients, weights, w*sigma
     static constexpr int OFF_U = 0;
     static constexpr int OFF_G = OFF_U + EPC * NP * D;
     static constexpr int OFF_W = OFF_G + NIP * NP * D;
-    static constexpr int OFF_D = OFF_W + NIP;
-    static constexpr int OFF_WS = OFF_D + NIP * NS * NS;
-    static constexpr int OFF_H = OFF_WS + NIP * NS;
-    static constexpr int N_DBL = OFF_H + NIP * NP * NS * D;
-    static constexpr size_t SMEM = sizeof(double) * N_DBL + sizeof(int) * (EPC * NP + EPC + NIP);
+    static constexpr int OFF_WS = OFF_W + NIP;
+    static constexpr int N_DBL = OFF_WS + NIP * NS;
+    // tangent region (KT): w*D, H, and an FP32 copy of the gradients when KT is float
+    static constexpr int OFF_D = 0;
+    static constexpr int OFF_H = OFF_D + NIP * NS * NS;
+    static constexpr int OFF_GK = OFF_H + NIP * NP * NS * D;
+    static constexpr int N_KT = OFF_GK + (F32 ? NIP * NP * D : 0);
+    static constexpr size_t BYTES_KT = (sizeof(KT) * N_KT + 7) / 8 * 8;
+    static constexpr size_t SMEM = sizeof(double) * N_DBL + BYTES_KT + sizeof(int) * (EPC * NP + EPC + NIP);
 };
 
 // Load the stored state of one point into active components.
@@ -91,22 +97,29 @@ __device__ __forceinline__ void strain_at(const double* __restrict__ g, const do
 }
 
 // ---------------------------------------------------------------------------
-template <int ID, int MODEL, bool DELTA, bool WANT_F>
+// KT is the value type of the tangent: double (the FP64 path) or float (the
+// mixed path: strains, return mapping and F stay FP64, and the FP64 tangent
+// coefficients are rounded once to FP32 before D, H and the K blocks are
+// formed and scattered with FP32 atomics).
+template <int ID, int MODEL, bool DELTA, bool WANT_F, class KT>
 __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
-    using S = AsmShape<ID>;
-    constexpr int D = S::D, NP = S::NP, NQ = S::NQ, NS = S::NS, NA = S::NA, EPC = S::EPC, NIP = S::NIP;
+    using S = AsmShape<ID, KT>;
+    constexpr int D = S::D, NP = S::NP, NQ = S::NQ, NS = S::NS, NA = S::NA, EPC = S::EPC;
     constexpr bool SYM = (MODEL != 3);
     constexpr int NB = SYM ? NP * (NP + 1) / 2 : NP * NP;
     extern __shared__ __align__(16) double smem[];
     double* s_u = smem + S::OFF_U;     // [EPC][NP][D]
     double* s_g = smem + S::OFF_G;     // [NIP][NP][D]
     double* s_w = smem + S::OFF_W;     // [NIP]
-    double* s_D = smem + S::OFF_D;     // [NIP][NS][NS]  (w * D)
     double* s_ws = smem + S::OFF_WS;   // [NIP][NS]      (w * sigma)
-    double* s_H = smem + S::OFF_H;     // [NIP][NP][NS][D]
-    int* s_node = reinterpret_cast<int*>(smem + S::N_DBL);   // [EPC][NP]
+    KT* s_kt = reinterpret_cast<KT*>(smem + S::N_DBL);
+    KT* s_D = s_kt + S::OFF_D;         // [NIP][NS][NS]  (w * D)
+    KT* s_H = s_kt + S::OFF_H;         // [NIP][NP][NS][D]
+    const KT* s_gk = S::F32 ? s_kt + S::OFF_GK : reinterpret_cast<const KT*>(s_g);   // gradients in KT
+    int* s_node = reinterpret_cast<int*>(reinterpret_cast<char*>(s_kt) + S::BYTES_KT);   // [EPC][NP]
     int* s_eplast = s_node + EPC * NP;                        // [EPC]
     int* s_ipflag = s_eplast + EPC;                           // [NIP]
+    KT* Kout = S::F32 ? reinterpret_cast<KT*>(a.Kvals32) : reinterpret_cast<KT*>(a.Kvals);
 
     const int tid = threadIdx.x;
     const int64_t n_elem = a.mesh.n_elem, n_int = a.mesh.n_int;
@@ -120,7 +133,11 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
     for (int i = tid; i < EPC; i += ASM_THREADS) s_eplast[i] = 0;
     {
         const double* src = a.mesh.dphi + ip0 * (NP * D);
-        for (int i = tid; i < nip * NP * D; i += ASM_THREADS) s_g[i] = src[i];
+        for (int i = tid; i < nip * NP * D; i += ASM_THREADS) {
+            const double g = src[i];
+            s_g[i] = g;
+            if (S::F32) const_cast<KT*>(s_gk)[i] = (KT)g;
+        }
         for (int i = tid; i < nip; i += ASM_THREADS) s_w[i] = a.mesh.wgt[ip0 + i];
     }
     __syncthreads();
@@ -160,12 +177,23 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
 #pragma unroll
             for (int r = 0; r < NS; ++r) s_ws[j * NS + r] = w * o.sig[row_active<NS>(r)];
         }
+        // split mode: an elastic point adds nothing (D - C = 0), its tangent is not formed
+        if (DELTA && !plastic) continue;
         if (DELTA) { o.cV -= a.mat.K; o.cD -= 2.0 * a.mat.G; }
+        if (S::F32) {
+            // the tangent from FP64 coefficients rounded once to FP32
+            PointTan<NA, KT> t;
+            tangent_coeffs(o, (KT)w, t);
 #pragma unroll
-        for (int r = 0; r < NS; ++r)
+            for (int r = 0; r < NS; ++r)
 #pragma unroll
-            for (int c = 0; c < NS; ++c)
-                s_D[(j * NS + r) * NS + c] = w * tangent_entry<NS, NA>(o, r, c);
+                for (int c = 0; c < NS; ++c) s_D[(j * NS + r) * NS + c] = tangent_entry_t<NS, NA>(t, r, c);
+        } else {
+#pragma unroll
+            for (int r = 0; r < NS; ++r)
+#pragma unroll
+                for (int c = 0; c < NS; ++c) s_D[(j * NS + r) * NS + c] = (KT)(w * tangent_entry<NS, NA>(o, r, c));
+        }
     }
     if (a.n_plastic) {
         // warp-aggregated count
@@ -177,32 +205,34 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
     __syncthreads();
 
     // (1b) H_p = (w D) G_p, one thread per (point, node)
-    for (int t = tid; t < nip * NP; t += ASM_THREADS) {
-        const int j = t / NP, p = t % NP;
-        double* H = s_H + (j * NP + p) * NS * D;
-        if (DELTA && !s_ipflag[j]) {
+    if (a.want_K) {
+        for (int t = tid; t < nip * NP; t += ASM_THREADS) {
+            const int j = t / NP, p = t % NP;
+            KT* H = s_H + (j * NP + p) * NS * D;
+            if (DELTA && !s_ipflag[j]) {
 #pragma unroll
-            for (int i = 0; i < NS * D; ++i) H[i] = 0.0;
-            continue;
-        }
-        const double* g = s_g + (j * NP + p) * D;
-        const double* Dm = s_D + j * NS * NS;
+                for (int i = 0; i < NS * D; ++i) H[i] = KT(0);
+                continue;
+            }
+            const KT* g = s_gk + (j * NP + p) * D;
+            const KT* Dm = s_D + j * NS * NS;
 #pragma unroll
-        for (int r = 0; r < NS; ++r) {
-            const double* dr = Dm + r * NS;
-            if (D == 2) {
-                H[r * 2 + 0] = dr[0] * g[0] + dr[2] * g[1];
-                H[r * 2 + 1] = dr[1] * g[1] + dr[2] * g[0];
-            } else {
-                H[r * 3 + 0] = dr[0] * g[0] + dr[3] * g[1] + dr[5] * g[2];
-                H[r * 3 + 1] = dr[1] * g[1] + dr[3] * g[0] + dr[4] * g[2];
-                H[r * 3 + 2] = dr[2] * g[2] + dr[4] * g[1] + dr[5] * g[0];
+            for (int r = 0; r < NS; ++r) {
+                const KT* dr = Dm + r * NS;
+                if (D == 2) {
+                    H[r * 2 + 0] = dr[0] * g[0] + dr[2] * g[1];
+                    H[r * 2 + 1] = dr[1] * g[1] + dr[2] * g[0];
+                } else {
+                    H[r * 3 + 0] = dr[0] * g[0] + dr[3] * g[1] + dr[5] * g[2];
+                    H[r * 3 + 1] = dr[1] * g[1] + dr[3] * g[0] + dr[4] * g[2];
+                    H[r * 3 + 2] = dr[2] * g[2] + dr[4] * g[1] + dr[5] * g[0];
+                }
             }
         }
     }
     __syncthreads();
 
-    // (2a) internal forces, one thread per (element, node)
+    // (2a) internal forces (FP64), one thread per (element, node)
     if (WANT_F) {
         for (int t = tid; t < ne * NP; t += ASM_THREADS) {
             const int e = t / NP, p = t % NP;
@@ -228,6 +258,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
             for (int c = 0; c < D; ++c) atomicAdd(a.F + node * D + c, f[c]);
         }
     }
+    if (!a.want_K) return;
 
     // (2b) element blocks K_pq, one thread per (element, node pair)
     for (int t = tid; t < ne * NB; t += ASM_THREADS) {
@@ -244,16 +275,16 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
             p = b / NP;
             q = b % NP;
         }
-        double k[D][D];
+        KT k[D][D];
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
-            for (int c = 0; c < D; ++c) k[r][c] = 0.0;
+            for (int c = 0; c < D; ++c) k[r][c] = KT(0);
 #pragma unroll
         for (int qq = 0; qq < NQ; ++qq) {
             const int j = e * NQ + qq;
-            const double* g = s_g + (j * NP + p) * D;
-            const double* H = s_H + (j * NP + q) * NS * D;
+            const KT* g = s_gk + (j * NP + p) * D;
+            const KT* H = s_H + (j * NP + q) * NS * D;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 if (D == 2) {
@@ -268,14 +299,14 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
         }
         const int64_t eg = e0 + e;
         const int64_t slot = a.mesh.slots[eg * (NP * NP) + p * NP + q];
-        double* dst = a.Kvals + slot * (D * D);
+        KT* dst = Kout + slot * (D * D);
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
             for (int c = 0; c < D; ++c) atomicAdd(dst + r * D + c, k[r][c]);
         if (SYM && p != q) {
             const int64_t slot2 = a.mesh.slots[eg * (NP * NP) + q * NP + p];
-            double* dst2 = a.Kvals + slot2 * (D * D);
+            KT* dst2 = Kout + slot2 * (D * D);
 #pragma unroll
             for (int r = 0; r < D; ++r)
 #pragma unroll
@@ -394,10 +425,10 @@ __global__ void __launch_bounds__(256) k_geometry(GeomArgs a) {
 // ---------------------------------------------------------------------------
 // Launchers for one element type.
 // ---------------------------------------------------------------------------
-template <int ID, int MODEL, bool DELTA, bool WANT_F>
+template <int ID, int MODEL, bool DELTA, bool WANT_F, class KT>
 cudaError_t launch_asm_t(const AsmArgs& a, cudaStream_t s) {
-    using S = AsmShape<ID>;
-    auto kern = k_assemble<ID, MODEL, DELTA, WANT_F>;
+    using S = AsmShape<ID, KT>;
+    auto kern = k_assemble<ID, MODEL, DELTA, WANT_F, KT>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -410,16 +441,28 @@ cudaError_t launch_asm_t(const AsmArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int ID>
-cudaError_t launch_assemble_elem(const AsmArgs& a, cudaStream_t s) {
-    if (a.elastic_only) return launch_asm_t<ID, 0, false, false>(a, s);
+template <int ID, int MODEL, class KT>
+cudaError_t launch_asm_model(const AsmArgs& a, cudaStream_t s) {
+    return a.mode == ASM_DELTA ? launch_asm_t<ID, MODEL, true, true, KT>(a, s)
+                               : launch_asm_t<ID, MODEL, false, true, KT>(a, s);
+}
+
+template <int ID, class KT>
+cudaError_t launch_assemble_kt(const AsmArgs& a, cudaStream_t s) {
     switch (a.mat.model) {
-        case 0: return a.mode == ASM_DELTA ? launch_asm_t<ID, 0, true, true>(a, s) : launch_asm_t<ID, 0, false, true>(a, s);
-        case 1: return a.mode == ASM_DELTA ? launch_asm_t<ID, 1, true, true>(a, s) : launch_asm_t<ID, 1, false, true>(a, s);
-        case 2: return a.mode == ASM_DELTA ? launch_asm_t<ID, 2, true, true>(a, s) : launch_asm_t<ID, 2, false, true>(a, s);
-        case 3: return a.mode == ASM_DELTA ? launch_asm_t<ID, 3, true, true>(a, s) : launch_asm_t<ID, 3, false, true>(a, s);
+        case 0: return launch_asm_model<ID, 0, KT>(a, s);
+        case 1: return launch_asm_model<ID, 1, KT>(a, s);
+        case 2: return launch_asm_model<ID, 2, KT>(a, s);
+        case 3: return launch_asm_model<ID, 3, KT>(a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int ID>
+cudaError_t launch_assemble_elem(const AsmArgs& a, cudaStream_t s) {
+    if (a.elastic_only) return launch_asm_t<ID, 0, false, false, double>(a, s);
+    if (a.Kvals32) return launch_assemble_kt<ID, float>(a, s);
+    return launch_assemble_kt<ID, double>(a, s);
 }
 
 template <int ID>

@@ -85,13 +85,14 @@ __device__ __forceinline__ void return_map(const MatConst& m, const PointIn<NA>&
         double sh = 0.0;
 #pragma unroll
         for (int a = 3; a < NA; ++a) sh += sd[a] * sd[a];
-        const double nrm = sqrt(dev_norm_sq_normal_shear(sd[0], sd[1], sd[2], sh));
+        // |s_tr| and 1/|s_tr| from one reciprocal square root (no FP64 division)
+        const double nsq = dev_norm_sq_normal_shear(sd[0], sd[1], sd[2], sh);
+        const double inv = nsq > 0.0 ? rsqrt(nsq) : 0.0;
+        const double nrm = nsq * inv;
         const double Yk = (MODEL == 1) ? m.Y : m.Y + m.H * in.alpha;
         const double crit = nrm - Yk;
         if (crit > 0.0) {
-            const double inv = 1.0 / nrm;
-            const double denom = 2.0 * G + m.H;
-            const double lam = crit / denom;
+            const double lam = crit * m.inv_vm;   // crit / (2G + H)
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 const double na = sd[a] * inv;
@@ -104,7 +105,7 @@ __device__ __forceinline__ void return_map(const MatConst& m, const PointIn<NA>&
             const double c4 = 4.0 * G * G;
             if (MODEL == 1) {
                 // C - c DEV + c (Y/|s|) (DEV - n(x)n),  c = 4G^2/(2G+a)
-                const double c = c4 / denom;
+                const double c = c4 * m.inv_vm;
                 const double cy = c * m.Y * inv;
                 out.cD = 2.0 * G - c + cy;
                 out.cN = -cy;
@@ -112,7 +113,7 @@ __device__ __forceinline__ void return_map(const MatConst& m, const PointIn<NA>&
                 // C - 4G^2/(2G+H) n(x)n - 4G^2 lam/|s| (DEV - n(x)n)
                 const double cl = c4 * lam * inv;
                 out.cD = 2.0 * G - cl;
-                out.cN = -c4 / denom + cl;
+                out.cN = -c4 * m.inv_vm + cl;
             }
             out.flag = 1;
         }
@@ -124,19 +125,21 @@ __device__ __forceinline__ void return_map(const MatConst& m, const PointIn<NA>&
     double sh = 0.0;
 #pragma unroll
     for (int a = 3; a < NA; ++a) sh += ed[a] * ed[a];
-    const double normE = sqrt(dev_norm_sq_normal_shear(ed[0], ed[1], ed[2], sh));
+    // |dev eps_tr| and its reciprocal from one reciprocal square root (no FP64 division)
+    const double nsq = dev_norm_sq_normal_shear(ed[0], ed[1], ed[2], sh);
+    const double inv = nsq > 0.0 ? rsqrt(nsq) : 0.0;
+    const double normE = nsq * inv;
     const double rho = 2.0 * G * normE;
     const double ck = m.c + m.Hc * in.alpha;
     const double denom_a = K * m.eta * m.eta_bar + m.Hc;
-    const double denom_s = G + denom_a;
     const double rs2 = 0.70710678118654752440;   // 1/sqrt(2)
     const double crit1 = rho * rs2 + m.eta * p_tr - ck;
-    const double crit2 = m.eta * p_tr - ck - denom_a * rho * rs2 / G;
+    // denom_a * rho / (sqrt(2) G) = sqrt(2) denom_a normE
+    const double crit2 = m.eta * p_tr - ck - denom_a * normE * 1.41421356237309504880;
     if (!(crit1 > 0.0)) return;
     if (!(crit2 > 0.0)) {
         // return to the smooth portion of the cone
-        const double lam = crit1 / denom_s;
-        const double inv = 1.0 / normE;
+        const double lam = crit1 * m.inv_den_s;   // crit1 / (G + K eta eta_bar + Hc)
         const double s2G = 1.41421356237309504880 * G;   // sqrt(2) G
         const double Kb = K * m.eta_bar;
 #pragma unroll
@@ -148,9 +151,9 @@ __device__ __forceinline__ void return_map(const MatConst& m, const PointIn<NA>&
             out.ep[a] += lam * (na * rs2 + (a < 3 ? m.eta_bar * (1.0 / 3.0) : 0.0)) * (a < 3 ? 1.0 : 2.0);
         }
         out.alpha += lam;
-        // C - c1 (DEV - n(x)n) - Mbar(x)M / denom_s,  c1 = 2 sqrt(2) G^2 lam / rho
-        const double c1 = 2.0 * s2G * G * lam / rho;
-        const double id = 1.0 / denom_s;
+        // C - c1 (DEV - n(x)n) - Mbar(x)M / denom_s,  c1 = 2 sqrt(2) G^2 lam / rho = sqrt(2) G lam / |dev eps_tr|
+        const double c1 = s2G * lam * inv;
+        const double id = m.inv_den_s;
         out.cV = K - K * K * m.eta * m.eta_bar * id;
         out.cD = 2.0 * G - c1;
         out.cN = c1 - 2.0 * G * G * id;
@@ -165,15 +168,15 @@ __device__ __forceinline__ void return_map(const MatConst& m, const PointIn<NA>&
         out.err = true;
         return;
     }
-    const double lam = (m.eta * p_tr - ck) / denom_a;
+    const double lam = (m.eta * p_tr - ck) * m.inv_den_a;
     const double p = p_tr - K * m.eta_bar * lam;
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         out.sig[a] = (a < 3) ? p : 0.0;
-        out.ep[a] = in.eps[a] - ((a < 3) ? p / (3.0 * K) : 0.0);
+        out.ep[a] = in.eps[a] - ((a < 3) ? p * m.inv_3K : 0.0);
     }
     out.alpha += lam;
-    out.cV = K * m.Hc / denom_a;
+    out.cV = K * m.Hc * m.inv_den_a;
     out.cD = 0.0;
 }
 
@@ -190,6 +193,36 @@ __device__ __forceinline__ double tangent_entry(const PointOut<NA>& o, int r, in
     if (ar < 3 && as < 3) dev = (ar == as ? 1.0 : 0.0) - 1.0 / 3.0;
     else if (ar == as) dev = 0.5;
     return o.cV * Ir * Is + o.cD * dev + o.cN * o.n[ar] * o.n[as] + o.cNI * o.n[ar] * Is + o.cIN * Ir * o.n[as];
+}
+
+// The tangent's coefficients, scaled by the point weight w, and the unit deviator,
+// rounded to precision T (the mixed path forms D, H and K in FP32 from these).
+template <int NA, class T>
+struct PointTan {
+    T cV, cD, cN, cNI, cIN;
+    T n[NA];
+};
+
+template <int NA, class T>
+__device__ __forceinline__ void tangent_coeffs(const PointOut<NA>& o, T w, PointTan<NA, T>& t) {
+    t.cV = w * (T)o.cV;
+    t.cD = w * (T)o.cD;
+    t.cN = w * (T)o.cN;
+    t.cNI = w * (T)o.cNI;
+    t.cIN = w * (T)o.cIN;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) t.n[a] = (T)o.n[a];
+}
+
+// w * D entry (row r, column s over the NS strain rows) from rounded coefficients.
+template <int NS, int NA, class T>
+__device__ __forceinline__ T tangent_entry_t(const PointTan<NA, T>& t, int r, int s) {
+    const int ar = row_active<NS>(r), as = row_active<NS>(s);
+    const T Ir = ar < 3 ? T(1) : T(0), Is = as < 3 ? T(1) : T(0);
+    T dev = T(0);
+    if (ar < 3 && as < 3) dev = (ar == as ? T(1) : T(0)) - T(1) / T(3);
+    else if (ar == as) dev = T(0.5);
+    return t.cV * Ir * Is + t.cD * dev + t.cN * t.n[ar] * t.n[as] + t.cNI * t.n[ar] * Is + t.cIN * Ir * t.n[as];
 }
 
 }  // namespace ep

@@ -127,8 +127,16 @@ bool make_matconst(const ep_material& m, int dim, MatConst& out, std::string& er
         }
         out.Hc = m.Hc;
     }
+    out.inv_vm = 1.0 / (2.0 * out.G + out.H);
+    const double den_a = out.K * out.eta * out.eta_bar + out.Hc;
+    out.inv_den_s = 1.0 / (out.G + den_a);
+    out.inv_den_a = den_a != 0.0 ? 1.0 / den_a : 0.0;
+    out.inv_3K = 1.0 / (3.0 * out.K);
     return true;
 }
+
+// Smallest relative tolerance asked of the FP32 inner Krylov solve of the mixed path.
+constexpr double MIXED_ETA_MIN = 1e-5;
 
 struct Ctx {
     std::string err;
@@ -143,6 +151,8 @@ struct Ctx {
     int32_t *elem = nullptr, *slots = nullptr, *row_ptr = nullptr, *col_idx = nullptr, *diag_slot = nullptr;
     double *dphi = nullptr, *wgt = nullptr;
     double *Kel = nullptr, *Kt = nullptr;
+    // mixed path (allocated on first use): FP32 tangent, FP32 K_elast, FP32 right-hand side
+    float *K32 = nullptr, *Kel32 = nullptr, *r32 = nullptr;
     // state
     double *ep = nullptr, *hard = nullptr, *sig = nullptr;
     uint8_t* flag = nullptr;
@@ -158,7 +168,8 @@ struct Ctx {
     unsigned long long* counter_host = nullptr;
     int* err_host = nullptr;
     KrylovWork kw{};
-    bool K_valid = false;
+    bool K_valid = false;      // Kt holds the tangent of the last assembly
+    bool K32_valid = false;    // K32 holds the tangent of the last assembly
     int n_committed = 0;
     double zeta_last = 0.0, zeta_prev = 0.0;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -210,8 +221,9 @@ static MeshDev mesh_dev(const Ctx* c) {
 
 static StateDev state_dev(const Ctx* c) { return StateDev{c->ep, c->hard, c->sig, c->flag}; }
 
-static BsrDev bsr_dev(const Ctx* c, const double* vals) {
-    BsrDev b;
+template <class T>
+static BsrT<T> bsr_dev(const Ctx* c, const T* vals) {
+    BsrT<T> b;
     b.n_rows = c->n_nodes;
     b.dim = c->dim;
     b.row_ptr = c->row_ptr;
@@ -222,15 +234,38 @@ static BsrDev bsr_dev(const Ctx* c, const double* vals) {
     return b;
 }
 
+// Buffers of the mixed path, on first use: K32, r32, the FP32 solver vectors, and K_elast rounded
+// once to FP32 (the split path's starting matrix).
+static ep_status ensure_mixed(Ctx* c) {
+    if (c->K32) return EP_OK;
+    const int64_t nk = c->nnzb * c->dim * c->dim;
+    CK(dalloc(c, &c->K32, nk));
+    CK(dalloc(c, &c->Kel32, nk));
+    CK(dalloc(c, &c->r32, c->n_dof));
+    CK(krylov_alloc_f32(c->kw, c->n_nodes, c->dim));
+    CK(vec_cvt_f32(c->Kel, c->Kel32, nk, c->stream));
+    c->launches += 1;
+    return EP_OK;
+}
+
 // Assemble F and K at u_dev with the committed state.  split: K = K_elast + plastic deltas.
-static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K) {
+// mixed: the tangent is formed in FP32 into K32 (F, strains and return mapping stay FP64).
+static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K, bool mixed) {
     cudaStream_t s = c->stream;
     CK(cudaMemsetAsync(c->F, 0, sizeof(double) * c->n_dof, s));
     CK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
-    const size_t kbytes = sizeof(double) * (size_t)c->nnzb * c->dim * c->dim;
-    if (want_K) {
-        if (split) CK(cudaMemcpyAsync(c->Kt, c->Kel, kbytes, cudaMemcpyDeviceToDevice, s));
-        else CK(cudaMemsetAsync(c->Kt, 0, kbytes, s));
+    if (mixed) {
+        ep_status st = ensure_mixed(c);
+        if (st != EP_OK) return st;
+    }
+    const size_t nk = (size_t)c->nnzb * c->dim * c->dim;
+    if (want_K && !mixed) {
+        if (split) CK(cudaMemcpyAsync(c->Kt, c->Kel, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+        else CK(cudaMemsetAsync(c->Kt, 0, sizeof(double) * nk, s));
+    }
+    if (want_K && mixed) {
+        if (split) CK(cudaMemcpyAsync(c->K32, c->Kel32, sizeof(float) * nk, cudaMemcpyDeviceToDevice, s));
+        else CK(cudaMemsetAsync(c->K32, 0, sizeof(float) * nk, s));
     }
     AsmArgs a{};
     a.mesh = mesh_dev(c);
@@ -239,6 +274,7 @@ static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K) 
     a.u = u_dev;
     a.F = c->F;
     a.Kvals = c->Kt;
+    a.Kvals32 = mixed ? c->K32 : nullptr;
     a.mode = split ? ASM_DELTA : ASM_FULL;
     a.want_K = want_K ? 1 : 0;
     a.elastic_only = 0;
@@ -248,7 +284,8 @@ static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K) 
     CK(launch_assemble(c->eid, a, s));
     if (c->profile) CK(cudaEventRecord(c->ev[5], s));
     c->launches += 1;
-    c->K_valid = want_K;
+    c->K_valid = want_K && !mixed;
+    c->K32_valid = want_K && mixed;
     return EP_OK;
 }
 
@@ -580,7 +617,10 @@ static ep_status field_ptr(Ctx* c, int32_t field, void** p, size_t* bytes, bool 
         case EP_K_ELASTIC: *p = c->Kel; *bytes = sizeof(double) * c->nnzb * d2; return EP_OK;
         case EP_WEIGHT: *p = c->wgt; *bytes = sizeof(double) * c->n_int; return EP_OK;
         case EP_DPHI: *p = c->dphi; *bytes = sizeof(double) * c->n_int * c->n_p * c->dim; return EP_OK;
-        case EP_SOLUTION: *p = c->kw.x; *bytes = sizeof(double) * c->n_dof; return EP_OK;
+        case EP_SOLUTION: *p = c->kw.d.x; *bytes = sizeof(double) * c->n_dof; return EP_OK;
+        case EP_K_VALUES_F32:
+            if (!c->K32) return EP_ERR_STATE;
+            *p = c->K32; *bytes = sizeof(float) * c->nnzb * d2; return EP_OK;
     }
     return EP_ERR_INVALID_ARG;
 }
@@ -590,9 +630,11 @@ ep_status ep_get(void* ctx, int32_t field, void* dst, size_t bytes, int32_t dst_
     Ctx* c = static_cast<Ctx*>(ctx);
     void* src = nullptr;
     size_t want = 0;
-    if (field_ptr(c, field, &src, &want, false) != EP_OK) {
-        c->err = "ep_get: unknown field";
-        return EP_ERR_INVALID_ARG;
+    const ep_status fs = field_ptr(c, field, &src, &want, false);
+    if (fs != EP_OK) {
+        c->err = fs == EP_ERR_STATE ? "ep_get: the field does not exist yet (no mixed-precision assembly)"
+                                    : "ep_get: unknown field";
+        return fs;
     }
     if (bytes != want) {
         c->err = "ep_get: size mismatch (expected " + std::to_string(want) + " bytes)";
@@ -630,14 +672,15 @@ static ep_status load_u(Ctx* c, const double* u, int32_t u_is_device) {
     return EP_OK;
 }
 
-ep_status ep_assemble(void* ctx, const double* u, int32_t u_is_device, int32_t split, int64_t* n_plastic) {
-    if (!ctx || !u) return EP_ERR_INVALID_ARG;
+ep_status ep_assemble_prec(void* ctx, const double* u, int32_t u_is_device, int32_t split, int32_t precision,
+                           int64_t* n_plastic) {
+    if (!ctx || !u || (precision != EP_FP64 && precision != EP_MIXED)) return EP_ERR_INVALID_ARG;
     Ctx* c = static_cast<Ctx*>(ctx);
     cudaSetDevice(c->device);
     ep_status st = load_u(c, u, u_is_device);
     if (st != EP_OK) return st;
     CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
-    st = assemble(c, c->u_it, split != 0, true);
+    st = assemble(c, c->u_it, split != 0, true, precision == EP_MIXED);
     if (st != EP_OK) return st;
     unsigned long long np = 0;
     bool rm_err = false;
@@ -649,6 +692,10 @@ ep_status ep_assemble(void* ctx, const double* u, int32_t u_is_device, int32_t s
         return EP_ERR_RETURN_MAP;
     }
     return EP_OK;
+}
+
+ep_status ep_assemble(void* ctx, const double* u, int32_t u_is_device, int32_t split, int64_t* n_plastic) {
+    return ep_assemble_prec(ctx, u, u_is_device, split, EP_FP64, n_plastic);
 }
 
 ep_status ep_commit(void* ctx, const double* u, int32_t u_is_device) {
@@ -670,8 +717,11 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
                           double* rel_resid) {
     if (!ctx || !b || !opts) return EP_ERR_INVALID_ARG;
     Ctx* c = static_cast<Ctx*>(ctx);
-    if (!c->K_valid) {
-        c->err = "ep_linear_solve: no assembled matrix (call ep_assemble first)";
+    const bool mixed = opts->precision == EP_MIXED;
+    if (opts->precision != EP_FP64 && !mixed) return EP_ERR_INVALID_ARG;
+    if (mixed ? !c->K32_valid : !c->K_valid) {
+        c->err = mixed ? "ep_linear_solve: no FP32 matrix (call ep_assemble_prec with EP_MIXED first)"
+                       : "ep_linear_solve: no assembled matrix (call ep_assemble first)";
         return EP_ERR_STATE;
     }
     if (!(opts->krylov_rtol > 0.0) || opts->krylov_maxit <= 0) {
@@ -685,14 +735,24 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
     }
     CK(cudaMemcpyAsync(c->r, b, sizeof(double) * c->n_dof, b_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->stream));
-    const BsrDev A = bsr_dev(c, c->Kt);
     c->kw.galerkin = 1;
     c->amg_elastic = false;
-    CK(krylov_precond(A, c->kw, opts->precond, c->stream));
     int its = 0, status = 0;
     double rel = 0.0;
-    CK(krylov_solve(A, c->kw, c->r, krylov_method(c, *opts), opts->krylov_rtol, opts->krylov_maxit, c->stream, &its, &rel,
-                    &status));
+    if (mixed) {
+        const BsrF A = bsr_dev(c, (const float*)c->K32);
+        CK(vec_cvt_f32(c->r, c->r32, c->n_dof, c->stream));
+        CK(krylov_precond(A, c->kw, opts->precond, c->stream));
+        CK(krylov_solve(A, c->kw, c->r32, krylov_method(c, *opts), opts->krylov_rtol, opts->krylov_maxit, c->stream,
+                        &its, &rel, &status));
+        CK(vec_cvt_f64(c->kw.f.x, c->kw.d.x, c->n_dof, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        const BsrDev A = bsr_dev(c, (const double*)c->Kt);
+        CK(krylov_precond(A, c->kw, opts->precond, c->stream));
+        CK(krylov_solve(A, c->kw, c->r, krylov_method(c, *opts), opts->krylov_rtol, opts->krylov_maxit, c->stream,
+                        &its, &rel, &status));
+    }
     if (iterations) *iterations = its;
     if (rel_resid) *rel_resid = rel;
     if (status != EP_OK) c->err = "Krylov: no convergence within the iteration cap, or breakdown";
@@ -706,10 +766,11 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     ep_opts o;
     if (opts) o = *opts;
     else ep_default_opts(&o);
-    if (o.precision != EP_FP64) {
-        c->err = "only EP_FP64 is available";
+    if (o.precision != EP_FP64 && o.precision != EP_MIXED) {
+        c->err = "precision must be EP_FP64 or EP_MIXED";
         return EP_ERR_INVALID_ARG;
     }
+    const bool mixed = o.precision == EP_MIXED;
     if (!(o.newton_rtol > 0.0) || o.newton_maxit < 1 || o.krylov_maxit < 1) return EP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
@@ -719,7 +780,12 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     }
     const int method = krylov_method(c, o);
     const bool split = o.split_elastic_cache != 0;
-    const BsrDev A = bsr_dev(c, c->Kt);
+    const BsrDev A = bsr_dev(c, (const double*)c->Kt);
+    if (mixed) {
+        ep_status st = ensure_mixed(c);
+        if (st != EP_OK) return st;
+    }
+    const BsrF Af = bsr_dev(c, (const float*)c->K32);
     c->profile = o.profile;
     c->kw.profile = o.profile;
     for (int k = 0; k < n_steps; ++k) {
@@ -749,10 +815,11 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         bool converged = false;
         for (;;) {
             CK(cudaEventRecord(c->ev[0], s));
-            st = assemble(c, c->u_it, split, true);
+            st = assemble(c, c->u_it, split, true, mixed);
             if (st != EP_OK) break;
             CK(cudaEventRecord(c->ev[1], s));
-            CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, c->n_dof, c->kw.part, c->kw.nparts, c->norms, s));
+            CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, mixed ? c->r32 : nullptr, c->n_dof, c->kw.part,
+                            c->kw.nparts, c->norms, s));
             c->launches += 2;
             rep.n_assemble += 1;
             CK(cudaMemcpyAsync(c->norms_host, c->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -798,19 +865,26 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 eta = std::min(1e-2, std::max(eta_ew, eta_min));
                 eta = std::max(eta, 1e-14);
             }
+            // an FP32 inner solve cannot go much below FP32 rounding; Newton (FP64 residual) refines further
+            if (mixed) eta = std::max(eta, MIXED_ETA_MIN);
             rnorm_prev = rnorm;
             CK(cudaEventRecord(c->ev[2], s));
             // coarse operators from the current tangent unless it is exactly K_elast
             const bool tangent_elastic = split && *c->counter_host == 0;
             c->kw.galerkin = (tangent_elastic && c->amg_elastic) ? 0 : 1;
             if (c->kw.galerkin) c->amg_elastic = tangent_elastic;
-            CK(krylov_precond(A, c->kw, o.precond, s));
             int kits = 0, kst = 0;
             double krel = 0.0;
             // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
             // nonassociated model
             const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
-            CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+            if (mixed) {
+                CK(krylov_precond(Af, c->kw, o.precond, s));
+                CK(krylov_solve(Af, c->kw, c->r32, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+            } else {
+                CK(krylov_precond(A, c->kw, o.precond, s));
+                CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+            }
             CK(cudaEventRecord(c->ev[3], s));
             rep.krylov_its += kits;
             if (c->verbose)
@@ -836,7 +910,8 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 c->err = "Krylov: no progress (relative residual " + std::to_string(krel) + ")";
                 break;
             }
-            CK(vec_axpy(c->u_it, 1.0, c->kw.x, c->n_dof, s));
+            if (mixed) CK(vec_axpy_f32(c->u_it, c->kw.f.x, c->n_dof, s));
+            else CK(vec_axpy(c->u_it, 1.0, c->kw.d.x, c->n_dof, s));
             c->launches += 1;
             CK(cudaEventSynchronize(c->ev[3]));
             CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));

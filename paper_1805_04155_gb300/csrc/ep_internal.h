@@ -47,6 +47,11 @@ struct MatConst {
     double K, G;        // bulk and shear moduli
     double Y, H;        // von Mises yield value and hardening modulus
     double eta, c, eta_bar, Hc;   // Drucker-Prager
+    // reciprocals computed once on the host (FP64 divisions are costly on the device)
+    double inv_vm;      // 1 / (2G + H)
+    double inv_den_s;   // 1 / (G + K eta eta_bar + Hc)
+    double inv_den_a;   // 1 / (K eta eta_bar + Hc), 0 when that is 0
+    double inv_3K;      // 1 / (3K)
 };
 
 // ---------------------------------------------------------------------------
@@ -77,6 +82,7 @@ struct AsmArgs {
     const double* u;           // [n_dof]
     double* F;                 // [n_dof], accumulated (caller zeroes)
     double* Kvals;             // [nnzb][dim][dim], accumulated (caller initialises)
+    float* Kvals32;            // non-null: the tangent is formed in FP32 and accumulated here instead of Kvals
     int mode;                  // AsmMode
     int want_K;                // 0: F only
     int elastic_only;          // 1: D = C everywhere (K_elast assembly), u/state ignored
@@ -127,15 +133,18 @@ bool build_pattern(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem
 // ---------------------------------------------------------------------------
 // Krylov solver on the block-CSR matrix (krylov.cu).
 // ---------------------------------------------------------------------------
-struct BsrDev {
+template <class T>
+struct BsrT {
     int64_t n_rows;            // node rows
     int dim;
     const int32_t* row_ptr;
     const int32_t* col_idx;
     const int32_t* diag_slot;  // [n_rows] block index of the diagonal block
-    const double* vals;        // [nnzb][dim][dim]
+    const T* vals;             // [nnzb][dim][dim]
     const uint8_t* free_dof;   // [n_rows*dim], 1 = free
 };
+using BsrDev = BsrT<double>;   // the FP64 tangent
+using BsrF = BsrT<float>;      // the FP32 tangent of the mixed path
 
 // Per-solve scalar record, written by the device, read by the host.
 struct KrylovRec {
@@ -150,14 +159,22 @@ struct KrylovRec {
 
 struct AmgDev;
 
+// Solver vectors of one precision.
+template <class T>
+struct KVecs {
+    T *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rhat = nullptr, *v = nullptr,
+      *s = nullptr, *t = nullptr, *phat = nullptr, *shat = nullptr;
+    T* minv = nullptr;       // preconditioner: [n_rows][dim][dim]
+    T* V = nullptr;          // GMRES basis [GM_M + 1][n]
+};
+
 struct KrylovWork {
     int64_t n;               // vector length (n_rows*dim)
     int nparts;              // partial-sum slots per reduction
     int grid, block;         // launch shape of the vector/SpMV kernels
-    double *x, *r, *z, *p, *q, *rhat, *v, *s, *t, *phat, *shat;
-    double* minv;            // preconditioner: [n_rows][dim][dim]
+    KVecs<double> d;         // FP64 solver (allocated by krylov_alloc)
+    KVecs<float> f;          // FP32 solver of the mixed path (allocated by krylov_alloc_f32 on first use)
     double* part;            // [max(8, GM_M + 2)][nparts] partial sums
-    double* V;               // GMRES basis [GM_M + 1][n]
     double* gm;              // GMRES small arrays: H [(GM_M+1) x GM_M], cs, sn, g [GM_M+1]
     double* hist;            // [3][maxit+2] rho, alpha, omega per iteration
     int hist_len;
@@ -177,16 +194,26 @@ struct KrylovWork {
 
 constexpr int GM_M = 128;    // largest GMRES restart length (buffers); the run-time length is KrylovWork::gm_m
 cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms);
+cudaError_t krylov_alloc_f32(KrylovWork& w, int64_t n_rows, int dim);
 void krylov_free(KrylovWork& w);
+// Preconditioner of A (kind 0 Jacobi, 1 block Jacobi, 2 AMG with block-Jacobi smoothing) in A's precision.
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s);
-// Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab, 3 GMRES(GM_M).
+cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t s);
+// Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab, 3 GMRES(m).
+// The FP64 overload works on w.d, the FP32 overload on w.f (solution in w.f.x).
 // Returns cudaSuccess; *status receives EP_OK / EP_ERR_KRYLOV / EP_ERR_NAN.
 cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
                          cudaStream_t s, int* its, double* relres, int* status);
+cudaError_t krylov_solve(const BsrF& A, KrylovWork& w, const float* b, int method, double rtol, int maxit,
+                         cudaStream_t s, int* its, double* relres, int* status);
 
 // Small vector kernels (krylov.cu).
+// r = (zeta f_unit - F) on the free DOFs (and its FP32 copy r32 when non-null); out3 = (||r||^2, ||f||^2, ||F||^2).
 cudaError_t vec_residual(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof, double* r,
-                         int64_t n, double* part, int nparts, double* out3, cudaStream_t s);
+                         float* r32, int64_t n, double* part, int nparts, double* out3, cudaStream_t s);
+cudaError_t vec_axpy_f32(double* y, const float* x, int64_t n, cudaStream_t s);   // y += x
+cudaError_t vec_cvt_f32(const double* x, float* y, int64_t n, cudaStream_t s);    // y = (float) x
+cudaError_t vec_cvt_f64(const float* x, double* y, int64_t n, cudaStream_t s);    // y = (double) x
 cudaError_t vec_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);
 cudaError_t vec_set_dirichlet(double* u, const double* uD_unit, double zeta, const uint8_t* free_dof, int64_t n,
                               cudaStream_t s);

@@ -4,16 +4,23 @@
 //
 // The paper solves this system with MATLAB's sparse direct solver; here it is
 // a hand-written PCG (symmetric tangents: elastic, von Mises, associated
-// Drucker-Prager) or BiCGStab (nonassociated Drucker-Prager), preconditioned
-// by point Jacobi or by the inverse dim x dim diagonal node blocks.
+// Drucker-Prager), BiCGStab or right-preconditioned GMRES(m) (nonassociated
+// Drucker-Prager), preconditioned by point Jacobi, by the inverse dim x dim
+// diagonal node blocks, or by the AMG V-cycle of amg.cu.
 //
-// Every reduction is deterministic: each CTA writes one partial sum, and
-// every consumer CTA re-reduces all partials in the same fixed order, so all
-// CTAs (and all runs) agree bit for bit and no extra finalising launch is
-// needed.  Iteration scalars (rho, alpha, omega) are kept per iteration in a
-// device array so that no kernel reads a value another CTA of the same launch
-// may be writing.  Kernels exit at once when the device record says the solve
-// has finished, so the host may enqueue iterations in chunks and poll rarely.
+// Every solver is templated on the vector type T: double for the FP64 path,
+// float for the inner solve of the mixed path (the Newton residual, computed
+// in FP64 by the assembly, is the outer refinement).  Scalars (rho, alpha,
+// omega, the GMRES Hessenberg matrix and rotations) are FP64 in both.
+//
+// Every reduction is deterministic: each CTA writes one partial sum (warp sums
+// in T, the CTA's warp partials in FP64), and every consumer CTA re-reduces
+// all partials in the same fixed order, so all CTAs (and all runs) agree bit
+// for bit and no extra finalising launch is needed.  Iteration scalars are
+// kept per iteration in a device array so that no kernel reads a value another
+// CTA of the same launch may be writing.  Kernels exit at once when the device
+// record says the solve has finished, so the host may enqueue iterations in
+// chunks and poll rarely.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -26,18 +33,20 @@ namespace ep {
 constexpr int VB = 512;   // threads per CTA of vector and SpMV kernels
 enum { P_RZ = 0, P_RR = 1, P_PQ = 2, P_TS = 3, P_TT = 4, P_N = 8 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
 
-// Sum over the CTA; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// Sum over the CTA (warp sums in T, then the warps' partials in FP64); result valid in thread 0.
+template <class T>
+__device__ __forceinline__ double block_sum(T v, double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     v = warp_sum(v);
     __syncthreads();
-    if (lane == 0) sh[wid] = v;
+    if (lane == 0) sh[wid] = (double)v;
     __syncthreads();
     double r = 0.0;
     if (wid == 0) {
@@ -62,13 +71,20 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
     return r;
 }
 
+// Broadcast a scalar computed by thread 0 (one division per CTA, not per thread).
+#define EP_CTA_SCALAR(name, expr)                 \
+    __shared__ double s_##name;                   \
+    if (threadIdx.x == 0) s_##name = (expr);      \
+    __syncthreads();                              \
+    const double name = s_##name;
+
 // ---------------------------------------------------------------------------
 // y = P A x (P = free-DOF mask), optional partial of dot(dv, y).
 // G lanes share one block row; lanes read consecutive blocks (coalesced).
 // ---------------------------------------------------------------------------
-template <int D, int G>
-__global__ void __launch_bounds__(VB) k_spmv(BsrDev A, const double* __restrict__ x, double* __restrict__ y,
-                                              const double* __restrict__ dv, double* part, const KrylovRec* rec) {
+template <int D, int G, class T>
+__global__ void __launch_bounds__(VB) k_spmv(BsrT<T> A, const T* __restrict__ x, T* __restrict__ y,
+                                              const T* __restrict__ dv, double* part, const KrylovRec* rec) {
     __shared__ double sh[32];
     if (rec && rec->done) return;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,24 +93,32 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrDev A, const double* __restrict_
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int GPW = 32 / G;
     const int lg = lane % G;
-    double dot = 0.0;
+    T dot = T(0);
     for (int64_t rbase = warp * GPW; rbase < A.n_rows; rbase += nwarps * GPW) {
         const int64_t row = rbase + lane / G;
-        double acc[D];
+        T acc[D];
 #pragma unroll
-        for (int r = 0; r < D; ++r) acc[r] = 0.0;
+        for (int r = 0; r < D; ++r) acc[r] = T(0);
         if (row < A.n_rows) {
             const int beg = A.row_ptr[row], end = A.row_ptr[row + 1];
             for (int k = beg + lg; k < end; k += G) {
                 const int64_t col = A.col_idx[k];
-                const double* blk = A.vals + (int64_t)k * (D * D);
-                double xc[D];
+                const T* blk = A.vals + (int64_t)k * (D * D);
+                T bv[D * D];
+                if constexpr (D == 2 && sizeof(T) == 4) {   // one 16-byte load per 2x2 FP32 block
+                    const float4 v = *reinterpret_cast<const float4*>(blk);
+                    bv[0] = v.x; bv[1] = v.y; bv[2] = v.z; bv[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < D * D; ++e) bv[e] = blk[e];
+                }
+                T xc[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) xc[c] = x[col * D + c];
 #pragma unroll
                 for (int r = 0; r < D; ++r)
 #pragma unroll
-                    for (int c = 0; c < D; ++c) acc[r] += blk[r * D + c] * xc[c];
+                    for (int c = 0; c < D; ++c) acc[r] += bv[r * D + c] * xc[c];
             }
         }
 #pragma unroll
@@ -105,7 +129,7 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrDev A, const double* __restrict_
 #pragma unroll
             for (int r = 0; r < D; ++r) {
                 const int64_t dof = row * D + r;
-                const double val = A.free_dof[dof] ? acc[r] : 0.0;
+                const T val = A.free_dof[dof] ? acc[r] : T(0);
                 y[dof] = val;
                 if (dv) dot += dv[dof] * val;
             }
@@ -118,16 +142,16 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrDev A, const double* __restrict_
 }
 
 // z = M^-1 r for one node block (minv row-major [D][D])
-template <int D>
-__device__ __forceinline__ void apply_minv(const double* __restrict__ minv, const double* __restrict__ r,
-                                           double* __restrict__ z, int64_t node) {
-    const double* m = minv + node * (D * D);
-    double rv[D];
+template <int D, class T>
+__device__ __forceinline__ void apply_minv(const T* __restrict__ minv, const T* __restrict__ r, T* __restrict__ z,
+                                           int64_t node) {
+    const T* m = minv + node * (D * D);
+    T rv[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) rv[c] = r[node * D + c];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int c = 0; c < D; ++c) s += m[i * D + c] * rv[c];
         z[node * D + i] = s;
@@ -138,12 +162,12 @@ __device__ __forceinline__ void apply_minv(const double* __restrict__ minv, cons
 // Preconditioner: kind 0 point Jacobi, 1 block Jacobi.  Prescribed DOFs get
 // identity rows/columns.  A zero or non-finite pivot also gets identity.
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void k_precond(BsrDev A, double* minv, int kind) {
+template <int D, class T>
+__global__ void k_precond(BsrT<T> A, T* minv, int kind) {
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= A.n_rows) return;
-    const double* blk = A.vals + (int64_t)A.diag_slot[node] * (D * D);
-    double m[D][D];
+    const T* blk = A.vals + (int64_t)A.diag_slot[node] * (D * D);
+    T m[D][D];
     bool fr[D];
 #pragma unroll
     for (int r = 0; r < D; ++r) fr[r] = A.free_dof[node * D + r] != 0;
@@ -151,23 +175,23 @@ __global__ void k_precond(BsrDev A, double* minv, int kind) {
     for (int r = 0; r < D; ++r)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            double v = blk[r * D + c];
-            if (!fr[r] || !fr[c] || (kind == 0 && r != c)) v = (r == c) ? 1.0 : 0.0;
+            T v = blk[r * D + c];
+            if (!fr[r] || !fr[c] || (kind == 0 && r != c)) v = (r == c) ? T(1) : T(0);
             m[r][c] = v;
         }
-    double inv[D][D];
-    double det;
+    T inv[D][D];
+    T det;
     if (D == 2) {
         det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
-        const double id = 1.0 / det;
+        const T id = T(1) / det;
         inv[0][0] = m[1][1] * id;  inv[0][1] = -m[0][1] * id;
         inv[1][0] = -m[1][0] * id; inv[1][1] = m[0][0] * id;
     } else {
-        const double c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
-        const double c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2];
-        const double c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+        const T c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+        const T c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+        const T c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
         det = m[0][0] * c00 + m[0][1] * c01 + m[0][2] * c02;
-        const double id = 1.0 / det;
+        const T id = T(1) / det;
         inv[0][0] = c00 * id;
         inv[0][1] = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) * id;
         inv[0][2] = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) * id;
@@ -178,22 +202,23 @@ __global__ void k_precond(BsrDev A, double* minv, int kind) {
         inv[2][1] = (m[0][1] * m[2][0] - m[0][0] * m[2][1]) * id;
         inv[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) * id;
     }
-    const bool ok = isfinite(det) && det != 0.0;
-    double* out = minv + node * (D * D);
+    const bool ok = isfinite(det) && det != T(0);
+    T* out = minv + node * (D * D);
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-        for (int c = 0; c < D; ++c) out[r * D + c] = ok ? inv[r][c] : (r == c ? 1.0 : 0.0);
+        for (int c = 0; c < D; ++c) out[r * D + c] = ok ? inv[r][c] : (r == c ? T(1) : T(0));
 }
 
 // ---------------------------------------------------------------------------
-// Solver kernels.  `it` is the iteration index supplied by the host.
+// CG and BiCGStab kernels.  `it` is the iteration index supplied by the host.
 // ---------------------------------------------------------------------------
+template <class T>
 struct KArgs {
     int64_t n_rows;
     const uint8_t* free_dof;
-    const double* minv;
-    double *x, *r, *z, *p, *q, *rhat, *v, *s, *t, *phat, *shat;
+    const T* minv;
+    T *x, *r, *z, *p, *q, *rhat, *v, *s, *t, *phat, *shat;
     double* part;       // [P_N][nparts]
     int nparts;
     double* h_rho;      // [hist_len]
@@ -223,21 +248,21 @@ __device__ __forceinline__ double shadow_value(int64_t i, int seed) {
 // init: r = P (b - A x) (warm) or x = 0, r = P b (cold); z = M^-1 r (CG) or
 // rhat = shadow, p = v = 0 (BiCGStab); partials (rhat or z).r and r.r.
 // For the warm start q must hold A x.
-template <int D>
-__global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__ b, int bicg, int warm, int seed) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_init(KArgs<T> a, const T* __restrict__ b, int bicg, int warm, int seed) {
     __shared__ double sh[32];
-    double s1 = 0.0, s2 = 0.0;
+    T s1 = T(0), s2 = T(0);
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
             const bool fr = a.free_dof[i] != 0;
-            const double ri = fr ? (warm ? b[i] - a.q[i] : b[i]) : 0.0;
+            const T ri = fr ? (warm ? b[i] - a.q[i] : b[i]) : T(0);
             a.r[i] = ri;
-            if (!warm) a.x[i] = 0.0;
-            a.p[i] = 0.0;
-            if (bicg) { a.rhat[i] = fr ? shadow_value(i, seed) : 0.0; a.v[i] = 0.0; }
+            if (!warm) a.x[i] = T(0);
+            a.p[i] = T(0);
+            if (bicg) { a.rhat[i] = fr ? (T)shadow_value(i, seed) : T(0); a.v[i] = T(0); }
         }
         if (!bicg && !a.amg) apply_minv<D>(a.minv, a.r, a.z, node);
 #pragma unroll
@@ -258,7 +283,8 @@ __global__ void __launch_bounds__(VB) k_init(KArgs a, const double* __restrict__
 }
 
 // Convergence test at the start of iteration `it`; returns true if the CTA must stop.
-__device__ __forceinline__ bool check_done(const KArgs& a, int it, double rz, double rr, double* sh) {
+template <class T>
+__device__ __forceinline__ bool check_done(const KArgs<T>& a, int it, double rz, double rr) {
     const bool first = (it == 0 && a.cold);
     const double rr0 = first ? rr : a.rec->rr0;
     int done = 0, why = 0;
@@ -272,47 +298,41 @@ __device__ __forceinline__ bool check_done(const KArgs& a, int it, double rz, do
         a.rec->its = it;
         if (done) { a.rec->done = done; a.rec->why = why; }
     }
-    (void)sh;
     return done != 0;
 }
 
 // CG: p = z + beta p
-template <int D>
-__global__ void __launch_bounds__(VB) k_cg_p(KArgs a, int it) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_cg_p(KArgs<T> a, int it) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double rz = sum_partials(PART(P_RZ), a.nparts, sh);
     const double rr = sum_partials(PART(P_RR), a.nparts, sh);
-    if (check_done(a, it, rz, rr, sh)) return;
-    // FP64 divisions are costly on this GPU: one per CTA, broadcast through shared memory
-    __shared__ double s_beta;
-    if (threadIdx.x == 0) s_beta = (it == 0) ? 0.0 : rz / a.h_rho[it - 1];
-    __syncthreads();
-    const double beta = s_beta;
+    if (check_done(a, it, rz, rr)) return;
+    EP_CTA_SCALAR(beta, (it == 0) ? 0.0 : rz / a.h_rho[it - 1])
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_rho[it] = rz;
+    const T bt = (T)beta;
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a.p[i] = a.z[i] + beta * a.p[i];
+        a.p[i] = a.z[i] + bt * a.p[i];
 }
 
 // CG: alpha = rho / (p.q); x += alpha p; r -= alpha q; z = M^-1 r; partials r.z, r.r
-template <int D>
-__global__ void __launch_bounds__(VB) k_cg_update(KArgs a, int it) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_cg_update(KArgs<T> a, int it) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double pq = sum_partials(PART(P_PQ), a.nparts, sh);
-    __shared__ double s_alpha;
-    if (threadIdx.x == 0) s_alpha = a.h_rho[it] / pq;
-    __syncthreads();
-    const double alpha = s_alpha;
-    double s1 = 0.0, s2 = 0.0;
+    EP_CTA_SCALAR(alpha, a.h_rho[it] / pq)
+    const T al = (T)alpha;
+    T s1 = T(0), s2 = T(0);
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
-            a.x[i] += alpha * a.p[i];
-            a.r[i] -= alpha * a.q[i];
+            a.x[i] += al * a.p[i];
+            a.r[i] -= al * a.q[i];
         }
         if (!a.amg) apply_minv<D>(a.minv, a.r, a.z, node);
 #pragma unroll
@@ -331,11 +351,12 @@ __global__ void __launch_bounds__(VB) k_cg_update(KArgs a, int it) {
 }
 
 // partial of (x, y) into PART(slot), skipped once the solve is done
-__global__ void __launch_bounds__(VB) k_dot(KArgs a, const double* __restrict__ x, const double* __restrict__ y,
-                                             int64_t n, int slot) {
+template <class T>
+__global__ void __launch_bounds__(VB) k_dot(KArgs<T> a, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+                                             int slot) {
     __shared__ double sh[32];
     if (a.rec->done) return;
-    double s1 = 0.0;
+    T s1 = T(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s1 += x[i] * y[i];
     const double b1 = block_sum(s1, sh);
@@ -343,40 +364,38 @@ __global__ void __launch_bounds__(VB) k_dot(KArgs a, const double* __restrict__ 
 }
 
 // BiCGStab: p = r + beta (p - omega v); phat = M^-1 p
-template <int D>
-__global__ void __launch_bounds__(VB) k_bicg_p(KArgs a, int it) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_bicg_p(KArgs<T> a, int it) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double rho = sum_partials(PART(P_RZ), a.nparts, sh);
     const double rr = sum_partials(PART(P_RR), a.nparts, sh);
-    if (check_done(a, it, rho, rr, sh)) return;
-    double beta = 0.0, om = 0.0;
+    if (check_done(a, it, rho, rr)) return;
+    double om = 0.0;
     if (it > 0) {
         om = a.h_omega[it - 1];
         if (om == 0.0) {   // t = 0 in the last step: breakdown (convergence was tested above)
             if (blockIdx.x == 0 && threadIdx.x == 0) { a.rec->done = 2; a.rec->why = 5; }
             return;
         }
-        __shared__ double s_beta;
-        if (threadIdx.x == 0) s_beta = (rho / a.h_rho[it - 1]) * (a.h_alpha[it - 1] / om);
-        __syncthreads();
-        beta = s_beta;
     }
+    EP_CTA_SCALAR(beta, it > 0 ? (rho / a.h_rho[it - 1]) * (a.h_alpha[it - 1] / om) : 0.0)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_rho[it] = rho;
+    const T bt = (T)beta, omt = (T)om;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
-            a.p[i] = a.r[i] + beta * (a.p[i] - om * a.v[i]);
+            a.p[i] = a.r[i] + bt * (a.p[i] - omt * a.v[i]);
         }
         if (!a.amg) apply_minv<D>(a.minv, a.p, a.phat, node);
     }
 }
 
 // BiCGStab: alpha = rho / (rhat.v); s = r - alpha v; shat = M^-1 s
-template <int D>
-__global__ void __launch_bounds__(VB) k_bicg_s(KArgs a, int it) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_bicg_s(KArgs<T> a, int it) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double rv = sum_partials(PART(P_PQ), a.nparts, sh);
@@ -384,40 +403,35 @@ __global__ void __launch_bounds__(VB) k_bicg_s(KArgs a, int it) {
         if (blockIdx.x == 0 && threadIdx.x == 0) { a.rec->done = 2; a.rec->why = 4; }
         return;
     }
-    __shared__ double s_alpha;
-    if (threadIdx.x == 0) s_alpha = a.h_rho[it] / rv;
-    __syncthreads();
-    const double alpha = s_alpha;
+    EP_CTA_SCALAR(alpha, a.h_rho[it] / rv)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_alpha[it] = alpha;
+    const T al = (T)alpha;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const int64_t i = node * D + c;
-            a.s[i] = a.r[i] - alpha * a.v[i];
+            a.s[i] = a.r[i] - al * a.v[i];
         }
         if (!a.amg) apply_minv<D>(a.minv, a.s, a.shat, node);
     }
 }
 
 // BiCGStab: omega = (t.s)/(t.t); x += alpha phat + omega shat; r = s - omega t; partials rhat.r, r.r
-template <int D>
-__global__ void __launch_bounds__(VB) k_bicg_x(KArgs a, int it) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_bicg_x(KArgs<T> a, int it) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double ts = sum_partials(PART(P_TS), a.nparts, sh);
     const double tt = sum_partials(PART(P_TT), a.nparts, sh);
-    const double alpha = a.h_alpha[it];
-    __shared__ double s_om;
-    if (threadIdx.x == 0) s_om = (tt > 0.0) ? ts / tt : 0.0;
-    __syncthreads();
-    const double om = s_om;
+    EP_CTA_SCALAR(om, (tt > 0.0) ? ts / tt : 0.0)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.h_omega[it] = om;
-    double s1 = 0.0, s2 = 0.0;
+    const T al = (T)a.h_alpha[it], omt = (T)om;
+    T s1 = T(0), s2 = T(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_rows * D;
          i += (int64_t)gridDim.x * blockDim.x) {
-        a.x[i] += alpha * a.phat[i] + om * a.shat[i];
-        const double ri = a.s[i] - om * a.t[i];
+        a.x[i] += al * a.phat[i] + omt * a.shat[i];
+        const T ri = a.s[i] - omt * a.t[i];
         a.r[i] = ri;
         s1 += a.rhat[i] * ri;
         s2 += ri * ri;
@@ -431,12 +445,13 @@ __global__ void __launch_bounds__(VB) k_bicg_x(KArgs a, int it) {
 }
 
 // Two dot partials (t.s and t.t) after the second SpMV of BiCGStab.
-__global__ void __launch_bounds__(VB) k_dot2(KArgs a, int64_t n) {
+template <class T>
+__global__ void __launch_bounds__(VB) k_dot2(KArgs<T> a, int64_t n) {
     __shared__ double sh[32];
     if (a.rec->done) return;
-    double s1 = 0.0, s2 = 0.0;
+    T s1 = T(0), s2 = T(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double ti = a.t[i];
+        const T ti = a.t[i];
         s1 += ti * a.s[i];
         s2 += ti * ti;
     }
@@ -449,8 +464,29 @@ __global__ void __launch_bounds__(VB) k_dot2(KArgs a, int64_t n) {
 }
 
 // ---------------------------------------------------------------------------
-// Host side
+// Host side: buffers
 // ---------------------------------------------------------------------------
+template <class T>
+static cudaError_t alloc_vecs(KVecs<T>& v, int64_t n, int64_t n_rows, int dim) {
+    const size_t vb = sizeof(T) * (size_t)std::max<int64_t>(n, 1);
+    T** vecs[] = {&v.x, &v.r, &v.z, &v.p, &v.q, &v.rhat, &v.v, &v.s, &v.t, &v.phat, &v.shat};
+    for (T** p : vecs) {
+        cudaError_t e = cudaMalloc(p, vb);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMalloc(&v.minv, sizeof(T) * (size_t)std::max<int64_t>(n_rows, 1) * dim * dim);
+    if (e != cudaSuccess) return e;
+    return cudaMalloc(&v.V, vb * (GM_M + 1));
+}
+
+template <class T>
+static void free_vecs(KVecs<T>& v) {
+    T* vecs[] = {v.x, v.r, v.z, v.p, v.q, v.rhat, v.v, v.s, v.t, v.phat, v.shat, v.minv, v.V};
+    for (T* p : vecs)
+        if (p) cudaFree(p);
+    v = KVecs<T>{};
+}
+
 cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms) {
     w = KrylovWork{};
     w.n = n_rows * dim;
@@ -460,16 +496,9 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
     w.hist_len = maxit_cap + 2;
     w.gm_m = 30;
     if (const char* m = std::getenv("EP_GMRES_M")) w.gm_m = std::atoi(m);
-    const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(w.n, 1);
-    double** vecs[] = {&w.x, &w.r, &w.z, &w.p, &w.q, &w.rhat, &w.v, &w.s, &w.t, &w.phat, &w.shat};
-    for (double** v : vecs) {
-        cudaError_t e = cudaMalloc(v, vb);
-        if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = cudaMalloc(&w.minv, sizeof(double) * (size_t)std::max<int64_t>(n_rows, 1) * dim * dim);
+    cudaError_t e = alloc_vecs(w.d, w.n, n_rows, dim);
     if (e != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.part, sizeof(double) * std::max<int>((int)P_N, GM_M + 2) * w.nparts)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.V, vb * (GM_M + 1))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.gm, sizeof(double) * ((GM_M + 1) * GM_M + 3 * (GM_M + 1)))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.hist, sizeof(double) * 3 * w.hist_len)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&w.rec, sizeof(KrylovRec))) != cudaSuccess) return e;
@@ -479,9 +508,16 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
     return cudaSuccess;
 }
 
+cudaError_t krylov_alloc_f32(KrylovWork& w, int64_t n_rows, int dim) {
+    if (w.f.x) return cudaSuccess;
+    return alloc_vecs(w.f, w.n, n_rows, dim);
+}
+
 void krylov_free(KrylovWork& w) {
-    double* vecs[] = {w.x, w.r, w.z, w.p, w.q, w.rhat, w.v, w.s, w.t, w.phat, w.shat, w.minv, w.part, w.hist, w.V, w.gm};
-    for (double* v : vecs)
+    free_vecs(w.d);
+    free_vecs(w.f);
+    double* arrs[] = {w.part, w.hist, w.gm};
+    for (double* v : arrs)
         if (v) cudaFree(v);
     if (w.rec) cudaFree(w.rec);
     if (w.rec_host) cudaFreeHost(w.rec_host);
@@ -490,37 +526,57 @@ void krylov_free(KrylovWork& w) {
     w = KrylovWork{};
 }
 
-cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s) {
+template <class T> static KVecs<T>& vecs_of(KrylovWork& w);
+template <> KVecs<double>& vecs_of<double>(KrylovWork& w) { return w.d; }
+template <> KVecs<float>& vecs_of<float>(KrylovWork& w) { return w.f; }
+
+template <class T>
+static cudaError_t precond_t(const BsrT<T>& A, KrylovWork& w, int kind, cudaStream_t s) {
     const unsigned g = (unsigned)((A.n_rows + 255) / 256);
     if (g == 0) return cudaSuccess;
     const int bj = (kind == 0) ? 0 : 1;    // the AMG smoother uses the block-Jacobi inverse
-    if (A.dim == 2) k_precond<2><<<g, 256, 0, s>>>(A, w.minv, bj);
-    else k_precond<3><<<g, 256, 0, s>>>(A, w.minv, bj);
+    T* minv = vecs_of<T>(w).minv;
+    if (A.dim == 2) k_precond<2, T><<<g, 256, 0, s>>>(A, minv, bj);
+    else k_precond<3, T><<<g, 256, 0, s>>>(A, minv, bj);
     w.launches += 1;
     w.use_amg = (kind == 2 && w.amg) ? 1 : 0;
     if (w.use_amg) {
-        cudaError_t e = amg_refresh(*w.amg, A, w.minv, w.galerkin, s);
+        cudaError_t e = amg_refresh(*w.amg, A, minv, w.galerkin, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
-template <int D>
-static void launch_spmv(const BsrDev& A, const double* x, double* y, const double* dv, double* part,
-                        const KrylovRec* rec, int grid, cudaStream_t s) {
-    if (D == 2) k_spmv<2, 4><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
-    else k_spmv<3, 8><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
+cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s) { return precond_t(A, w, kind, s); }
+cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t s) { return precond_t(A, w, kind, s); }
+
+template <int D, class T>
+static void launch_spmv(const BsrT<T>& A, const T* x, T* y, const T* dv, double* part, const KrylovRec* rec, int grid,
+                        cudaStream_t s) {
+    if (D == 2) k_spmv<2, 4, T><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
+    else k_spmv<3, 8, T><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
 }
 
-template <int D>
-static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
+// AMG V-cycle out = M^-1 in, in the solver's precision
+static cudaError_t amg_apply_t(KrylovWork& w, const BsrDev& A, const double* in, double* out, const KrylovRec* rec,
+                               cudaStream_t s) {
+    return amg_apply(*w.amg, A, in, out, rec, s);
+}
+static cudaError_t amg_apply_t(KrylovWork& w, const BsrF& A, const float* in, float* out, const KrylovRec* rec,
+                               cudaStream_t s) {
+    return amg_apply(*w.amg, A, in, out, rec, s);
+}
+
+template <int D, class T>
+static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int method, double rtol, int maxit,
                            cudaStream_t s, int* its, double* relres, int* status) {
-    KArgs a;
+    KVecs<T>& vv = vecs_of<T>(w);
+    KArgs<T> a;
     a.n_rows = A.n_rows;
     a.free_dof = A.free_dof;
-    a.minv = w.minv;
-    a.x = w.x; a.r = w.r; a.z = w.z; a.p = w.p; a.q = w.q; a.rhat = w.rhat; a.v = w.v; a.s = w.s; a.t = w.t;
-    a.phat = w.phat; a.shat = w.shat;
+    a.minv = vv.minv;
+    a.x = vv.x; a.r = vv.r; a.z = vv.z; a.p = vv.p; a.q = vv.q; a.rhat = vv.rhat; a.v = vv.v; a.s = vv.s; a.t = vv.t;
+    a.phat = vv.phat; a.shat = vv.shat;
     a.part = w.part;
     a.nparts = w.nparts;
     if (maxit > w.hist_len - 2) maxit = w.hist_len - 2;
@@ -540,14 +596,14 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
     a.cold = (restart == 0);
     a.maxit = maxit - total_its;
     if (restart > 0) {   // warm restart from the current x after a breakdown
-        launch_spmv<D>(A, w.x, w.q, nullptr, nullptr, nullptr, grid, s);
+        launch_spmv<D, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
         w.launches += 1;
     }
-    k_init<D><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
+    k_init<D, T><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
     w.launches += 1;
     if (a.amg && !bicg) {   // z = M^-1 r0, then (r, z)
-        amg_apply(*w.amg, A, w.minv, w.r, w.z, w.rec, s);
-        k_dot<<<grid, VB, 0, s>>>(a, w.r, w.z, w.n, P_RZ);
+        amg_apply_t(w, A, vv.r, vv.z, w.rec, s);
+        k_dot<T><<<grid, VB, 0, s>>>(a, vv.r, vv.z, w.n, P_RZ);
         w.launches += 1;
     }
     int it = 0;
@@ -557,30 +613,30 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
         int nev = 0;
         for (; it < stop; ++it) {
             if (!bicg) {
-                k_cg_p<D><<<grid, VB, 0, s>>>(a, it);
+                k_cg_p<D, T><<<grid, VB, 0, s>>>(a, it);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D>(A, w.p, w.q, w.p, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
+                launch_spmv<D, T>(A, vv.p, vv.q, vv.p, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                k_cg_update<D><<<grid, VB, 0, s>>>(a, it);
+                k_cg_update<D, T><<<grid, VB, 0, s>>>(a, it);
                 w.launches += 3;
                 if (a.amg) {
-                    amg_apply(*w.amg, A, w.minv, w.r, w.z, w.rec, s);
-                    k_dot<<<grid, VB, 0, s>>>(a, w.r, w.z, w.n, P_RZ);
+                    amg_apply_t(w, A, vv.r, vv.z, w.rec, s);
+                    k_dot<T><<<grid, VB, 0, s>>>(a, vv.r, vv.z, w.n, P_RZ);
                     w.launches += 1;
                 }
             } else {
-                k_bicg_p<D><<<grid, VB, 0, s>>>(a, it);
-                if (a.amg) amg_apply(*w.amg, A, w.minv, w.p, w.phat, w.rec, s);
+                k_bicg_p<D, T><<<grid, VB, 0, s>>>(a, it);
+                if (a.amg) amg_apply_t(w, A, vv.p, vv.phat, w.rec, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D>(A, w.phat, w.v, w.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
+                launch_spmv<D, T>(A, vv.phat, vv.v, vv.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                k_bicg_s<D><<<grid, VB, 0, s>>>(a, it);
-                if (a.amg) amg_apply(*w.amg, A, w.minv, w.s, w.shat, w.rec, s);
+                k_bicg_s<D, T><<<grid, VB, 0, s>>>(a, it);
+                if (a.amg) amg_apply_t(w, A, vv.s, vv.shat, w.rec, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D>(A, w.shat, w.t, nullptr, nullptr, w.rec, grid, s);
+                launch_spmv<D, T>(A, vv.shat, vv.t, nullptr, nullptr, w.rec, grid, s);
                 if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                k_dot2<<<grid, VB, 0, s>>>(a, w.n);
-                k_bicg_x<D><<<grid, VB, 0, s>>>(a, it);
+                k_dot2<T><<<grid, VB, 0, s>>>(a, w.n);
+                k_bicg_x<D, T><<<grid, VB, 0, s>>>(a, it);
                 w.launches += 6;
             }
         }
@@ -619,22 +675,23 @@ static cudaError_t solve_t(const BsrDev& A, KrylovWork& w, const double* b, int 
     return cudaSuccess;
 }
 
-
 // ---------------------------------------------------------------------------
 // GMRES(m), right preconditioned: x = x0 + M^-1 V y.  The Hessenberg matrix,
-// the Givens rotations and the residual estimate live in device memory and are
-// updated by thread 0 of CTA 0; every CTA recomputes the reductions it needs
-// from the partial sums, so no launch reads a value written in that launch.
+// the Givens rotations and the residual estimate live in device memory (FP64)
+// and are updated by thread 0 of CTA 0; every CTA recomputes the reductions it
+// needs from the partial sums, so no launch reads a value written in that
+// launch.
 // ---------------------------------------------------------------------------
+template <class T>
 struct GArgs {
     int64_t n_rows;
     const uint8_t* free_dof;
-    const double* minv;
-    double* x;
-    double* r;          // r0 of the cycle
-    double* q;          // A x for warm restarts
-    double* z;          // M^-1 v_j
-    double* V;          // [m+1][n]
+    const T* minv;
+    T* x;
+    T* r;               // r0 of the cycle
+    T* q;               // A x for warm restarts
+    T* z;               // M^-1 v_j
+    T* V;               // [m+1][n]
     double* H;          // [m+1][m], H[i*m + j]
     double* cs;
     double* sn;
@@ -650,15 +707,15 @@ struct GArgs {
 #define GPART(k) (a.part + (int64_t)(k) * a.nparts)
 
 // r = P(b - q) (warm) or P b with x = 0 (cold); partial ||r||^2 -> GPART(0)
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_init(GArgs a, const double* __restrict__ b, int warm) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_init(GArgs<T> a, const T* __restrict__ b, int warm) {
     __shared__ double sh[32];
-    double s1 = 0.0;
+    T s1 = T(0);
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double ri = a.free_dof[i] ? (warm ? b[i] - a.q[i] : b[i]) : 0.0;
+        const T ri = a.free_dof[i] ? (warm ? b[i] - a.q[i] : b[i]) : T(0);
         a.r[i] = ri;
-        if (!warm) a.x[i] = 0.0;
+        if (!warm) a.x[i] = T(0);
         s1 += ri * ri;
     }
     const double b1 = block_sum(s1, sh);
@@ -669,8 +726,8 @@ __global__ void __launch_bounds__(VB) k_gm_init(GArgs a, const double* __restric
 }
 
 // beta = ||r||, v_0 = r / beta, g = (beta, 0, ...); convergence test of the cycle start
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_start(GArgs a) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_start(GArgs<T> a) {
     __shared__ double sh[32];
     const double rr = sum_partials(GPART(0), a.nparts, sh);
     const double rr0 = a.cold ? rr : a.rec->rr0;
@@ -689,32 +746,32 @@ __global__ void __launch_bounds__(VB) k_gm_start(GArgs a) {
         else if (conv) { a.rec->done = 1; a.rec->why = 1; }
     }
     if (conv || !isfinite(rr)) return;
-    const double ib = s_b[1];
+    const T ib = (T)s_b[1];
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a.V[i] = a.r[i] * ib;
 }
 
 // z = M^-1 v_j
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_prec(GArgs a, int j) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_prec(GArgs<T> a, int j) {
     if (a.rec->done) return;
-    const double* v = a.V + (int64_t)j * a.n_rows * D;
+    const T* v = a.V + (int64_t)j * a.n_rows * D;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x)
         apply_minv<D>(a.minv, v, a.z, node);
 }
 
 // partials of h_i = (w, v_i), i = 0..j, with w = V[j+1]; grid (nparts, j + 1): CTA (b, i) -> GPART(i)[b]
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_dots(GArgs a, int j) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_dots(GArgs<T> a, int j) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     const int i = blockIdx.y;
     const int64_t n = a.n_rows * D;
-    const double* w = a.V + (int64_t)(j + 1) * n;
-    const double* v = a.V + (int64_t)i * n;
-    double acc = 0.0;
+    const T* w = a.V + (int64_t)(j + 1) * n;
+    const T* v = a.V + (int64_t)i * n;
+    T acc = T(0);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         acc += w[k] * v[k];
     const double bsum = block_sum(acc, sh);
@@ -722,23 +779,24 @@ __global__ void __launch_bounds__(VB) k_gm_dots(GArgs a, int j) {
 }
 
 // w -= sum_i h_i v_i; partial ||w||^2 -> GPART(GM_M + 1); CTA 0 stores H[:, j]
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_orth(GArgs a, int j) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
     __shared__ double sh[32];
-    __shared__ double h[GM_M];
+    __shared__ T h[GM_M];
     if (a.rec->done) return;
     for (int i = 0; i <= j; ++i) {
         const double v = sum_partials(GPART(i), a.nparts, sh);
-        if (threadIdx.x == 0) h[i] = v;
+        if (threadIdx.x == 0) {
+            h[i] = (T)v;
+            if (blockIdx.x == 0) a.H[i * GM_M + j] = v;
+        }
     }
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int i = 0; i <= j; ++i) a.H[i * GM_M + j] = h[i];
     const int64_t n = a.n_rows * D;
-    double* w = a.V + (int64_t)(j + 1) * n;
-    double s1 = 0.0;
+    T* w = a.V + (int64_t)(j + 1) * n;
+    T s1 = T(0);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        double wk = w[k];
+        T wk = w[k];
         for (int i = 0; i <= j; ++i) wk -= h[i] * a.V[(int64_t)i * n + k];
         w[k] = wk;
         s1 += wk * wk;
@@ -748,8 +806,8 @@ __global__ void __launch_bounds__(VB) k_gm_orth(GArgs a, int j) {
 }
 
 // h_{j+1,j} = ||w||, v_{j+1} = w / h; CTA 0: Givens update and convergence test
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_norm(GArgs a, int j, int it_base, int maxit) {
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_norm(GArgs<T> a, int j, int it_base, int maxit) {
     __shared__ double sh[32];
     if (a.rec->done) return;
     __shared__ double s_h[2];
@@ -786,39 +844,47 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs a, int j, int it_base, int
         else if (j + 1 == a.m) { a.rec->done = 4; }   // end of the cycle: update and restart
     }
     if (hn == 0.0 || !isfinite(hn)) return;
-    const double ih = s_h[1];
+    const T ih = (T)s_h[1];
     const int64_t n = a.n_rows * D;
-    double* w = a.V + (int64_t)(j + 1) * n;
+    T* w = a.V + (int64_t)(j + 1) * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         w[k] *= ih;
 }
 
-// x += M^-1 (V_k y), y = R^-1 g (k = its of the cycle); every CTA solves the small triangle itself
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_update(GArgs a, int k) {
-    __shared__ double y[GM_M];
+// y = R^-1 g (k x k upper triangle) into shared memory, by thread 0 of every CTA
+template <class T>
+__device__ __forceinline__ void gm_solve_y(const GArgs<T>& a, int k, T* y) {
+    __shared__ double yd[GM_M];
     if (threadIdx.x == 0) {
         for (int i = k - 1; i >= 0; --i) {
             double s = a.g[i];
-            for (int l = i + 1; l < k; ++l) s -= a.H[i * GM_M + l] * y[l];
-            y[i] = s / a.H[i * GM_M + i];
+            for (int l = i + 1; l < k; ++l) s -= a.H[i * GM_M + l] * yd[l];
+            yd[i] = s / a.H[i * GM_M + i];
+            y[i] = (T)yd[i];
         }
     }
     __syncthreads();
+}
+
+// x += M^-1 (V_k y), y = R^-1 g (k = its of the cycle); every CTA solves the small triangle itself
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_update(GArgs<T> a, int k) {
+    __shared__ T y[GM_M];
+    gm_solve_y(a, k, y);
     const int64_t n = a.n_rows * D;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
-        double u[D];
+        T u[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            double s = 0.0;
+            T s = T(0);
             for (int i = 0; i < k; ++i) s += y[i] * a.V[(int64_t)i * n + node * D + c];
             u[c] = s;
         }
-        const double* m = a.minv + node * (D * D);
+        const T* m = a.minv + node * (D * D);
 #pragma unroll
         for (int r = 0; r < D; ++r) {
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
             for (int c = 0; c < D; ++c) s += m[r * D + c] * u[c];
             a.x[node * D + r] += s;
@@ -827,42 +893,37 @@ __global__ void __launch_bounds__(VB) k_gm_update(GArgs a, int k) {
 }
 
 // u = V_k y (y = R^-1 g solved redundantly by every CTA)
-template <int D>
-__global__ void __launch_bounds__(VB) k_gm_combine(GArgs a, int k, double* __restrict__ u) {
-    __shared__ double y[GM_M];
-    if (threadIdx.x == 0) {
-        for (int i = k - 1; i >= 0; --i) {
-            double s = a.g[i];
-            for (int l = i + 1; l < k; ++l) s -= a.H[i * GM_M + l] * y[l];
-            y[i] = s / a.H[i * GM_M + i];
-        }
-    }
-    __syncthreads();
+template <int D, class T>
+__global__ void __launch_bounds__(VB) k_gm_combine(GArgs<T> a, int k, T* __restrict__ u) {
+    __shared__ T y[GM_M];
+    gm_solve_y(a, k, y);
     const int64_t n = a.n_rows * D;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
+        T s = T(0);
         for (int i = 0; i < k; ++i) s += y[i] * a.V[(int64_t)i * n + t];
         u[t] = s;
     }
 }
 
-__global__ void k_axpy_plain(double* __restrict__ x, const double* __restrict__ z, int64_t n) {
+template <class T>
+__global__ void k_axpy_plain(T* __restrict__ x, const T* __restrict__ z, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += z[i];
 }
 
-template <int D>
-static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b, double rtol, int maxit,
+template <int D, class T>
+static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, double rtol, int maxit,
                                  cudaStream_t s, int* its, double* relres, int* status) {
-    GArgs a;
+    KVecs<T>& vv = vecs_of<T>(w);
+    GArgs<T> a;
     a.n_rows = A.n_rows;
     a.free_dof = A.free_dof;
-    a.minv = w.minv;
-    a.x = w.x;
-    a.r = w.r;
-    a.q = w.q;
-    a.z = w.z;
-    a.V = w.V;
+    a.minv = vv.minv;
+    a.x = vv.x;
+    a.r = vv.r;
+    a.q = vv.q;
+    a.z = vv.z;
+    a.V = vv.V;
     a.H = w.gm;
     a.cs = w.gm + (GM_M + 1) * GM_M;
     a.sn = a.cs + (GM_M + 1);
@@ -879,23 +940,23 @@ static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b
     for (int cycle = 0;; ++cycle) {
         a.cold = (cycle == 0);
         if (cycle > 0) {
-            launch_spmv<D>(A, w.x, w.q, nullptr, nullptr, nullptr, grid, s);
+            launch_spmv<D, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
             w.launches += 1;
         }
-        k_gm_init<D><<<grid, VB, 0, s>>>(a, b, cycle > 0 ? 1 : 0);
-        k_gm_start<D><<<grid, VB, 0, s>>>(a);
+        k_gm_init<D, T><<<grid, VB, 0, s>>>(a, b, cycle > 0 ? 1 : 0);
+        k_gm_start<D, T><<<grid, VB, 0, s>>>(a);
         w.launches += 2;
         int nev = 0;
         for (int j = 0; j < a.m; ++j) {
-            if (use_amg) amg_apply(*w.amg, A, w.minv, a.V + (int64_t)j * w.n, a.z, w.rec, s);
-            else k_gm_prec<D><<<grid, VB, 0, s>>>(a, j);
+            if (use_amg) amg_apply_t(w, A, a.V + (int64_t)j * w.n, a.z, w.rec, s);
+            else k_gm_prec<D, T><<<grid, VB, 0, s>>>(a, j);
             const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
             if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-            launch_spmv<D>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
+            launch_spmv<D, T>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
             if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-            k_gm_dots<D><<<dim3(grid, j + 1), VB, 0, s>>>(a, j);
-            k_gm_orth<D><<<grid, VB, 0, s>>>(a, j);
-            k_gm_norm<D><<<grid, VB, 0, s>>>(a, j, total, maxit);
+            k_gm_dots<D, T><<<dim3(grid, j + 1), VB, 0, s>>>(a, j);
+            k_gm_orth<D, T><<<grid, VB, 0, s>>>(a, j);
+            k_gm_norm<D, T><<<grid, VB, 0, s>>>(a, j, total, maxit);
             w.launches += 5;
         }
         cudaError_t e = cudaGetLastError();
@@ -915,12 +976,12 @@ static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b
         }
         if (last.its > 0) {
             if (use_amg) {
-                k_gm_combine<D><<<grid, VB, 0, s>>>(a, last.its, w.q);
-                amg_apply(*w.amg, A, w.minv, w.q, w.z, nullptr, s);
-                k_axpy_plain<<<grid, VB, 0, s>>>(w.x, w.z, w.n);
+                k_gm_combine<D, T><<<grid, VB, 0, s>>>(a, last.its, vv.q);
+                amg_apply_t(w, A, vv.q, vv.z, nullptr, s);
+                k_axpy_plain<T><<<grid, VB, 0, s>>>(vv.x, vv.z, w.n);
                 w.launches += 2;
             } else {
-                k_gm_update<D><<<grid, VB, 0, s>>>(a, last.its);
+                k_gm_update<D, T><<<grid, VB, 0, s>>>(a, last.its);
                 w.launches += 1;
             }
         }
@@ -936,14 +997,25 @@ static cudaError_t solve_gmres_t(const BsrDev& A, KrylovWork& w, const double* b
     return cudaStreamSynchronize(s);
 }
 
+template <class T>
+static cudaError_t solve_any(const BsrT<T>& A, KrylovWork& w, const T* b, int method, double rtol, int maxit,
+                             cudaStream_t s, int* its, double* relres, int* status) {
+    if (method == 3) {
+        if (A.dim == 2) return solve_gmres_t<2, T>(A, w, b, rtol, maxit, s, its, relres, status);
+        return solve_gmres_t<3, T>(A, w, b, rtol, maxit, s, its, relres, status);
+    }
+    if (A.dim == 2) return solve_t<2, T>(A, w, b, method, rtol, maxit, s, its, relres, status);
+    return solve_t<3, T>(A, w, b, method, rtol, maxit, s, its, relres, status);
+}
+
 cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int method, double rtol, int maxit,
                          cudaStream_t s, int* its, double* relres, int* status) {
-    if (method == 3) {
-        if (A.dim == 2) return solve_gmres_t<2>(A, w, b, rtol, maxit, s, its, relres, status);
-        return solve_gmres_t<3>(A, w, b, rtol, maxit, s, its, relres, status);
-    }
-    if (A.dim == 2) return solve_t<2>(A, w, b, method, rtol, maxit, s, its, relres, status);
-    return solve_t<3>(A, w, b, method, rtol, maxit, s, its, relres, status);
+    return solve_any(A, w, b, method, rtol, maxit, s, its, relres, status);
+}
+cudaError_t krylov_solve(const BsrF& A, KrylovWork& w, const float* b, int method, double rtol, int maxit,
+                         cudaStream_t s, int* its, double* relres, int* status) {
+    if (!w.f.x) return cudaErrorInvalidValue;
+    return solve_any(A, w, b, method, rtol, maxit, s, its, relres, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -951,7 +1023,8 @@ cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int me
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(VB) k_residual(const double* __restrict__ f_unit, double zeta,
                                                   const double* __restrict__ F, const uint8_t* __restrict__ free_dof,
-                                                  double* __restrict__ r, int64_t n, double* part, int nparts) {
+                                                  double* __restrict__ r, float* __restrict__ r32, int64_t n,
+                                                  double* part, int nparts) {
     __shared__ double sh[32];
     double s_r = 0.0, s_f = 0.0, s_F = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -960,6 +1033,7 @@ __global__ void __launch_bounds__(VB) k_residual(const double* __restrict__ f_un
         const bool fr = free_dof[i] != 0;
         const double ri = fr ? fi - Fi : 0.0;
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         s_r += ri * ri;
         s_f += fr ? fi * fi : 0.0;
         s_F += Fi * Fi;
@@ -983,8 +1057,8 @@ __global__ void k_finalize3(const double* part, int nparts, double* out3) {
 }
 
 cudaError_t vec_residual(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof, double* r,
-                         int64_t n, double* part, int nparts, double* out3, cudaStream_t s) {
-    k_residual<<<nparts, VB, 0, s>>>(f_unit, zeta, F, free_dof, r, n, part, nparts);
+                         float* r32, int64_t n, double* part, int nparts, double* out3, cudaStream_t s) {
+    k_residual<<<nparts, VB, 0, s>>>(f_unit, zeta, F, free_dof, r, r32, n, part, nparts);
     k_finalize3<<<1, 32, 0, s>>>(part, nparts, out3);
     return cudaGetLastError();
 }
@@ -1002,6 +1076,17 @@ __global__ void k_set_dirichlet(double* u, const double* uD, double zeta, const 
 __global__ void k_extrapolate(double* u, const double* u_prev, double ratio, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         u[i] += ratio * (u[i] - u_prev[i]);
+}
+
+__global__ void k_axpy_f32(double* __restrict__ y, const float* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += (double)x[i];
+}
+
+template <class TI, class TO>
+__global__ void k_convert(const TI* __restrict__ x, TO* __restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (TO)x[i];
 }
 
 __global__ void k_mask_copy(double* dst, const double* src, const uint8_t* free_dof, int64_t n) {
@@ -1025,6 +1110,18 @@ cudaError_t vec_set_dirichlet(double* u, const double* uD_unit, double zeta, con
 }
 cudaError_t vec_extrapolate(double* u, const double* u_prev, double ratio, int64_t n, cudaStream_t s) {
     k_extrapolate<<<vgrid(n), VB, 0, s>>>(u, u_prev, ratio, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_axpy_f32(double* y, const float* x, int64_t n, cudaStream_t s) {
+    k_axpy_f32<<<vgrid(n), VB, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_cvt_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
+    k_convert<double, float><<<vgrid(n), VB, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_cvt_f64(const float* x, double* y, int64_t n, cudaStream_t s) {
+    k_convert<float, double><<<vgrid(n), VB, 0, s>>>(x, y, n);
     return cudaGetLastError();
 }
 cudaError_t vec_mask_copy(double* dst, const double* src, const uint8_t* free_dof, int64_t n, cudaStream_t s) {

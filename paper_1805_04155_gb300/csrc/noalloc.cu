@@ -99,10 +99,10 @@ extern "C" ep_status ep_linear_solve_noalloc(int32_t dim, int64_t n_nodes, const
     w.nparts = w.grid;
     w.hist_len = NOALLOC_MAX_IT + 2;
     w.gm_m = 0;
-    double** vecs[NV] = {&w.r, &w.z, &w.p, &w.q, &w.rhat, &w.v, &w.s, &w.t, &w.phat, &w.shat};
+    double** vecs[NV] = {&w.d.r, &w.d.z, &w.d.p, &w.d.q, &w.d.rhat, &w.d.v, &w.d.s, &w.d.t, &w.d.phat, &w.d.shat};
     for (int64_t i = 0; i < NV; ++i) *vecs[i] = base + i * NOALLOC_MAX_DOF;
-    w.x = x;
-    w.minv = base + OFF_MINV;
+    w.d.x = x;
+    w.d.minv = base + OFF_MINV;
     w.part = base + OFF_PART;
     w.hist = base + OFF_HIST;
     w.rec = reinterpret_cast<KrylovRec*>(base + OFF_REC);

@@ -23,13 +23,15 @@ EP_P1, EP_P2, EP_Q1, EP_Q2 = range(4)
 ELEM_IDS = {"P1": EP_P1, "P2": EP_P2, "Q1": EP_Q1, "Q2": EP_Q2}
 # ep_model
 EP_ELASTIC, EP_VM_KIN, EP_VM_ISO, EP_DP = range(4)
+# ep_precision
+EP_FP64, EP_MIXED = range(2)
 # ep_field
 (EP_U, EP_STRESS, EP_PLASTIC_STRAIN, EP_HARDENING, EP_PLASTIC_FLAG, EP_F_INT, EP_K_ROW_PTR, EP_K_COL_IDX,
- EP_K_VALUES, EP_K_ELASTIC, EP_WEIGHT, EP_DPHI, EP_SOLUTION) = range(13)
+ EP_K_VALUES, EP_K_ELASTIC, EP_WEIGHT, EP_DPHI, EP_SOLUTION, EP_K_VALUES_F32) = range(14)
 
 EXPORTED = [
     "ep_default_opts", "ep_create", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set",
-    "ep_assemble", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error",
+    "ep_assemble", "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error",
     "ep_linear_solve_noalloc",
 ]
 EP_NOALLOC_MAX_DOF = 32768
@@ -88,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_get.argtypes = [vp, i32, vp, sz, i32]
     lib.ep_set.argtypes = [vp, i32, vp, sz, i32]
     lib.ep_assemble.argtypes = [vp, vp, i32, i32, C.POINTER(i64)]
+    lib.ep_assemble_prec.argtypes = [vp, vp, i32, i32, i32, C.POINTER(i64)]
     lib.ep_commit.argtypes = [vp, vp, i32]
     lib.ep_linear_solve.argtypes = [vp, vp, i32, C.POINTER(ep_opts), C.POINTER(i32), dp]
     lib.ep_constitutive.argtypes = [C.POINTER(ep_material), i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -99,7 +102,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_last_error.argtypes = [vp]
     lib.ep_last_error.restype = C.c_char_p
     for name in ("ep_create", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set", "ep_assemble",
-                 "ep_commit", "ep_linear_solve", "ep_constitutive"):
+                 "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -213,6 +216,7 @@ class Context:
             EP_K_VALUES: ((i.nnz_blocks, i.dim, i.dim), np.float64),
             EP_K_ELASTIC: ((i.nnz_blocks, i.dim, i.dim), np.float64), EP_WEIGHT: ((i.n_int,), np.float64),
             EP_DPHI: ((i.n_int, i.n_p, i.dim), np.float64), EP_SOLUTION: ((self.n_dof,), np.float64),
+            EP_K_VALUES_F32: ((i.nnz_blocks, i.dim, i.dim), np.float32),
         }[field]
 
     # -- C calls -------------------------------------------------------------------
@@ -241,10 +245,14 @@ class Context:
             return a.ctypes.data, 0
         return v.data_ptr(), 1
 
-    def assemble(self, u, split=True) -> int:
+    def assemble(self, u, split=True, precision=EP_FP64) -> int:
         p, dev = self._vec_arg(u)
         npl = C.c_int64(0)
-        self._check(lib().ep_assemble(self.h, C.c_void_p(p), dev, int(bool(split)), C.byref(npl)))
+        if precision == EP_FP64:
+            self._check(lib().ep_assemble(self.h, C.c_void_p(p), dev, int(bool(split)), C.byref(npl)))
+        else:
+            self._check(lib().ep_assemble_prec(self.h, C.c_void_p(p), dev, int(bool(split)), int(precision),
+                                               C.byref(npl)))
         return npl.value
 
     def commit(self, u):
@@ -268,12 +276,13 @@ class Context:
             self._check(st)
         return out if raise_on_error else (st, out)
 
-    def K_csr(self, elastic=False):
-        """K as scipy CSR (DOF level) from the block-CSR arrays."""
+    def K_csr(self, elastic=False, f32=False):
+        """K as scipy CSR (DOF level) from the block-CSR arrays (f32: the FP32 tangent, as float64)."""
         import scipy.sparse as sp
         rp = self.get(EP_K_ROW_PTR)
         ci = self.get(EP_K_COL_IDX)
-        vals = self.get(EP_K_ELASTIC if elastic else EP_K_VALUES)
+        field = EP_K_ELASTIC if elastic else (EP_K_VALUES_F32 if f32 else EP_K_VALUES)
+        vals = self.get(field).astype(np.float64)
         return sp.bsr_matrix((vals, ci, rp), shape=(self.n_dof, self.n_dof)).tocsr()
 
 
