@@ -10,11 +10,13 @@ K = 40 times exactly one full 40-step load path.
 value = integration points assembled per second over the timed region
         (n_int x assemblies / elapsed), i.e. the rate at which the solver
         drives every integration point through return mapping + tangent
-        assembly, Krylov and update included, for the primary precision
-        (--precision, default mixed: FP32 tangent and inner Krylov, FP64
-        return mapping, residual and update).  The other precision runs the
-        same load path after it ("compare": value, load-path time, Newton and
-        Krylov iterations, and the difference of the final displacements).
+        assembly, Krylov and update included, for the primary precision.
+        Both precisions are timed on the same load steps from the virgin
+        state: fp64 and mixed (FP32 tangent and inner Krylov while they
+        contract well, FP64 return mapping, residual and update); with
+        --precision auto (default) the faster is the primary and the other
+        is reported under "compare" (value, load-path time, Newton and Krylov
+        iterations, and the difference of the final displacements).
 roofline: the dominant kernel of the step (measured with CUDA events around
         every launch inside the timed region, on the context's stream).
 e2e:    the same metric through the C ABI with host buffers: each step
@@ -243,8 +245,9 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="cells per side (0: the workload's full size)")
     ap.add_argument("--skip", type=int, default=0,
                     help="run the first S load steps untimed before the timed region (bounded profiling)")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the load path in the other precision")
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"],
+                    help="primary precision; auto: time both, report the faster as the primary")
+    ap.add_argument("--no-compare", action="store_true", help="time the primary precision only (auto: mixed)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -318,41 +321,47 @@ def main():
             ms = float(t.item())
         return ms
 
-    prec = args.precision
-    other = "fp64" if prec == "mixed" else "mixed"
+    if args.no_compare:
+        precs = ["mixed" if args.precision == "auto" else args.precision]
+    else:
+        precs = ["mixed", "fp64"] if args.precision in ("auto", "mixed") else ["fp64", "mixed"]
     # warm-up: first W load steps in each precision used, then back to the virgin state
-    for p_ in ([prec] if args.no_compare else [prec, other]):
+    for p_ in precs:
         for j in range(args.warmup):
             ctx.solve_load_path([prob.zeta[j % n_path]], opts_for(p_))
         reset()
 
-    clocks = Clocks(local)
-    ms, wall, reps = timed(prec, False, args.steps, args.skip)
-    clk = clocks.stop()
-    ms = max_over_ranks(ms)
+    # the timed runs: the same load steps in each precision, from the virgin state
     ends_on_path_end = (args.skip + args.steps) % n_path == 0
-    u_primary = ctx.get(ep.EP_U) if ends_on_path_end else None
+    clocks = Clocks(local)
+    runs = {}
+    for p_ in precs:
+        reset()
+        ms_p, wall_p, reps_p = timed(p_, False, args.steps, args.skip)
+        runs[p_] = (max_over_ranks(ms_p), wall_p, reps_p, ctx.get(ep.EP_U) if ends_on_path_end else None)
+    clk = clocks.stop()
+    prec = args.precision if args.precision != "auto" else min(runs, key=lambda k: runs[k][0])
+    ms, wall, reps, u_primary = runs[prec]
     assemblies = sum(r.n_assemble for r in reps)
     n_int = info.n_int
     value = world * n_int * assemblies / (ms / 1e3) / 1e9
 
     compare = None
-    if not args.no_compare:
-        reset()
-        ms_o, _, reps_o = timed(other, False, n_path, 0)
-        ms_o = max_over_ranks(ms_o)
+    others = [p_ for p_ in precs if p_ != prec]
+    if others:
+        other = others[0]
+        ms_o, _, reps_o, u_o = runs[other]
         a_o = sum(r.n_assemble for r in reps_o)
-        u_o = ctx.get(ep.EP_U)
         compare = {"precision": other, "value": world * n_int * a_o / (ms_o / 1e3) / 1e9, "unit": UNIT,
-                   "load_path_s": ms_o / 1e3, "newton_its": int(sum(r.newton_its for r in reps_o)),
+                   "load_path_s": ms_o / 1e3 * n_path / args.steps,
+                   "newton_its": int(sum(r.newton_its for r in reps_o)),
+                   "newton_its_fp32": int(sum(r.newton_its_fp32 for r in reps_o)),
                    "krylov_its": int(sum(r.krylov_its for r in reps_o)),
                    "max_rel_resid": max(r.rel_resid for r in reps_o),
                    "assembly_avg_us": 1e3 * sum(r.t_assemble_kernel_ms for r in reps_o) / max(1, a_o),
                    "spmv_avg_us": 1e3 * sum(r.t_spmv_kernel_ms for r in reps_o) / max(1, sum(r.n_spmv for r in reps_o))}
-        if u_primary is not None:
+        if u_primary is not None and u_o is not None:
             compare["u_rel_diff"] = float(np.linalg.norm(u_primary - u_o) / max(np.linalg.norm(u_o), 1e-300))
-        # the primary precision's load path time over one full path, for the side-by-side
-        compare["primary_load_path_s"] = ms / 1e3 * n_path / args.steps
 
     e2e = None
     if not args.no_e2e:
@@ -421,6 +430,7 @@ def main():
             "clocks": clk, "gpu_launches": int(sum(r.launches for r in reps)),
             "load_path_s": ms / 1e3 * n_path / args.steps,
             "newton_its": int(sum(r.newton_its for r in reps)), "krylov_its": int(sum(r.krylov_its for r in reps)),
+            "newton_its_fp32": int(sum(r.newton_its_fp32 for r in reps)),
             "n_plastic_final": int(reps[-1].n_plastic) if reps else 0,
             "max_rel_resid": max(r.rel_resid for r in reps) if reps else None,
             "wall_s": wall}

@@ -72,7 +72,13 @@ typedef enum {
  * their assembly into K and the inner Krylov solve (vectors, SpMV,
  * preconditioner) run in FP32.  Newton on the FP64 residual is the outer
  * refinement, so the load path still reaches newton_rtol; the inner relative
- * tolerance is not taken below 1e-5.
+ * tolerance is not taken below 1e-5.  Newton on an FP32 tangent contracts
+ * only linearly (by about cond(K) * 2^-24 per iteration), so once an FP32
+ * iteration reduces the FP64 residual by less than a factor 50, the FP64
+ * tangent and solve finish the load step.  When a Newton iteration on the FP32 tangent reduces
+ * the FP64 residual by less than half (an ill-conditioned tangent, e.g. near a
+ * limit load), that load step and the rest of the path continue in FP64
+ * (until EP_U is set again).
  */
 typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
 
@@ -128,6 +134,8 @@ typedef struct {
     double t_assemble_kernel_ms; /* summed duration of the assembly kernel launches (profile = 1) */
     double t_spmv_kernel_ms;     /* summed duration of those SpMV launches (profile = 1) */
     int64_t n_plastic_assembled; /* plastic points summed over the step's assemblies (local-tangent work done) */
+    int32_t newton_its_fp32;     /* EP_MIXED: Newton iterations of the step that used the FP32 tangent and solve */
+    int32_t reserved;
 } ep_step_report;
 
 /* Fields readable with ep_get / writable with ep_set. */

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "amg.h"
+#include "pdl.cuh"
 
 namespace ep {
 
@@ -118,6 +119,7 @@ template <int RB, int G, class T>
 __global__ void __launch_bounds__(AB) k_cheb(Mat<T> A, const T* __restrict__ dinv, const T* __restrict__ b,
                                               const T* __restrict__ x_in, T* __restrict__ x_out, T* __restrict__ d,
                                               const float* __restrict__ coef, int step, const KrylovRec* rec) {
+    pdl_enter();
     if (rec && rec->done) return;
     struct { T inv_theta, c1, c2; } cf = {(T)coef[0], (T)coef[1], (T)coef[2]};
     ROW_LOOP_BEGIN(A.n_rows)
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(AB) k_cheb(Mat<T> A, const T* __restrict__ din
 template <int RB, int G, class T>
 __global__ void __launch_bounds__(AB) k_resid(Mat<T> A, const T* __restrict__ b, const T* __restrict__ x,
                                                T* __restrict__ r, const KrylovRec* rec) {
+    pdl_enter();
     if (rec && rec->done) return;
     ROW_LOOP_BEGIN(A.n_rows)
     T acc[RB];
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(AB) k_resid(Mat<T> A, const T* __restrict__ b,
 template <int RB, int CB, int G, class TX, class TY>
 __global__ void __launch_bounds__(AB) k_mv(Mat<float> M, const TX* __restrict__ x, TY* __restrict__ y, int add,
                                             const KrylovRec* rec) {
+    pdl_enter();
     if (rec && rec->done) return;
     ROW_LOOP_BEGIN(M.n_rows)
     float acc[RB];
@@ -190,6 +194,7 @@ __global__ void __launch_bounds__(AB) k_mv(Mat<float> M, const TX* __restrict__ 
 // x = Ainv b, dense FP32 (coarsest level); one warp per row
 __global__ void __launch_bounds__(AB) k_dense(const float* __restrict__ Ainv, int64_t n, const float* __restrict__ b,
                                                float* __restrict__ x, const KrylovRec* rec) {
+    pdl_enter();
     if (rec && rec->done) return;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -418,10 +423,16 @@ __global__ void k_pw_init(T* x, int64_t n, const uint8_t* mask) {
 // ---------------------------------------------------------------------------
 // Dispatch helpers
 // ---------------------------------------------------------------------------
+// SMs of the device (set at upload).  Row kernels use at most one resident wave of CTAs
+// (RES_CTAS of AB threads per SM at <= 40 registers) and loop over the rows: every extra wave
+// costs CTA launch and drain time on these short kernels.
+static int g_num_sms = 152;
+constexpr int RES_CTAS = 6;
+
 static unsigned rows_grid(int64_t n_rows, int G) {
     const int64_t groups_per_cta = AB / G;
     int64_t g = (n_rows + groups_per_cta - 1) / groups_per_cta;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)g_num_sms * RES_CTAS));
 }
 
 template <class T>
@@ -429,43 +440,74 @@ static Mat<float> mat0f(const BsrT<T>& A, const float* v) { return Mat<float>{A.
 
 template <class TI, class TO>
 __global__ void k_cvt(const TI* __restrict__ in, TO* __restrict__ out, int64_t n, const KrylovRec* rec) {
+    pdl_enter();
     if (rec && rec->done) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (TO)in[i];
 }
 
-static unsigned cvt_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+static unsigned cvt_grid(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g_num_sms * RES_CTAS));
+}
 static Mat<float> matf(const DevPat& p, const float* v) { return Mat<float>{p.n_rows, p.row_ptr, p.col_idx, v, nullptr}; }
 
-template <class T>
-static void cheb(int bs, const Mat<T>& A, const T* dinv, const T* b, const T* xi, T* xo, T* d, const float* coef_l,
-                 int step, const KrylovRec* rec, cudaStream_t s) {
-    const float* cf = coef_l + step * 3;
-    switch (bs) {
-        case 2: k_cheb<2, 4, T><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, dinv, b, xi, xo, d, cf, step, rec); break;
-        case 3: k_cheb<3, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, cf, step, rec); break;
-        case 6: k_cheb<6, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, dinv, b, xi, xo, d, cf, step, rec); break;
+// Lanes per block row (G): about two blocks per lane, and enough lanes in total to keep the SMs
+// busy on short levels (few rows: up to a warp per row, but no more lanes than blocks).
+static int lanes_for(int64_t n_rows, double avg_blocks) {
+    auto floor2 = [](double v) { int g = 1; while (2 * g <= v) g *= 2; return g; };
+    auto ceil2 = [](double v) { int g = 1; while (g < v) g *= 2; return g; };
+    int g = std::max(2, std::min(32, floor2(avg_blocks / 2.0)));
+    if (n_rows * g < 32768) g = std::max(g, std::min({32, ceil2(32768.0 / std::max<int64_t>(1, n_rows)), ceil2(avg_blocks)}));
+    return g;
+}
+
+#define EP_G_SWITCH(G, CALL)                  \
+    switch (G) {                              \
+        case 2: { constexpr int GG = 2; CALL; } break;   \
+        case 4: { constexpr int GG = 4; CALL; } break;   \
+        case 8: { constexpr int GG = 8; CALL; } break;   \
+        case 16: { constexpr int GG = 16; CALL; } break; \
+        default: { constexpr int GG = 32; CALL; } break; \
     }
+
+template <class T>
+static void cheb(int bs, int g, const Mat<T>& A, const T* dinv, const T* b, const T* xi, T* xo, T* d,
+                 const float* coef_l, int step, const KrylovRec* rec, cudaStream_t s) {
+    const float* cf = coef_l + step * 3;
+#define EP_CHEB(RB) EP_G_SWITCH(g, launch_pdl(k_cheb<RB, GG, T>, dim3(rows_grid(A.n_rows, GG)), dim3(AB), 0, s, A, dinv, \
+                                              b, xi, xo, d, cf, step, rec))
+    switch (bs) {
+        case 2: EP_CHEB(2) break;
+        case 3: EP_CHEB(3) break;
+        case 6: EP_CHEB(6) break;
+    }
+#undef EP_CHEB
 }
 template <class T>
-static void resid(int bs, const Mat<T>& A, const T* b, const T* x, T* r, const KrylovRec* rec, cudaStream_t s) {
+static void resid(int bs, int g, const Mat<T>& A, const T* b, const T* x, T* r, const KrylovRec* rec, cudaStream_t s) {
+#define EP_RESID(RB) EP_G_SWITCH(g, launch_pdl(k_resid<RB, GG, T>, dim3(rows_grid(A.n_rows, GG)), dim3(AB), 0, s, A, b, \
+                                               x, r, rec))
     switch (bs) {
-        case 2: k_resid<2, 4, T><<<rows_grid(A.n_rows, 4), AB, 0, s>>>(A, b, x, r, rec); break;
-        case 3: k_resid<3, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, b, x, r, rec); break;
-        case 6: k_resid<6, 8, T><<<rows_grid(A.n_rows, 8), AB, 0, s>>>(A, b, x, r, rec); break;
+        case 2: EP_RESID(2) break;
+        case 3: EP_RESID(3) break;
+        case 6: EP_RESID(6) break;
     }
+#undef EP_RESID
 }
 template <class TX, class TY>
 static void mv(const DevPat& p, const float* v, const TX* x, TY* y, int add, const KrylovRec* rec, cudaStream_t s) {
     const Mat<float> M = matf(p, v);
+#define EP_MV(RB, CB) EP_G_SWITCH(p.g, launch_pdl(k_mv<RB, CB, GG, TX, TY>, dim3(rows_grid(M.n_rows, GG)), dim3(AB), 0, \
+                                                  s, M, x, y, add, rec))
     switch (p.rb * 10 + p.cb) {
-        case 23: k_mv<2, 3, 4, TX, TY><<<rows_grid(M.n_rows, 4), AB, 0, s>>>(M, x, y, add, rec); break;
-        case 32: k_mv<3, 2, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
-        case 33: k_mv<3, 3, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
-        case 36: k_mv<3, 6, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
-        case 63: k_mv<6, 3, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
-        case 66: k_mv<6, 6, 8, TX, TY><<<rows_grid(M.n_rows, 8), AB, 0, s>>>(M, x, y, add, rec); break;
+        case 23: EP_MV(2, 3) break;
+        case 32: EP_MV(3, 2) break;
+        case 33: EP_MV(3, 3) break;
+        case 36: EP_MV(3, 6) break;
+        case 63: EP_MV(6, 3) break;
+        case 66: EP_MV(6, 6) break;
     }
+#undef EP_MV
 }
 
 template <class T>
@@ -483,6 +525,7 @@ static cudaError_t up_pat(AmgDev& D, DevPat& d, const HostBsr& h) {
     d.cb = h.cb;
     d.n_rows = h.n_rows;
     d.n_cols = h.n_cols;
+    d.g = lanes_for(h.n_rows, h.n_rows ? (double)h.col_idx.size() / h.n_rows : 1.0);
     cudaError_t e;
     if ((e = up(D, &d.row_ptr, h.row_ptr)) != cudaSuccess) return e;
     return up(D, &d.col_idx, h.col_idx);
@@ -502,6 +545,7 @@ static cudaError_t dvec(AmgDev& D, T** p, int64_t n) {
 }
 
 cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
+    if (num_sms > 0) g_num_sms = num_sms;
     D.n_levels = (int)H.levels.size();
     cudaError_t e;
     std::vector<double> lam(AMG_MAX_LEVELS, 1.0);
@@ -540,6 +584,10 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
     }
     D.nparts = 2 * (num_sms > 0 ? num_sms : 152);
     D.nnzb0 = H.nnzb0;
+    {
+        const int64_t rows0 = H.levels[0].n / H.levels[0].bs;
+        D.g0 = lanes_for(rows0, rows0 ? (double)H.nnzb0 / rows0 : 1.0);
+    }
     if ((e = dvec(D, &D.lam, AMG_MAX_LEVELS)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.coef, AMG_MAX_LEVELS * AMG_CHEB_DEGREE * 3)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw, 2)) != cudaSuccess) return e;
@@ -705,6 +753,7 @@ cudaError_t amg_refresh(AmgDev& D, const BsrF& A0, const float* minv0, int galer
 // 1-level hierarchy: out = Ainv in, FP32 inverse applied to FP64 vectors
 __global__ void __launch_bounds__(AB) k_dense_d(const float* __restrict__ Ainv, int64_t n, const double* __restrict__ b,
                                                  double* __restrict__ x, const KrylovRec* rec) {
+    pdl_enter();
     if (rec && rec->done) return;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -726,25 +775,25 @@ static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* 
     const int bs0 = A0.dim;
     const float* cf0 = D.coef;
     // level 0: pre-smoothing from zero, residual, restriction
-    cheb<float>(bs0, M0, D.minv0, b0, nullptr, l0.x2, l0.d, cf0, 0, rec, s);
-    cheb<float>(bs0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
-    resid<float>(bs0, M0, b0, x0, l0.r, rec, s);
+    cheb<float>(bs0, D.g0, M0, D.minv0, b0, nullptr, l0.x2, l0.d, cf0, 0, rec, s);
+    cheb<float>(bs0, D.g0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
+    resid<float>(bs0, D.g0, M0, b0, x0, l0.r, rec, s);
     mv<float, float>(l0.R, l0.Rvals, l0.r, D.lv[1].b, 0, rec, s);
     D.launches += 4;
     // coarse levels (FP32), descending
     for (int l = 1; l < L - 1; ++l) {
         AmgDevLevel& v = D.lv[l];
         const Mat<float> A = matf(v.A, v.Avals);
-        cheb<float>(v.bs, A, v.dinv, v.b, nullptr, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
-        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
-        resid<float>(v.bs, A, v.b, v.x, v.r, rec, s);
+        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, nullptr, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
+        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
+        resid<float>(v.bs, v.A.g, A, v.b, v.x, v.r, rec, s);
         mv<float, float>(v.R, v.Rvals, v.r, D.lv[l + 1].b, 0, rec, s);
         D.launches += 4;
     }
     {
         AmgDevLevel& c = D.lv[L - 1];
         const unsigned g = (unsigned)((c.n * 32 + AB - 1) / AB);
-        k_dense<<<g, AB, 0, s>>>(c.dense_inv, c.n, c.b, c.x, rec);
+        launch_pdl(k_dense, dim3(g), dim3(AB), 0, s, c.dense_inv, c.n, c.b, c.x, rec);
         D.launches += 1;
     }
     // ascending
@@ -752,13 +801,13 @@ static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* 
         AmgDevLevel& v = D.lv[l];
         const Mat<float> A = matf(v.A, v.Avals);
         mv<float, float>(v.P, v.Pvals, D.lv[l + 1].x, v.x, 1, rec, s);
-        cheb<float>(v.bs, A, v.dinv, v.b, v.x, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
-        cheb<float>(v.bs, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
+        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, v.x, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
+        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
         D.launches += 3;
     }
     mv<float, float>(l0.P, l0.Pvals, D.lv[1].x, x0, 1, rec, s);
-    cheb<float>(bs0, M0, D.minv0, b0, x0, l0.x2, l0.d, cf0, 0, rec, s);
-    cheb<float>(bs0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
+    cheb<float>(bs0, D.g0, M0, D.minv0, b0, x0, l0.x2, l0.d, cf0, 0, rec, s);
+    cheb<float>(bs0, D.g0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
     D.launches += 3;
     return cudaGetLastError();
 }
@@ -768,13 +817,13 @@ cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* in, double* out
     AmgDevLevel& l0 = D.lv[0];
     if (D.n_levels == 1) {
         const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
-        k_dense_d<<<g, AB, 0, s>>>(l0.dense_inv, l0.n, in, out, rec);
+        launch_pdl(k_dense_d, dim3(g), dim3(AB), 0, s, l0.dense_inv, l0.n, in, out, rec);
         D.launches += 1;
         return cudaGetLastError();
     }
-    k_cvt<double, float><<<cvt_grid(l0.n), 256, 0, s>>>(in, l0.b, l0.n, rec);
+    launch_pdl(k_cvt<double, float>, dim3(cvt_grid(l0.n)), dim3(256), 0, s, in, l0.b, l0.n, rec);
     cudaError_t e = vcycle(D, A0, l0.b, l0.x, rec, s);
-    k_cvt<float, double><<<cvt_grid(l0.n), 256, 0, s>>>(l0.x, out, l0.n, rec);
+    launch_pdl(k_cvt<float, double>, dim3(cvt_grid(l0.n)), dim3(256), 0, s, l0.x, out, l0.n, rec);
     D.launches += 2;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -784,7 +833,7 @@ cudaError_t amg_apply(AmgDev& D, const BsrF& A0, const float* in, float* out, co
     AmgDevLevel& l0 = D.lv[0];
     if (D.n_levels == 1) {
         const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
-        k_dense<<<g, AB, 0, s>>>(l0.dense_inv, l0.n, in, out, rec);
+        launch_pdl(k_dense, dim3(g), dim3(AB), 0, s, l0.dense_inv, l0.n, in, out, rec);
         D.launches += 1;
         return cudaGetLastError();
     }

@@ -60,6 +60,7 @@ bool amg_invert_dense(std::vector<double>& M, int n);
 // of the FP64 Krylov iteration it serves.
 struct DevPat {
     int rb = 0, cb = 0;
+    int g = 8;                         // lanes per block row in the row kernels (from the average row length)
     int64_t n_rows = 0, n_cols = 0;
     int32_t *row_ptr = nullptr, *col_idx = nullptr;
 };
@@ -87,6 +88,7 @@ struct AmgDev {
     const float* K0 = nullptr;         // level-0 values of the V-cycle (K32, or the mixed path's FP32 tangent)
     const float* minv0 = nullptr;      // their block-Jacobi inverse
     int64_t nnzb0 = 0;
+    int g0 = 4;                        // lanes per block row of the level-0 matrix
     double* pw = nullptr;              // power-iteration work [2][n0] (FP64)
     float* pwf = nullptr;              // power-iteration work [2][n1] (FP32)
     double* pw_part = nullptr;

@@ -137,6 +137,16 @@ bool make_matconst(const ep_material& m, int dim, MatConst& out, std::string& er
 
 // Smallest relative tolerance asked of the FP32 inner Krylov solve of the mixed path.
 constexpr double MIXED_ETA_MIN = 1e-5;
+// A Newton iteration on the FP32 tangent that reduces the FP64 residual by less than this factor
+// ends the FP32 phase: the rest of the load path uses the FP64 tangent and solve.  Near a limit
+// load the tangent is so ill-conditioned that its FP32 rounding (relative 2^-24 per entry) moves
+// the soft modes by O(1), and Newton on it stalls.
+constexpr double MIXED_STALL_RATIO = 0.5;
+// Newton on an FP32 tangent contracts linearly, by about kappa * 2^-24 per iteration (kappa the
+// tangent's condition number), where FP64 Newton with the adaptive forcing term contracts by about
+// its Krylov tolerance (1e-3 .. 1e-2).  When an FP32 iteration of the mixed path contracts the FP64
+// residual by less than this factor, the rest of the load step uses the FP64 tangent and solve.
+constexpr double MIXED_RHO_MAX = 0.02;
 
 struct Ctx {
     std::string err;
@@ -183,6 +193,8 @@ struct Ctx {
     AmgDev amg;
     bool amg_built = false;
     bool amg_elastic = true;     // the AMG coarse operators currently come from K_elast
+    int64_t amg_np = -1;         // plastic points of the tangent the coarse operators were last built from
+    bool mixed_fallback = false; // the mixed path has switched to FP64 for the rest of the load path
     double amg_setup_ms = 0.0;
     std::vector<void*> allocs;
 };
@@ -662,7 +674,10 @@ ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_
     cudaSetDevice(c->device);
     CK(cudaMemcpyAsync(dst, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (field == EP_U) c->n_committed = 0;   // no extrapolation history across a reset
+    if (field == EP_U) {
+        c->n_committed = 0;      // no extrapolation history across a reset
+        c->mixed_fallback = false;
+    }
     return EP_OK;
 }
 
@@ -788,6 +803,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     const BsrF Af = bsr_dev(c, (const float*)c->K32);
     c->profile = o.profile;
     c->kw.profile = o.profile;
+    c->kw.verbose = c->verbose;
     for (int k = 0; k < n_steps; ++k) {
         const auto t_step0 = std::chrono::steady_clock::now();
         ep_step_report rep{};
@@ -813,12 +829,15 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         double rel = 0.0, rnorm_prev = -1.0;
         int it = 0;
         bool converged = false;
+        bool use32 = false;      // this iteration's tangent and solve in FP32
+        bool fp64_step = false;  // the rest of this step in FP64 (an FP32 iteration contracted poorly)
         for (;;) {
+            use32 = mixed && !c->mixed_fallback && !fp64_step;
             CK(cudaEventRecord(c->ev[0], s));
-            st = assemble(c, c->u_it, split, true, mixed);
+            st = assemble(c, c->u_it, split, true, use32);
             if (st != EP_OK) break;
             CK(cudaEventRecord(c->ev[1], s));
-            CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, mixed ? c->r32 : nullptr, c->n_dof, c->kw.part,
+            CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, use32 ? c->r32 : nullptr, c->n_dof, c->kw.part,
                             c->kw.nparts, c->norms, s));
             c->launches += 2;
             rep.n_assemble += 1;
@@ -865,22 +884,45 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 eta = std::min(1e-2, std::max(eta_ew, eta_min));
                 eta = std::max(eta, 1e-14);
             }
+            // FP32 phase of the mixed path: if the last FP32 Newton step barely reduced the FP64
+            // residual, the FP32 tangent is too coarse here; this and later steps use FP64, starting
+            // with an FP64 assembly at the same iterate (this iteration's tangent is FP32)
+            // (the tangent of this iteration is already assembled: a poor contraction switches the next
+            // iteration to FP64, a stall this one)
+            if (use32 && rnorm_prev > 0.0 && rnorm > MIXED_RHO_MAX * rnorm_prev) fp64_step = true;
+            if (use32 && rnorm_prev > 0.0 && rnorm > MIXED_STALL_RATIO * rnorm_prev) {
+                c->mixed_fallback = true;
+                if (c->verbose) std::fprintf(stderr, "[ep] step %d: FP32 tangent stalled, FP64 from here\n", k);
+                continue;
+            }
             // an FP32 inner solve cannot go much below FP32 rounding; Newton (FP64 residual) refines further
-            if (mixed) eta = std::max(eta, MIXED_ETA_MIN);
+            if (use32) eta = std::max(eta, MIXED_ETA_MIN);
             rnorm_prev = rnorm;
             CK(cudaEventRecord(c->ev[2], s));
-            // coarse operators from the current tangent unless it is exactly K_elast
-            const bool tangent_elastic = split && *c->counter_host == 0;
-            c->kw.galerkin = (tangent_elastic && c->amg_elastic) ? 0 : 1;
-            if (c->kw.galerkin) c->amg_elastic = tangent_elastic;
+            // Coarse operators: rebuilt (Galerkin, from the current tangent) at the first Newton
+            // iteration of a step and whenever the plastic set changed by more than 5% of the points
+            // since the last rebuild; otherwise the last ones are reused (a preconditioner need not
+            // follow the tangent exactly; level 0 always is the current tangent).  An elastic
+            // tangent is K_elast, whose coarse operators are kept from the setup.
+            const int64_t np_now = (int64_t)*c->counter_host;
+            const bool tangent_elastic = split && np_now == 0;
+            if (tangent_elastic) c->kw.galerkin = c->amg_elastic ? 0 : 1;
+            else c->kw.galerkin = (c->amg_elastic || it == 0 || std::llabs(np_now - c->amg_np) * 20 > c->n_int) ? 1 : 0;
+            if (c->kw.galerkin) {
+                c->amg_elastic = tangent_elastic;
+                c->amg_np = np_now;
+            }
             int kits = 0, kst = 0;
             double krel = 0.0;
             // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
             // nonassociated model
             const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
-            if (mixed) {
+            if (use32) {
+                rep.newton_its_fp32 += 1;
+                // an FP32 solve that needs far more iterations than usual is stagnating on rounding
+                const int maxit32 = std::min(o.krylov_maxit, std::max(300, 4 * c->kw.last_its));
                 CK(krylov_precond(Af, c->kw, o.precond, s));
-                CK(krylov_solve(Af, c->kw, c->r32, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+                CK(krylov_solve(Af, c->kw, c->r32, m_it, eta, maxit32, s, &kits, &krel, &kst));
             } else {
                 CK(krylov_precond(A, c->kw, o.precond, s));
                 CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
@@ -904,13 +946,21 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 c->err = "Krylov: non-finite residual";
                 break;
             }
+            if (kst != EP_OK && use32) {
+                // the FP32 inner solve stagnated: FP32 is too coarse for this tangent; keep the step if
+                // it made progress, and continue the load path in FP64
+                c->mixed_fallback = true;
+                if (c->verbose) std::fprintf(stderr, "[ep] step %d: FP32 solve stagnated, FP64 from here\n", k);
+                if (!(krel < 0.5)) continue;   // no progress: redo this iteration in FP64
+                kst = EP_OK;
+            }
             if (kst != EP_OK && !(krel < 0.5)) {
                 // accept a partially converged solve as an inexact Newton step; fail only if it made no progress
                 st = EP_ERR_KRYLOV;
                 c->err = "Krylov: no progress (relative residual " + std::to_string(krel) + ")";
                 break;
             }
-            if (mixed) CK(vec_axpy_f32(c->u_it, c->kw.f.x, c->n_dof, s));
+            if (use32) CK(vec_axpy_f32(c->u_it, c->kw.f.x, c->n_dof, s));
             else CK(vec_axpy(c->u_it, 1.0, c->kw.d.x, c->n_dof, s));
             c->launches += 1;
             CK(cudaEventSynchronize(c->ev[3]));

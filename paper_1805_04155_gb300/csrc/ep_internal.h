@@ -184,8 +184,10 @@ struct KrylovWork {
     int use_amg;             // set by krylov_precond: 1 when the current preconditioner is the AMG V-cycle
     int gm_m;                // GMRES restart length (<= GM_M)
     int galerkin;            // 1: recompute the AMG coarse operators from the current matrix in krylov_precond
+    int last_its;            // iterations of the previous solve: sizes the first chunk of launches of the next
     // instrumentation
     int profile;             // 1: CUDA events around every SpMV launch
+    int verbose;             // 2: per-cycle host enqueue / wait times on stderr
     int launches;            // kernels launched by the solver (accumulates)
     int spmv_n;              // SpMV launches that did work (profile = 1)
     double spmv_ms;          // their summed duration

@@ -22,11 +22,14 @@
 // record says the solve has finished, so the host may enqueue iterations in
 // chunks and poll rarely.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 
 #include "amg.h"
 #include "ep_internal.h"
+#include "pdl.cuh"
 
 namespace ep {
 
@@ -85,6 +88,7 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 template <int D, int G, class T>
 __global__ void __launch_bounds__(VB) k_spmv(BsrT<T> A, const T* __restrict__ x, T* __restrict__ y,
                                               const T* __restrict__ dv, double* part, const KrylovRec* rec) {
+    pdl_enter();
     __shared__ double sh[32];
     if (rec && rec->done) return;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,6 +254,7 @@ __device__ __forceinline__ double shadow_value(int64_t i, int seed) {
 // For the warm start q must hold A x.
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_init(KArgs<T> a, const T* __restrict__ b, int bicg, int warm, int seed) {
+    pdl_enter();
     __shared__ double sh[32];
     T s1 = T(0), s2 = T(0);
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
@@ -304,6 +309,7 @@ __device__ __forceinline__ bool check_done(const KArgs<T>& a, int it, double rz,
 // CG: p = z + beta p
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_cg_p(KArgs<T> a, int it) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double rz = sum_partials(PART(P_RZ), a.nparts, sh);
@@ -320,6 +326,7 @@ __global__ void __launch_bounds__(VB) k_cg_p(KArgs<T> a, int it) {
 // CG: alpha = rho / (p.q); x += alpha p; r -= alpha q; z = M^-1 r; partials r.z, r.r
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_cg_update(KArgs<T> a, int it) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double pq = sum_partials(PART(P_PQ), a.nparts, sh);
@@ -354,6 +361,7 @@ __global__ void __launch_bounds__(VB) k_cg_update(KArgs<T> a, int it) {
 template <class T>
 __global__ void __launch_bounds__(VB) k_dot(KArgs<T> a, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
                                              int slot) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     T s1 = T(0);
@@ -366,6 +374,7 @@ __global__ void __launch_bounds__(VB) k_dot(KArgs<T> a, const T* __restrict__ x,
 // BiCGStab: p = r + beta (p - omega v); phat = M^-1 p
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_bicg_p(KArgs<T> a, int it) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double rho = sum_partials(PART(P_RZ), a.nparts, sh);
@@ -396,6 +405,7 @@ __global__ void __launch_bounds__(VB) k_bicg_p(KArgs<T> a, int it) {
 // BiCGStab: alpha = rho / (rhat.v); s = r - alpha v; shat = M^-1 s
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_bicg_s(KArgs<T> a, int it) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double rv = sum_partials(PART(P_PQ), a.nparts, sh);
@@ -420,6 +430,7 @@ __global__ void __launch_bounds__(VB) k_bicg_s(KArgs<T> a, int it) {
 // BiCGStab: omega = (t.s)/(t.t); x += alpha phat + omega shat; r = s - omega t; partials rhat.r, r.r
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_bicg_x(KArgs<T> a, int it) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     const double ts = sum_partials(PART(P_TS), a.nparts, sh);
@@ -447,6 +458,7 @@ __global__ void __launch_bounds__(VB) k_bicg_x(KArgs<T> a, int it) {
 // Two dot partials (t.s and t.t) after the second SpMV of BiCGStab.
 template <class T>
 __global__ void __launch_bounds__(VB) k_dot2(KArgs<T> a, int64_t n) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     T s1 = T(0), s2 = T(0);
@@ -491,7 +503,9 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
     w = KrylovWork{};
     w.n = n_rows * dim;
     w.block = VB;
-    w.grid = 2 * (num_sms > 0 ? num_sms : 152);
+    // one resident wave of 512-thread CTAs (<= 42 registers: 3 per SM); the SpMV and the vector kernels
+    // are latency-bound gathers and streams, and a third CTA per SM adds the bytes in flight they need
+    w.grid = 3 * (num_sms > 0 ? num_sms : 152);
     w.nparts = w.grid;
     w.hist_len = maxit_cap + 2;
     w.gm_m = 30;
@@ -553,8 +567,8 @@ cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t 
 template <int D, class T>
 static void launch_spmv(const BsrT<T>& A, const T* x, T* y, const T* dv, double* part, const KrylovRec* rec, int grid,
                         cudaStream_t s) {
-    if (D == 2) k_spmv<2, 4, T><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
-    else k_spmv<3, 8, T><<<grid, VB, 0, s>>>(A, x, y, dv, part, rec);
+    if (D == 2) launch_pdl(k_spmv<2, 4, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
+    else launch_pdl(k_spmv<3, 8, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
 }
 
 // AMG V-cycle out = M^-1 in, in the solver's precision
@@ -589,8 +603,16 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
     a.amg = (w.use_amg && w.amg) ? 1 : 0;
     const int grid = w.grid;
     const bool bicg = (method == 2);
-    const int chunk = 16;   // iterations enqueued between two polls of the device record
+    // Iterations enqueued between two polls of the device record: the first chunk covers the
+    // previous solve's count (consecutive Newton systems need similar counts), later ones are
+    // short, so few launches run after convergence (each costs a few microseconds even when its
+    // CTAs exit at once) and few polls stall the GPU.
+    int chunk = std::max(4, std::min(64, w.last_its + 2));
     const int max_restarts = bicg ? 8 : 0;
+    // FP32: the recursively updated residual can drift from b - A x by O(u32) times the largest
+    // intermediate residual; a solve that reports convergence is restarted once from its x, which
+    // recomputes the true residual (and continues only if that one misses the tolerance)
+    int n_verify = sizeof(T) == 4 ? 1 : 0;
     int total_its = 0;
     for (int restart = 0;; ++restart) {
     a.cold = (restart == 0);
@@ -599,11 +621,11 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
         launch_spmv<D, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
         w.launches += 1;
     }
-    k_init<D, T><<<grid, VB, 0, s>>>(a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
+    launch_pdl(k_init<D, T>, dim3(grid), dim3(VB), 0, s, a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
     w.launches += 1;
     if (a.amg && !bicg) {   // z = M^-1 r0, then (r, z)
         amg_apply_t(w, A, vv.r, vv.z, w.rec, s);
-        k_dot<T><<<grid, VB, 0, s>>>(a, vv.r, vv.z, w.n, P_RZ);
+        launch_pdl(k_dot<T>, dim3(grid), dim3(VB), 0, s, a, vv.r, vv.z, w.n, P_RZ);
         w.launches += 1;
     }
     int it = 0;
@@ -612,31 +634,33 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
         const int stop = std::min(it + chunk, a.maxit + 1);
         int nev = 0;
         for (; it < stop; ++it) {
+            // profiling events: as many iterations of the chunk as the event array holds
+            const bool ev_ok = w.profile && nev + (bicg ? 4 : 2) <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
             if (!bicg) {
-                k_cg_p<D, T><<<grid, VB, 0, s>>>(a, it);
-                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                launch_pdl(k_cg_p<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D, T>(A, vv.p, vv.q, vv.p, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
-                if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                k_cg_update<D, T><<<grid, VB, 0, s>>>(a, it);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
+                launch_pdl(k_cg_update<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 w.launches += 3;
                 if (a.amg) {
                     amg_apply_t(w, A, vv.r, vv.z, w.rec, s);
-                    k_dot<T><<<grid, VB, 0, s>>>(a, vv.r, vv.z, w.n, P_RZ);
+                    launch_pdl(k_dot<T>, dim3(grid), dim3(VB), 0, s, a, vv.r, vv.z, w.n, P_RZ);
                     w.launches += 1;
                 }
             } else {
-                k_bicg_p<D, T><<<grid, VB, 0, s>>>(a, it);
+                launch_pdl(k_bicg_p<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 if (a.amg) amg_apply_t(w, A, vv.p, vv.phat, w.rec, s);
-                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D, T>(A, vv.phat, vv.v, vv.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
-                if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                k_bicg_s<D, T><<<grid, VB, 0, s>>>(a, it);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
+                launch_pdl(k_bicg_s<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 if (a.amg) amg_apply_t(w, A, vv.s, vv.shat, w.rec, s);
-                if (w.profile) cudaEventRecord(w.ev[nev++], s);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D, T>(A, vv.shat, vv.t, nullptr, nullptr, w.rec, grid, s);
-                if (w.profile) cudaEventRecord(w.ev[nev++], s);
-                k_dot2<T><<<grid, VB, 0, s>>>(a, w.n);
-                k_bicg_x<D, T><<<grid, VB, 0, s>>>(a, it);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
+                launch_pdl(k_dot2<T>, dim3(grid), dim3(VB), 0, s, a, w.n);
+                launch_pdl(k_bicg_x<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 w.launches += 6;
             }
         }
@@ -660,13 +684,19 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
             }
         }
         if (w.rec_host->done || it > a.maxit) break;
+        chunk = 6;
     }
     total_its += w.rec_host->its;
     if (w.rec_host->done == 2 && restart < max_restarts && std::isfinite(w.rec_host->rr) && total_its < maxit) continue;
+    if (w.rec_host->done == 1 && n_verify > 0 && w.rec_host->its > 0 && total_its < maxit) {
+        --n_verify;
+        continue;
+    }
     break;
     }
     const KrylovRec& r = *w.rec_host;
     *its = total_its;
+    w.last_its = total_its;
     *relres = (r.rr0 > 0.0) ? sqrt(r.rr / r.rr0) : 0.0;
     if (r.done == 1) *status = EP_OK;
     else if (!std::isfinite(r.rr)) *status = EP_ERR_NAN;
@@ -709,6 +739,7 @@ struct GArgs {
 // r = P(b - q) (warm) or P b with x = 0 (cold); partial ||r||^2 -> GPART(0)
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_init(GArgs<T> a, const T* __restrict__ b, int warm) {
+    pdl_enter();
     __shared__ double sh[32];
     T s1 = T(0);
     const int64_t n = a.n_rows * D;
@@ -728,6 +759,7 @@ __global__ void __launch_bounds__(VB) k_gm_init(GArgs<T> a, const T* __restrict_
 // beta = ||r||, v_0 = r / beta, g = (beta, 0, ...); convergence test of the cycle start
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_start(GArgs<T> a) {
+    pdl_enter();
     __shared__ double sh[32];
     const double rr = sum_partials(GPART(0), a.nparts, sh);
     const double rr0 = a.cold ? rr : a.rec->rr0;
@@ -755,6 +787,7 @@ __global__ void __launch_bounds__(VB) k_gm_start(GArgs<T> a) {
 // z = M^-1 v_j
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_prec(GArgs<T> a, int j) {
+    pdl_enter();
     if (a.rec->done) return;
     const T* v = a.V + (int64_t)j * a.n_rows * D;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
@@ -765,6 +798,7 @@ __global__ void __launch_bounds__(VB) k_gm_prec(GArgs<T> a, int j) {
 // partials of h_i = (w, v_i), i = 0..j, with w = V[j+1]; grid (nparts, j + 1): CTA (b, i) -> GPART(i)[b]
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_dots(GArgs<T> a, int j) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     const int i = blockIdx.y;
@@ -778,9 +812,48 @@ __global__ void __launch_bounds__(VB) k_gm_dots(GArgs<T> a, int j) {
     if (threadIdx.x == 0) GPART(i)[blockIdx.x] = bsum;
 }
 
+// The same partials from one CTA row (grid = nparts): v_0..v_j are taken MJ at a time, each
+// thread keeping its MJ products in registers (w re-read per group, from L2), and each sum is
+// reduced over the CTA in the same order as block_sum (warp sums in T, warp partials in FP64).
+template <int D, class T, int MJ>
+__global__ void __launch_bounds__(VB) k_gm_dots1(GArgs<T> a, int j) {
+    pdl_enter();
+    __shared__ double sh[MJ][VB / 32];
+    if (a.rec->done) return;
+    const int64_t n = a.n_rows * D;
+    const T* w = a.V + (int64_t)(j + 1) * n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i0 = 0; i0 <= j; i0 += MJ) {
+        T acc[MJ];
+#pragma unroll
+        for (int i = 0; i < MJ; ++i) acc[i] = T(0);
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+            const T wk = w[k];
+            const T* vk = a.V + (int64_t)i0 * n + k;
+#pragma unroll
+            for (int i = 0; i < MJ; ++i)
+                if (i0 + i <= j) acc[i] += wk * vk[(int64_t)i * n];
+        }
+#pragma unroll
+        for (int i = 0; i < MJ; ++i)
+            if (i0 + i <= j) {
+                const T v = warp_sum(acc[i]);
+                if (lane == 0) sh[i][wid] = (double)v;
+            }
+        __syncthreads();
+        if ((int)threadIdx.x < MJ && i0 + (int)threadIdx.x <= j) {
+            double r = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += sh[threadIdx.x][q];
+            GPART(i0 + threadIdx.x)[blockIdx.x] = r;
+        }
+        __syncthreads();
+    }
+}
+
 // w -= sum_i h_i v_i; partial ||w||^2 -> GPART(GM_M + 1); CTA 0 stores H[:, j]
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
+    pdl_enter();
     __shared__ double sh[32];
     __shared__ T h[GM_M];
     if (a.rec->done) return;
@@ -808,6 +881,7 @@ __global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
 // h_{j+1,j} = ||w||, v_{j+1} = w / h; CTA 0: Givens update and convergence test
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_norm(GArgs<T> a, int j, int it_base, int maxit) {
+    pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
     __shared__ double s_h[2];
@@ -869,6 +943,7 @@ __device__ __forceinline__ void gm_solve_y(const GArgs<T>& a, int k, T* y) {
 // x += M^-1 (V_k y), y = R^-1 g (k = its of the cycle); every CTA solves the small triangle itself
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_update(GArgs<T> a, int k) {
+    pdl_enter();
     __shared__ T y[GM_M];
     gm_solve_y(a, k, y);
     const int64_t n = a.n_rows * D;
@@ -895,6 +970,7 @@ __global__ void __launch_bounds__(VB) k_gm_update(GArgs<T> a, int k) {
 // u = V_k y (y = R^-1 g solved redundantly by every CTA)
 template <int D, class T>
 __global__ void __launch_bounds__(VB) k_gm_combine(GArgs<T> a, int k, T* __restrict__ u) {
+    pdl_enter();
     __shared__ T y[GM_M];
     gm_solve_y(a, k, y);
     const int64_t n = a.n_rows * D;
@@ -907,6 +983,7 @@ __global__ void __launch_bounds__(VB) k_gm_combine(GArgs<T> a, int k, T* __restr
 
 template <class T>
 __global__ void k_axpy_plain(T* __restrict__ x, const T* __restrict__ z, int64_t n) {
+    pdl_enter();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += z[i];
 }
@@ -937,58 +1014,84 @@ static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, do
     const bool use_amg = w.use_amg && w.amg;
     int total = 0;
     KrylovRec last{};
+    double rr_prev_end = 0.0;   // residual estimate ||r||^2 at the end of the previous cycle
+    int n_verify = sizeof(T) == 4 ? 1 : 0;   // FP32: re-check a converged estimate once (see solve_t)
     for (int cycle = 0;; ++cycle) {
         a.cold = (cycle == 0);
         if (cycle > 0) {
             launch_spmv<D, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
             w.launches += 1;
         }
-        k_gm_init<D, T><<<grid, VB, 0, s>>>(a, b, cycle > 0 ? 1 : 0);
-        k_gm_start<D, T><<<grid, VB, 0, s>>>(a);
+        launch_pdl(k_gm_init<D, T>, dim3(grid), dim3(VB), 0, s, a, b, cycle > 0 ? 1 : 0);
+        launch_pdl(k_gm_start<D, T>, dim3(grid), dim3(VB), 0, s, a);
         w.launches += 2;
-        int nev = 0;
-        for (int j = 0; j < a.m; ++j) {
-            if (use_amg) amg_apply_t(w, A, a.V + (int64_t)j * w.n, a.z, w.rec, s);
-            else k_gm_prec<D, T><<<grid, VB, 0, s>>>(a, j);
-            const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
-            if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-            launch_spmv<D, T>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
-            if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-            k_gm_dots<D, T><<<dim3(grid, j + 1), VB, 0, s>>>(a, j);
-            k_gm_orth<D, T><<<grid, VB, 0, s>>>(a, j);
-            k_gm_norm<D, T><<<grid, VB, 0, s>>>(a, j, total, maxit);
-            w.launches += 5;
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(w.rec_host, w.rec, sizeof(KrylovRec), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-            return e;
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        last = *w.rec_host;
-        if (w.profile) {
-            for (int j = 0; j < nev / 2 && j < last.its; ++j) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, w.ev[2 * j], w.ev[2 * j + 1]) == cudaSuccess) {
-                    w.spmv_ms += ms;
-                    w.spmv_n += 1;
+        // the cycle's iterations in chunks, polling the device record between chunks (the first
+        // chunk covers the previous solve's count, see solve_t)
+        int chunk = std::max(4, std::min(a.m, w.last_its + 2 - total));
+        double t_enq = 0.0, t_wait = 0.0;
+        for (int j0 = 0; j0 < a.m; j0 += chunk, chunk = 6) {
+            const auto t0 = std::chrono::steady_clock::now();
+            const int j1 = std::min(a.m, j0 + chunk);
+            int nev = 0;
+            for (int j = j0; j < j1; ++j) {
+                if (use_amg) amg_apply_t(w, A, a.V + (int64_t)j * w.n, a.z, w.rec, s);
+                else launch_pdl(k_gm_prec<D, T>, dim3(grid), dim3(VB), 0, s, a, j);
+                const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
+                launch_spmv<D, T>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
+                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
+                launch_pdl(k_gm_dots1<D, T, sizeof(T) == 8 ? 4 : 8>, dim3(grid), dim3(VB), 0, s, a, j);
+                launch_pdl(k_gm_orth<D, T>, dim3(grid), dim3(VB), 0, s, a, j);
+                launch_pdl(k_gm_norm<D, T>, dim3(grid), dim3(VB), 0, s, a, j, total, maxit);
+                w.launches += 5;
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            if ((e = cudaMemcpyAsync(w.rec_host, w.rec, sizeof(KrylovRec), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return e;
+            const auto t1 = std::chrono::steady_clock::now();
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            t_enq += std::chrono::duration<double, std::milli>(t1 - t0).count();
+            t_wait += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+            last = *w.rec_host;
+            if (w.profile) {
+                for (int q = 0; q < nev / 2 && j0 + q < last.its; ++q) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, w.ev[2 * q], w.ev[2 * q + 1]) == cudaSuccess) {
+                        w.spmv_ms += ms;
+                        w.spmv_n += 1;
+                    }
                 }
             }
+            if (last.done) break;
         }
+        if (w.verbose > 1)
+            std::fprintf(stderr, "[ep]   gmres cycle %d: its %d, host enqueue %.3f ms, wait %.3f ms\n", cycle,
+                         last.its, t_enq, t_wait);
         if (last.its > 0) {
             if (use_amg) {
-                k_gm_combine<D, T><<<grid, VB, 0, s>>>(a, last.its, vv.q);
+                launch_pdl(k_gm_combine<D, T>, dim3(grid), dim3(VB), 0, s, a, last.its, vv.q);
                 amg_apply_t(w, A, vv.q, vv.z, nullptr, s);
-                k_axpy_plain<T><<<grid, VB, 0, s>>>(vv.x, vv.z, w.n);
+                launch_pdl(k_axpy_plain<T>, dim3(grid), dim3(VB), 0, s, vv.x, vv.z, w.n);
                 w.launches += 2;
             } else {
-                k_gm_update<D, T><<<grid, VB, 0, s>>>(a, last.its);
+                launch_pdl(k_gm_update<D, T>, dim3(grid), dim3(VB), 0, s, a, last.its);
                 w.launches += 1;
             }
         }
         total += last.its;
+        if (last.done == 1 && n_verify > 0 && last.its > 0) {   // a new cycle recomputes b - A x
+            --n_verify;
+            continue;
+        }
         if (last.done != 4) break;           // converged, breakdown, non-finite or cap
+        // an FP32 solve whose restart cycle gained less than 10% has reached what its rounding
+        // allows on this matrix: stop (the caller treats it as an inexact or failed solve)
+        if (sizeof(T) == 4 && last.rr > 0.81 * (cycle == 0 ? last.rr0 : rr_prev_end)) break;
+        rr_prev_end = last.rr;
     }
     *its = total;
+    w.last_its = total;
     *relres = last.rr0 > 0.0 ? sqrt(last.rr / last.rr0) : 0.0;
     if (last.done == 1) *status = EP_OK;
     else if (!std::isfinite(last.rr)) *status = EP_ERR_NAN;

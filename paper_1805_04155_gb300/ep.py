@@ -66,7 +66,8 @@ class ep_step_report(C.Structure):
                 ("rel_resid", C.c_double), ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("t_step_ms", C.c_double), ("status", C.c_int32), ("launches", C.c_int32),
                 ("n_assemble", C.c_int32), ("n_spmv", C.c_int32), ("t_assemble_kernel_ms", C.c_double),
-                ("t_spmv_kernel_ms", C.c_double), ("n_plastic_assembled", C.c_int64)]
+                ("t_spmv_kernel_ms", C.c_double), ("n_plastic_assembled", C.c_int64),
+                ("newton_its_fp32", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ep_info(C.Structure):
