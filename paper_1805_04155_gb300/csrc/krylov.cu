@@ -59,12 +59,27 @@ __device__ __forceinline__ double block_sum(T v, double* sh) {
     return r;
 }
 
+// Sum of the n partials of one warp-lane stripe (lane, lane + 32, ...), loaded 8 at a time so the
+// L2 latencies overlap; the same order in every warp.
+__device__ __forceinline__ double lane_partials(const double* __restrict__ part, int n, int lane) {
+    double v = 0.0;
+    for (int i0 = 0; i0 < n; i0 += 256) {
+        double t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q * 32 + lane;
+            t[q] = i < n ? part[i] : 0.0;
+        }
+        v += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+    }
+    return v;
+}
+
 // Sum of n partials in a fixed order; identical in every thread of every CTA.
 __device__ __forceinline__ double sum_partials(const double* part, int n, double* sh) {
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+        double v = lane_partials(part, n, threadIdx.x);
         v = warp_sum(v);
         if (threadIdx.x == 0) sh[0] = v;
     }
@@ -567,7 +582,9 @@ cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t 
 template <int D, class T>
 static void launch_spmv(const BsrT<T>& A, const T* x, T* y, const T* dv, double* part, const KrylovRec* rec, int grid,
                         cudaStream_t s) {
-    if (D == 2) launch_pdl(k_spmv<2, 4, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
+    // FP64: 2 lanes per 2x2-block row (fewer idle lanes and cross-lane FP64 adds on the FP64 pipe)
+    if (D == 2 && sizeof(T) == 8) launch_pdl(k_spmv<2, 2, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
+    else if (D == 2) launch_pdl(k_spmv<2, 4, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
     else launch_pdl(k_spmv<3, 8, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
 }
 
@@ -812,12 +829,39 @@ __global__ void __launch_bounds__(VB) k_gm_dots(GArgs<T> a, int j) {
     if (threadIdx.x == 0) GPART(i)[blockIdx.x] = bsum;
 }
 
-// The same partials from one CTA row (grid = nparts): v_0..v_j are taken MJ at a time, each
-// thread keeping its MJ products in registers (w re-read per group, from L2), and each sum is
-// reduced over the CTA in the same order as block_sum (warp sums in T, warp partials in FP64).
+// Sum of MJ per-lane values over a warp by recursive halving: at each of the first log2(MJ) levels
+// a lane keeps half of its slots and adds its partner's copies of them, then the remaining levels
+// sum within lane groups.  On return lane (s << (5 - log2 MJ)) holds slot s's total.  FP64 adds
+// per lane: MJ - 1 + 5 - log2 MJ instead of 5 MJ for MJ separate butterflies (an FP64 warp add
+// occupies this GPU's FP64 pipe for 16 cycles).
+template <int MJ, class T>
+__device__ __forceinline__ T warp_multi_sum(const T (&v)[MJ], int lane) {
+    T cur[MJ];
+#pragma unroll
+    for (int q = 0; q < MJ; ++q) cur[q] = v[q];
+    int off = 16;
+#pragma unroll
+    for (int width = MJ; width > 1; width /= 2, off >>= 1) {
+        const int half = width / 2;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const T keep = up ? cur[q + half] : cur[q];
+            const T send = up ? cur[q] : cur[q + half];
+            cur[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    for (; off > 0; off >>= 1) cur[0] += __shfl_xor_sync(0xffffffffu, cur[0], off);
+    return cur[0];
+}
+
+// The same partials from one launch (grid <= nparts; slots of absent CTAs are zeroed): v_0..v_j
+// are taken MJ at a time, each thread keeping its MJ products in registers (w re-read per group,
+// from L2), each group reduced over the warp by warp_multi_sum and over the CTA's warps in FP64.
 template <int D, class T, int MJ>
 __global__ void __launch_bounds__(VB) k_gm_dots1(GArgs<T> a, int j) {
     pdl_enter();
+    constexpr int LG = (MJ == 2 ? 1 : MJ == 4 ? 2 : MJ == 8 ? 3 : MJ == 16 ? 4 : 5);
     __shared__ double sh[MJ][VB / 32];
     if (a.rec->done) return;
     const int64_t n = a.n_rows * D;
@@ -834,17 +878,15 @@ __global__ void __launch_bounds__(VB) k_gm_dots1(GArgs<T> a, int j) {
             for (int i = 0; i < MJ; ++i)
                 if (i0 + i <= j) acc[i] += wk * vk[(int64_t)i * n];
         }
-#pragma unroll
-        for (int i = 0; i < MJ; ++i)
-            if (i0 + i <= j) {
-                const T v = warp_sum(acc[i]);
-                if (lane == 0) sh[i][wid] = (double)v;
-            }
+        const T r = warp_multi_sum<MJ>(acc, lane);
+        if ((lane & ((32 >> LG) - 1)) == 0) sh[lane >> (5 - LG)][wid] = (double)r;
         __syncthreads();
         if ((int)threadIdx.x < MJ && i0 + (int)threadIdx.x <= j) {
-            double r = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += sh[threadIdx.x][q];
-            GPART(i0 + threadIdx.x)[blockIdx.x] = r;
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
+            double* slot = GPART(i0 + threadIdx.x);
+            slot[blockIdx.x] = t;
+            for (int q = blockIdx.x + gridDim.x; q < a.nparts; q += gridDim.x) slot[q] = 0.0;
         }
         __syncthreads();
     }
@@ -857,20 +899,31 @@ __global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
     __shared__ double sh[32];
     __shared__ T h[GM_M];
     if (a.rec->done) return;
-    for (int i = 0; i <= j; ++i) {
-        const double v = sum_partials(GPART(i), a.nparts, sh);
-        if (threadIdx.x == 0) {
-            h[i] = (T)v;
-            if (blockIdx.x == 0) a.H[i * GM_M + j] = v;
+    {
+        // h_i, i = 0..j: warp q reduces slots q, q + 16, ... (each in the fixed order of lane_partials)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int i = wid; i <= j; i += nw) {
+            const double v = warp_sum(lane_partials(GPART(i), a.nparts, lane));
+            if (lane == 0) {
+                h[i] = (T)v;
+                if (blockIdx.x == 0) a.H[i * GM_M + j] = v;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     const int64_t n = a.n_rows * D;
     T* w = a.V + (int64_t)(j + 1) * n;
     T s1 = T(0);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        T wk = w[k];
-        for (int i = 0; i <= j; ++i) wk -= h[i] * a.V[(int64_t)i * n + k];
+        // two interleaved sums: half the dependent FMA chain
+        T c0 = T(0), c1 = T(0);
+        int i = 0;
+        for (; i + 1 <= j; i += 2) {
+            c0 += h[i] * a.V[(int64_t)i * n + k];
+            c1 += h[i + 1] * a.V[(int64_t)(i + 1) * n + k];
+        }
+        if (i <= j) c0 += h[i] * a.V[(int64_t)i * n + k];
+        const T wk = w[k] - (c0 + c1);
         w[k] = wk;
         s1 += wk * wk;
     }
@@ -893,14 +946,18 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs<T> a, int j, int it_base, 
     const double hn = s_h[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double* H = a.H;
-        H[(j + 1) * GM_M + j] = hn;
-        // apply the previous rotations to column j
+        // apply the previous rotations to column j, held in a local array (not a chain of
+        // dependent global-memory round trips)
+        double col[GM_M + 1];
+        for (int i = 0; i <= j; ++i) col[i] = H[i * GM_M + j];
+        col[j + 1] = hn;
         for (int i = 0; i < j; ++i) {
-            const double t1 = H[i * GM_M + j], t2 = H[(i + 1) * GM_M + j];
-            H[i * GM_M + j] = a.cs[i] * t1 + a.sn[i] * t2;
-            H[(i + 1) * GM_M + j] = -a.sn[i] * t1 + a.cs[i] * t2;
+            const double t1 = col[i], t2 = col[i + 1];
+            col[i] = a.cs[i] * t1 + a.sn[i] * t2;
+            col[i + 1] = -a.sn[i] * t1 + a.cs[i] * t2;
         }
-        const double h0 = H[j * GM_M + j], h1 = H[(j + 1) * GM_M + j];
+        for (int i = 0; i < j; ++i) H[i * GM_M + j] = col[i];
+        const double h0 = col[j], h1 = col[j + 1];
         const double den = hypot(h0, h1);
         const double c = den > 0.0 ? h0 / den : 1.0, s = den > 0.0 ? h1 / den : 0.0;
         a.cs[j] = c;
@@ -1040,7 +1097,10 @@ static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, do
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D, T>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                launch_pdl(k_gm_dots1<D, T, sizeof(T) == 8 ? 4 : 8>, dim3(grid), dim3(VB), 0, s, a, j);
+                // one resident wave (FP32: 61 registers, 2 CTAs per SM); FP64: one CTA per SM, fewer
+                // cross-lane FP64 adds
+                launch_pdl(k_gm_dots1<D, T, sizeof(T) == 8 ? 4 : 8>,
+                           dim3(std::max(1, sizeof(T) == 8 ? grid / 3 : 2 * grid / 3)), dim3(VB), 0, s, a, j);
                 launch_pdl(k_gm_orth<D, T>, dim3(grid), dim3(VB), 0, s, a, j);
                 launch_pdl(k_gm_norm<D, T>, dim3(grid), dim3(VB), 0, s, a, j, total, maxit);
                 w.launches += 5;
