@@ -73,9 +73,12 @@ typedef enum {
  * preconditioner) run in FP32.  Newton on the FP64 residual is the outer
  * refinement, so the load path still reaches newton_rtol; the inner relative
  * tolerance is not taken below 1e-5.  Newton on an FP32 tangent contracts
- * only linearly (by about cond(K) * 2^-24 per iteration), so once an FP32
- * iteration reduces the FP64 residual by less than a factor 50, the FP64
- * tangent and solve finish the load step.  When a Newton iteration on the FP32 tangent reduces
+ * only linearly (by about cond(K) * 2^-24 per iteration): once an FP32
+ * iteration reduces the FP64 residual by less than 1/(10 eta) (eta its Krylov
+ * tolerance), the same iterate is re-assembled and the step continues with the
+ * FP64 tangent, solved by GMRES on the FP64 operator with an FP32 Krylov basis
+ * and preconditioner (CG, for symmetric tangents, in FP64).  When a Newton
+ * iteration on the FP32 tangent reduces
  * the FP64 residual by less than half (an ill-conditioned tangent, e.g. near a
  * limit load), that load step and the rest of the path continue in FP64
  * (until EP_U is set again).

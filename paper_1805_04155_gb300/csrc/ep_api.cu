@@ -143,10 +143,11 @@ constexpr double MIXED_ETA_MIN = 1e-5;
 // the soft modes by O(1), and Newton on it stalls.
 constexpr double MIXED_STALL_RATIO = 0.5;
 // Newton on an FP32 tangent contracts linearly, by about kappa * 2^-24 per iteration (kappa the
-// tangent's condition number), where FP64 Newton with the adaptive forcing term contracts by about
-// its Krylov tolerance (1e-3 .. 1e-2).  When an FP32 iteration of the mixed path contracts the FP64
-// residual by less than this factor, the rest of the load step uses the FP64 tangent and solve.
-constexpr double MIXED_RHO_MAX = 0.02;
+// tangent's condition number), where Newton on the FP64 tangent contracts by about its Krylov
+// tolerance eta.  When an FP32 iteration of the mixed path reduced the FP64 residual by less than
+// 1 / (MIXED_RHO_FACTOR * eta), the FP32 tangent limits Newton: the step continues, from the same
+// iterate (re-assembled), with the FP64 tangent.
+constexpr double MIXED_RHO_FACTOR = 10.0;
 
 struct Ctx {
     std::string err;
@@ -831,6 +832,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         bool converged = false;
         bool use32 = false;      // this iteration's tangent and solve in FP32
         bool fp64_step = false;  // the rest of this step in FP64 (an FP32 iteration contracted poorly)
+        double eta_prev = 1.0;   // Krylov tolerance of the last solve
         for (;;) {
             use32 = mixed && !c->mixed_fallback && !fp64_step;
             CK(cudaEventRecord(c->ev[0], s));
@@ -887,17 +889,29 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             // FP32 phase of the mixed path: if the last FP32 Newton step barely reduced the FP64
             // residual, the FP32 tangent is too coarse here; this and later steps use FP64, starting
             // with an FP64 assembly at the same iterate (this iteration's tangent is FP32)
-            // (the tangent of this iteration is already assembled: a poor contraction switches the next
-            // iteration to FP64, a stall this one)
-            if (use32 && rnorm_prev > 0.0 && rnorm > MIXED_RHO_MAX * rnorm_prev) fp64_step = true;
+            // (this iteration's tangent is FP32: on a switch the same iterate is re-assembled in FP64)
             if (use32 && rnorm_prev > 0.0 && rnorm > MIXED_STALL_RATIO * rnorm_prev) {
                 c->mixed_fallback = true;
                 if (c->verbose) std::fprintf(stderr, "[ep] step %d: FP32 tangent stalled, FP64 from here\n", k);
                 continue;
             }
+            if (use32 && rnorm_prev > 0.0 && rnorm > MIXED_RHO_FACTOR * eta_prev * rnorm_prev) {
+                fp64_step = true;
+                if (c->verbose > 1)
+                    std::fprintf(stderr, "[ep] step %d: FP32 contraction %.2e vs tolerance %.2e, FP64 tangent\n", k,
+                                 rnorm / rnorm_prev, eta_prev);
+                continue;
+            }
+            // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
+            // nonassociated model
+            const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
+            // the mixed path's FP64-tangent iterations solve with GMRES on the FP64 operator and an
+            // FP32 basis (orthogonalisation, preconditioner and basis in FP32)
+            const bool basis32 = mixed && !use32 && m_it == 3;
             // an FP32 inner solve cannot go much below FP32 rounding; Newton (FP64 residual) refines further
-            if (use32) eta = std::max(eta, MIXED_ETA_MIN);
+            if (use32 || basis32) eta = std::max(eta, MIXED_ETA_MIN);
             rnorm_prev = rnorm;
+            eta_prev = eta;
             CK(cudaEventRecord(c->ev[2], s));
             // Coarse operators: rebuilt (Galerkin, from the current tangent) at the first Newton
             // iteration of a step and whenever the plastic set changed by more than 5% of the points
@@ -914,19 +928,29 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             }
             int kits = 0, kst = 0;
             double krel = 0.0;
-            // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
-            // nonassociated model
-            const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
+            // inside Newton a stagnating FP32-basis solve is cut short (the FP64 path takes over)
+            c->kw.stall_guard = 1;
             if (use32) {
                 rep.newton_its_fp32 += 1;
                 // an FP32 solve that needs far more iterations than usual is stagnating on rounding
                 const int maxit32 = std::min(o.krylov_maxit, std::max(300, 4 * c->kw.last_its));
                 CK(krylov_precond(Af, c->kw, o.precond, s));
                 CK(krylov_solve(Af, c->kw, c->r32, m_it, eta, maxit32, s, &kits, &krel, &kst));
+            } else if (basis32) {
+                const int maxit32 = std::min(o.krylov_maxit, std::max(300, 4 * c->kw.last_its));
+                CK(krylov_precond(A, c->kw, o.precond, s));
+                CK(krylov_solve_fp32_basis(A, c->kw, c->r, eta, maxit32, s, &kits, &krel, &kst));
+                if (kst != EP_OK && !(krel < 0.5)) {   // no progress with the FP32 basis: the FP64 solve
+                    int k2 = 0;
+                    CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &k2, &krel, &kst));
+                    kits += k2;
+                }
+                if (kst != EP_OK && krel < 0.5) kst = EP_OK;   // partial progress: an inexact Newton step
             } else {
                 CK(krylov_precond(A, c->kw, o.precond, s));
                 CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
             }
+            c->kw.stall_guard = 0;
             CK(cudaEventRecord(c->ev[3], s));
             rep.krylov_its += kits;
             if (c->verbose)

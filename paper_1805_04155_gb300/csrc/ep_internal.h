@@ -185,6 +185,7 @@ struct KrylovWork {
     int gm_m;                // GMRES restart length (<= GM_M)
     int galerkin;            // 1: recompute the AMG coarse operators from the current matrix in krylov_precond
     int last_its;            // iterations of the previous solve: sizes the first chunk of launches of the next
+    int stall_guard;         // 1: an FP32-basis GMRES stops when a restart cycle does not halve the residual
     // instrumentation
     int profile;             // 1: CUDA events around every SpMV launch
     int verbose;             // 2: per-cycle host enqueue / wait times on stderr
@@ -208,6 +209,11 @@ cudaError_t krylov_solve(const BsrDev& A, KrylovWork& w, const double* b, int me
                          cudaStream_t s, int* its, double* relres, int* status);
 cudaError_t krylov_solve(const BsrF& A, KrylovWork& w, const float* b, int method, double rtol, int maxit,
                          cudaStream_t s, int* its, double* relres, int* status);
+// GMRES with the FP64 operator and an FP32 basis (w.f's V, z and preconditioner; solution w.d.x):
+// the operator keeps FP64 accuracy (no cancellation error on the soft modes) while the
+// orthogonalisation and the preconditioner move FP32 vectors.  Needs krylov_precond(A) first.
+cudaError_t krylov_solve_fp32_basis(const BsrDev& A, KrylovWork& w, const double* b, double rtol, int maxit,
+                                    cudaStream_t s, int* its, double* relres, int* status);
 
 // Small vector kernels (krylov.cu).
 // r = (zeta f_unit - F) on the free DOFs (and its FP32 copy r32 when non-null); out3 = (||r||^2, ||f||^2, ||F||^2).

@@ -100,9 +100,9 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 // y = P A x (P = free-DOF mask), optional partial of dot(dv, y).
 // G lanes share one block row; lanes read consecutive blocks (coalesced).
 // ---------------------------------------------------------------------------
-template <int D, int G, class T>
-__global__ void __launch_bounds__(VB) k_spmv(BsrT<T> A, const T* __restrict__ x, T* __restrict__ y,
-                                              const T* __restrict__ dv, double* part, const KrylovRec* rec) {
+template <int D, int G, class TA, class TX, class TY>
+__global__ void __launch_bounds__(VB) k_spmv(BsrT<TA> A, const TX* __restrict__ x, TY* __restrict__ y,
+                                              const TY* __restrict__ dv, double* part, const KrylovRec* rec) {
     pdl_enter();
     __shared__ double sh[32];
     if (rec && rec->done) return;
@@ -112,28 +112,28 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrT<T> A, const T* __restrict__ x,
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int GPW = 32 / G;
     const int lg = lane % G;
-    T dot = T(0);
+    TA dot = TA(0);
     for (int64_t rbase = warp * GPW; rbase < A.n_rows; rbase += nwarps * GPW) {
         const int64_t row = rbase + lane / G;
-        T acc[D];
+        TA acc[D];
 #pragma unroll
-        for (int r = 0; r < D; ++r) acc[r] = T(0);
+        for (int r = 0; r < D; ++r) acc[r] = TA(0);
         if (row < A.n_rows) {
             const int beg = A.row_ptr[row], end = A.row_ptr[row + 1];
             for (int k = beg + lg; k < end; k += G) {
                 const int64_t col = A.col_idx[k];
-                const T* blk = A.vals + (int64_t)k * (D * D);
-                T bv[D * D];
-                if constexpr (D == 2 && sizeof(T) == 4) {   // one 16-byte load per 2x2 FP32 block
+                const TA* blk = A.vals + (int64_t)k * (D * D);
+                TA bv[D * D];
+                if constexpr (D == 2 && sizeof(TA) == 4) {   // one 16-byte load per 2x2 FP32 block
                     const float4 v = *reinterpret_cast<const float4*>(blk);
                     bv[0] = v.x; bv[1] = v.y; bv[2] = v.z; bv[3] = v.w;
                 } else {
 #pragma unroll
                     for (int e = 0; e < D * D; ++e) bv[e] = blk[e];
                 }
-                T xc[D];
+                TA xc[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) xc[c] = x[col * D + c];
+                for (int c = 0; c < D; ++c) xc[c] = (TA)x[col * D + c];
 #pragma unroll
                 for (int r = 0; r < D; ++r)
 #pragma unroll
@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrT<T> A, const T* __restrict__ x,
 #pragma unroll
             for (int r = 0; r < D; ++r) {
                 const int64_t dof = row * D + r;
-                const T val = A.free_dof[dof] ? acc[r] : T(0);
-                y[dof] = val;
-                if (dv) dot += dv[dof] * val;
+                const TA val = A.free_dof[dof] ? acc[r] : TA(0);
+                y[dof] = (TY)val;
+                if (dv) dot += (TA)dv[dof] * val;
             }
         }
     }
@@ -579,13 +579,14 @@ static cudaError_t precond_t(const BsrT<T>& A, KrylovWork& w, int kind, cudaStre
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s) { return precond_t(A, w, kind, s); }
 cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t s) { return precond_t(A, w, kind, s); }
 
-template <int D, class T>
-static void launch_spmv(const BsrT<T>& A, const T* x, T* y, const T* dv, double* part, const KrylovRec* rec, int grid,
-                        cudaStream_t s) {
+// y = P A x with A's values TA (accumulation in TA), x and y of their own types
+template <int D, class TA, class TX, class TY>
+static void launch_spmv(const BsrT<TA>& A, const TX* x, TY* y, const TY* dv, double* part, const KrylovRec* rec,
+                        int grid, cudaStream_t s) {
     // FP64: 2 lanes per 2x2-block row (fewer idle lanes and cross-lane FP64 adds on the FP64 pipe)
-    if (D == 2 && sizeof(T) == 8) launch_pdl(k_spmv<2, 2, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
-    else if (D == 2) launch_pdl(k_spmv<2, 4, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
-    else launch_pdl(k_spmv<3, 8, T>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
+    if (D == 2 && sizeof(TA) == 8) launch_pdl(k_spmv<2, 2, TA, TX, TY>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
+    else if (D == 2) launch_pdl(k_spmv<2, 4, TA, TX, TY>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
+    else launch_pdl(k_spmv<3, 8, TA, TX, TY>, dim3(grid), dim3(VB), 0, s, A, x, y, dv, part, rec);
 }
 
 // AMG V-cycle out = M^-1 in, in the solver's precision
@@ -596,6 +597,12 @@ static cudaError_t amg_apply_t(KrylovWork& w, const BsrDev& A, const double* in,
 static cudaError_t amg_apply_t(KrylovWork& w, const BsrF& A, const float* in, float* out, const KrylovRec* rec,
                                cudaStream_t s) {
     return amg_apply(*w.amg, A, in, out, rec, s);
+}
+// FP64 operator, FP32 vectors (the V-cycle's level 0 is the refresh's FP32 copy; A gives the pattern)
+static cudaError_t amg_apply_t(KrylovWork& w, const BsrDev& A, const float* in, float* out, const KrylovRec* rec,
+                               cudaStream_t s) {
+    const BsrF pat{A.n_rows, A.dim, A.row_ptr, A.col_idx, A.diag_slot, nullptr, A.free_dof};
+    return amg_apply(*w.amg, pat, in, out, rec, s);
 }
 
 template <int D, class T>
@@ -635,7 +642,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
     a.cold = (restart == 0);
     a.maxit = maxit - total_its;
     if (restart > 0) {   // warm restart from the current x after a breakdown
-        launch_spmv<D, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
+        launch_spmv<D, T, T, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
         w.launches += 1;
     }
     launch_pdl(k_init<D, T>, dim3(grid), dim3(VB), 0, s, a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
@@ -656,7 +663,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
             if (!bicg) {
                 launch_pdl(k_cg_p<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D, T>(A, vv.p, vv.q, vv.p, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
+                launch_spmv<D, T, T, T>(A, vv.p, vv.q, vv.p, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_pdl(k_cg_update<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 w.launches += 3;
@@ -669,12 +676,12 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
                 launch_pdl(k_bicg_p<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 if (a.amg) amg_apply_t(w, A, vv.p, vv.phat, w.rec, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D, T>(A, vv.phat, vv.v, vv.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
+                launch_spmv<D, T, T, T>(A, vv.phat, vv.v, vv.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_pdl(k_bicg_s<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 if (a.amg) amg_apply_t(w, A, vv.s, vv.shat, w.rec, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D, T>(A, vv.shat, vv.t, nullptr, nullptr, w.rec, grid, s);
+                launch_spmv<D, T, T, T>(A, vv.shat, vv.t, nullptr, nullptr, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_pdl(k_dot2<T>, dim3(grid), dim3(VB), 0, s, a, w.n);
                 launch_pdl(k_bicg_x<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
@@ -729,16 +736,16 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
 // needs from the partial sums, so no launch reads a value written in that
 // launch.
 // ---------------------------------------------------------------------------
-template <class T>
-struct GArgs {
+template <class TX, class TV>
+struct GArgs {          // TX: solution and residual; TV: Krylov basis and preconditioned vectors
     int64_t n_rows;
     const uint8_t* free_dof;
-    const T* minv;
-    T* x;
-    T* r;               // r0 of the cycle
-    T* q;               // A x for warm restarts
-    T* z;               // M^-1 v_j
-    T* V;               // [m+1][n]
+    const TV* minv;
+    TX* x;
+    TX* r;              // r0 of the cycle
+    TX* q;              // A x for warm restarts
+    TV* z;              // M^-1 v_j
+    TV* V;              // [m+1][n]
     double* H;          // [m+1][m], H[i*m + j]
     double* cs;
     double* sn;
@@ -754,16 +761,16 @@ struct GArgs {
 #define GPART(k) (a.part + (int64_t)(k) * a.nparts)
 
 // r = P(b - q) (warm) or P b with x = 0 (cold); partial ||r||^2 -> GPART(0)
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_init(GArgs<T> a, const T* __restrict__ b, int warm) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_init(GArgs<TX, TV> a, const TX* __restrict__ b, int warm) {
     pdl_enter();
     __shared__ double sh[32];
-    T s1 = T(0);
+    TX s1 = TX(0);
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T ri = a.free_dof[i] ? (warm ? b[i] - a.q[i] : b[i]) : T(0);
+        const TX ri = a.free_dof[i] ? (warm ? b[i] - a.q[i] : b[i]) : TX(0);
         a.r[i] = ri;
-        if (!warm) a.x[i] = T(0);
+        if (!warm) a.x[i] = TX(0);
         s1 += ri * ri;
     }
     const double b1 = block_sum(s1, sh);
@@ -774,8 +781,8 @@ __global__ void __launch_bounds__(VB) k_gm_init(GArgs<T> a, const T* __restrict_
 }
 
 // beta = ||r||, v_0 = r / beta, g = (beta, 0, ...); convergence test of the cycle start
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_start(GArgs<T> a) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_start(GArgs<TX, TV> a) {
     pdl_enter();
     __shared__ double sh[32];
     const double rr = sum_partials(GPART(0), a.nparts, sh);
@@ -795,38 +802,21 @@ __global__ void __launch_bounds__(VB) k_gm_start(GArgs<T> a) {
         else if (conv) { a.rec->done = 1; a.rec->why = 1; }
     }
     if (conv || !isfinite(rr)) return;
-    const T ib = (T)s_b[1];
+    const TX ib = (TX)s_b[1];
     const int64_t n = a.n_rows * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a.V[i] = a.r[i] * ib;
+        a.V[i] = (TV)(a.r[i] * ib);
 }
 
 // z = M^-1 v_j
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_prec(GArgs<T> a, int j) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_prec(GArgs<TX, TV> a, int j) {
     pdl_enter();
     if (a.rec->done) return;
-    const T* v = a.V + (int64_t)j * a.n_rows * D;
+    const TV* v = a.V + (int64_t)j * a.n_rows * D;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x)
         apply_minv<D>(a.minv, v, a.z, node);
-}
-
-// partials of h_i = (w, v_i), i = 0..j, with w = V[j+1]; grid (nparts, j + 1): CTA (b, i) -> GPART(i)[b]
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_dots(GArgs<T> a, int j) {
-    pdl_enter();
-    __shared__ double sh[32];
-    if (a.rec->done) return;
-    const int i = blockIdx.y;
-    const int64_t n = a.n_rows * D;
-    const T* w = a.V + (int64_t)(j + 1) * n;
-    const T* v = a.V + (int64_t)i * n;
-    T acc = T(0);
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        acc += w[k] * v[k];
-    const double bsum = block_sum(acc, sh);
-    if (threadIdx.x == 0) GPART(i)[blockIdx.x] = bsum;
 }
 
 // Sum of MJ per-lane values over a warp by recursive halving: at each of the first log2(MJ) levels
@@ -858,27 +848,27 @@ __device__ __forceinline__ T warp_multi_sum(const T (&v)[MJ], int lane) {
 // The same partials from one launch (grid <= nparts; slots of absent CTAs are zeroed): v_0..v_j
 // are taken MJ at a time, each thread keeping its MJ products in registers (w re-read per group,
 // from L2), each group reduced over the warp by warp_multi_sum and over the CTA's warps in FP64.
-template <int D, class T, int MJ>
-__global__ void __launch_bounds__(VB) k_gm_dots1(GArgs<T> a, int j) {
+template <int D, class TX, class TV, int MJ>
+__global__ void __launch_bounds__(VB) k_gm_dots1(GArgs<TX, TV> a, int j) {
     pdl_enter();
     constexpr int LG = (MJ == 2 ? 1 : MJ == 4 ? 2 : MJ == 8 ? 3 : MJ == 16 ? 4 : 5);
     __shared__ double sh[MJ][VB / 32];
     if (a.rec->done) return;
     const int64_t n = a.n_rows * D;
-    const T* w = a.V + (int64_t)(j + 1) * n;
+    const TV* w = a.V + (int64_t)(j + 1) * n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i0 = 0; i0 <= j; i0 += MJ) {
-        T acc[MJ];
+        TV acc[MJ];
 #pragma unroll
-        for (int i = 0; i < MJ; ++i) acc[i] = T(0);
+        for (int i = 0; i < MJ; ++i) acc[i] = TV(0);
         for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-            const T wk = w[k];
-            const T* vk = a.V + (int64_t)i0 * n + k;
+            const TV wk = w[k];
+            const TV* vk = a.V + (int64_t)i0 * n + k;
 #pragma unroll
             for (int i = 0; i < MJ; ++i)
                 if (i0 + i <= j) acc[i] += wk * vk[(int64_t)i * n];
         }
-        const T r = warp_multi_sum<MJ>(acc, lane);
+        const TV r = warp_multi_sum<MJ>(acc, lane);
         if ((lane & ((32 >> LG) - 1)) == 0) sh[lane >> (5 - LG)][wid] = (double)r;
         __syncthreads();
         if ((int)threadIdx.x < MJ && i0 + (int)threadIdx.x <= j) {
@@ -893,11 +883,11 @@ __global__ void __launch_bounds__(VB) k_gm_dots1(GArgs<T> a, int j) {
 }
 
 // w -= sum_i h_i v_i; partial ||w||^2 -> GPART(GM_M + 1); CTA 0 stores H[:, j]
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_orth(GArgs<TX, TV> a, int j) {
     pdl_enter();
     __shared__ double sh[32];
-    __shared__ T h[GM_M];
+    __shared__ TV h[GM_M];
     if (a.rec->done) return;
     {
         // h_i, i = 0..j: warp q reduces slots q, q + 16, ... (each in the fixed order of lane_partials)
@@ -905,25 +895,25 @@ __global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
         for (int i = wid; i <= j; i += nw) {
             const double v = warp_sum(lane_partials(GPART(i), a.nparts, lane));
             if (lane == 0) {
-                h[i] = (T)v;
+                h[i] = (TV)v;
                 if (blockIdx.x == 0) a.H[i * GM_M + j] = v;
             }
         }
         __syncthreads();
     }
     const int64_t n = a.n_rows * D;
-    T* w = a.V + (int64_t)(j + 1) * n;
-    T s1 = T(0);
+    TV* w = a.V + (int64_t)(j + 1) * n;
+    TV s1 = TV(0);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         // two interleaved sums: half the dependent FMA chain
-        T c0 = T(0), c1 = T(0);
+        TV c0 = TV(0), c1 = TV(0);
         int i = 0;
         for (; i + 1 <= j; i += 2) {
             c0 += h[i] * a.V[(int64_t)i * n + k];
             c1 += h[i + 1] * a.V[(int64_t)(i + 1) * n + k];
         }
         if (i <= j) c0 += h[i] * a.V[(int64_t)i * n + k];
-        const T wk = w[k] - (c0 + c1);
+        const TV wk = w[k] - (c0 + c1);
         w[k] = wk;
         s1 += wk * wk;
     }
@@ -932,8 +922,8 @@ __global__ void __launch_bounds__(VB) k_gm_orth(GArgs<T> a, int j) {
 }
 
 // h_{j+1,j} = ||w||, v_{j+1} = w / h; CTA 0: Givens update and convergence test
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_norm(GArgs<T> a, int j, int it_base, int maxit) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_norm(GArgs<TX, TV> a, int j, int it_base, int maxit) {
     pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
@@ -975,87 +965,91 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs<T> a, int j, int it_base, 
         else if (j + 1 == a.m) { a.rec->done = 4; }   // end of the cycle: update and restart
     }
     if (hn == 0.0 || !isfinite(hn)) return;
-    const T ih = (T)s_h[1];
+    const TV ih = (TV)s_h[1];
     const int64_t n = a.n_rows * D;
-    T* w = a.V + (int64_t)(j + 1) * n;
+    TV* w = a.V + (int64_t)(j + 1) * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         w[k] *= ih;
 }
 
 // y = R^-1 g (k x k upper triangle) into shared memory, by thread 0 of every CTA
-template <class T>
-__device__ __forceinline__ void gm_solve_y(const GArgs<T>& a, int k, T* y) {
+template <class TX, class TV>
+__device__ __forceinline__ void gm_solve_y(const GArgs<TX, TV>& a, int k, TV* y) {
     __shared__ double yd[GM_M];
     if (threadIdx.x == 0) {
         for (int i = k - 1; i >= 0; --i) {
             double s = a.g[i];
             for (int l = i + 1; l < k; ++l) s -= a.H[i * GM_M + l] * yd[l];
             yd[i] = s / a.H[i * GM_M + i];
-            y[i] = (T)yd[i];
+            y[i] = (TV)yd[i];
         }
     }
     __syncthreads();
 }
 
 // x += M^-1 (V_k y), y = R^-1 g (k = its of the cycle); every CTA solves the small triangle itself
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_update(GArgs<T> a, int k) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_update(GArgs<TX, TV> a, int k) {
     pdl_enter();
-    __shared__ T y[GM_M];
+    __shared__ TV y[GM_M];
     gm_solve_y(a, k, y);
     const int64_t n = a.n_rows * D;
     for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < a.n_rows;
          node += (int64_t)gridDim.x * blockDim.x) {
-        T u[D];
+        TV u[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            T s = T(0);
+            TV s = TV(0);
             for (int i = 0; i < k; ++i) s += y[i] * a.V[(int64_t)i * n + node * D + c];
             u[c] = s;
         }
-        const T* m = a.minv + node * (D * D);
+        const TV* m = a.minv + node * (D * D);
 #pragma unroll
         for (int r = 0; r < D; ++r) {
-            T s = T(0);
+            TV s = TV(0);
 #pragma unroll
             for (int c = 0; c < D; ++c) s += m[r * D + c] * u[c];
-            a.x[node * D + r] += s;
+            a.x[node * D + r] += (TX)s;
         }
     }
 }
 
 // u = V_k y (y = R^-1 g solved redundantly by every CTA)
-template <int D, class T>
-__global__ void __launch_bounds__(VB) k_gm_combine(GArgs<T> a, int k, T* __restrict__ u) {
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_combine(GArgs<TX, TV> a, int k, TV* __restrict__ u) {
     pdl_enter();
-    __shared__ T y[GM_M];
+    __shared__ TV y[GM_M];
     gm_solve_y(a, k, y);
     const int64_t n = a.n_rows * D;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        T s = T(0);
+        TV s = TV(0);
         for (int i = 0; i < k; ++i) s += y[i] * a.V[(int64_t)i * n + t];
         u[t] = s;
     }
 }
 
-template <class T>
-__global__ void k_axpy_plain(T* __restrict__ x, const T* __restrict__ z, int64_t n) {
+// x += z (z of the basis precision)
+template <class TX, class TV>
+__global__ void k_axpy_plain(TX* __restrict__ x, const TV* __restrict__ z, int64_t n) {
     pdl_enter();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += z[i];
+        x[i] += (TX)z[i];
 }
 
-template <int D, class T>
-static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, double rtol, int maxit,
+// TA: operator values; TX: solution and residual; TV: basis (TA = TX = TV for the FP64 and FP32
+// solvers; TA = TX = double, TV = float for the FP32-basis solve with the FP64 operator)
+template <int D, class TA, class TX, class TV>
+static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, double rtol, int maxit,
                                  cudaStream_t s, int* its, double* relres, int* status) {
-    KVecs<T>& vv = vecs_of<T>(w);
-    GArgs<T> a;
+    KVecs<TX>& vx = vecs_of<TX>(w);
+    KVecs<TV>& vv = vecs_of<TV>(w);
+    GArgs<TX, TV> a;
     a.n_rows = A.n_rows;
     a.free_dof = A.free_dof;
     a.minv = vv.minv;
-    a.x = vv.x;
-    a.r = vv.r;
-    a.q = vv.q;
+    a.x = vx.x;
+    a.r = vx.r;
+    a.q = vx.q;
     a.z = vv.z;
     a.V = vv.V;
     a.H = w.gm;
@@ -1072,15 +1066,15 @@ static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, do
     int total = 0;
     KrylovRec last{};
     double rr_prev_end = 0.0;   // residual estimate ||r||^2 at the end of the previous cycle
-    int n_verify = sizeof(T) == 4 ? 1 : 0;   // FP32: re-check a converged estimate once (see solve_t)
+    int n_verify = sizeof(TV) == 4 ? 1 : 0;   // FP32 basis: re-check a converged estimate once (see solve_t)
     for (int cycle = 0;; ++cycle) {
         a.cold = (cycle == 0);
         if (cycle > 0) {
-            launch_spmv<D, T>(A, vv.x, vv.q, nullptr, nullptr, nullptr, grid, s);
+            launch_spmv<D, TA, TX, TX>(A, vx.x, vx.q, nullptr, nullptr, nullptr, grid, s);
             w.launches += 1;
         }
-        launch_pdl(k_gm_init<D, T>, dim3(grid), dim3(VB), 0, s, a, b, cycle > 0 ? 1 : 0);
-        launch_pdl(k_gm_start<D, T>, dim3(grid), dim3(VB), 0, s, a);
+        launch_pdl(k_gm_init<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, b, cycle > 0 ? 1 : 0);
+        launch_pdl(k_gm_start<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a);
         w.launches += 2;
         // the cycle's iterations in chunks, polling the device record between chunks (the first
         // chunk covers the previous solve's count, see solve_t)
@@ -1092,17 +1086,17 @@ static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, do
             int nev = 0;
             for (int j = j0; j < j1; ++j) {
                 if (use_amg) amg_apply_t(w, A, a.V + (int64_t)j * w.n, a.z, w.rec, s);
-                else launch_pdl(k_gm_prec<D, T>, dim3(grid), dim3(VB), 0, s, a, j);
+                else launch_pdl(k_gm_prec<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j);
                 const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D, T>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
+                launch_spmv<D, TA, TV, TV>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 // one resident wave (FP32: 61 registers, 2 CTAs per SM); FP64: one CTA per SM, fewer
                 // cross-lane FP64 adds
-                launch_pdl(k_gm_dots1<D, T, sizeof(T) == 8 ? 4 : 8>,
-                           dim3(std::max(1, sizeof(T) == 8 ? grid / 3 : 2 * grid / 3)), dim3(VB), 0, s, a, j);
-                launch_pdl(k_gm_orth<D, T>, dim3(grid), dim3(VB), 0, s, a, j);
-                launch_pdl(k_gm_norm<D, T>, dim3(grid), dim3(VB), 0, s, a, j, total, maxit);
+                launch_pdl(k_gm_dots1<D, TX, TV, sizeof(TV) == 8 ? 4 : 8>,
+                           dim3(std::max(1, sizeof(TV) == 8 ? grid / 3 : 2 * grid / 3)), dim3(VB), 0, s, a, j);
+                launch_pdl(k_gm_orth<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j);
+                launch_pdl(k_gm_norm<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j, total, maxit);
                 w.launches += 5;
             }
             cudaError_t e = cudaGetLastError();
@@ -1130,12 +1124,12 @@ static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, do
                          last.its, t_enq, t_wait);
         if (last.its > 0) {
             if (use_amg) {
-                launch_pdl(k_gm_combine<D, T>, dim3(grid), dim3(VB), 0, s, a, last.its, vv.q);
+                launch_pdl(k_gm_combine<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, last.its, vv.q);
                 amg_apply_t(w, A, vv.q, vv.z, nullptr, s);
-                launch_pdl(k_axpy_plain<T>, dim3(grid), dim3(VB), 0, s, vv.x, vv.z, w.n);
+                launch_pdl(k_axpy_plain<TX, TV>, dim3(grid), dim3(VB), 0, s, vx.x, vv.z, w.n);
                 w.launches += 2;
             } else {
-                launch_pdl(k_gm_update<D, T>, dim3(grid), dim3(VB), 0, s, a, last.its);
+                launch_pdl(k_gm_update<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, last.its);
                 w.launches += 1;
             }
         }
@@ -1145,9 +1139,9 @@ static cudaError_t solve_gmres_t(const BsrT<T>& A, KrylovWork& w, const T* b, do
             continue;
         }
         if (last.done != 4) break;           // converged, breakdown, non-finite or cap
-        // an FP32 solve whose restart cycle gained less than 10% has reached what its rounding
-        // allows on this matrix: stop (the caller treats it as an inexact or failed solve)
-        if (sizeof(T) == 4 && last.rr > 0.81 * (cycle == 0 ? last.rr0 : rr_prev_end)) break;
+        // an FP32-basis solve whose restart cycle did not halve the residual has reached what its
+        // rounding allows on this matrix: stop (the caller treats it as an inexact or failed solve)
+        if (sizeof(TV) == 4 && w.stall_guard && last.rr > 0.25 * (cycle == 0 ? last.rr0 : rr_prev_end)) break;
         rr_prev_end = last.rr;
     }
     *its = total;
@@ -1164,8 +1158,8 @@ template <class T>
 static cudaError_t solve_any(const BsrT<T>& A, KrylovWork& w, const T* b, int method, double rtol, int maxit,
                              cudaStream_t s, int* its, double* relres, int* status) {
     if (method == 3) {
-        if (A.dim == 2) return solve_gmres_t<2, T>(A, w, b, rtol, maxit, s, its, relres, status);
-        return solve_gmres_t<3, T>(A, w, b, rtol, maxit, s, its, relres, status);
+        if (A.dim == 2) return solve_gmres_t<2, T, T, T>(A, w, b, rtol, maxit, s, its, relres, status);
+        return solve_gmres_t<3, T, T, T>(A, w, b, rtol, maxit, s, its, relres, status);
     }
     if (A.dim == 2) return solve_t<2, T>(A, w, b, method, rtol, maxit, s, its, relres, status);
     return solve_t<3, T>(A, w, b, method, rtol, maxit, s, its, relres, status);
@@ -1179,6 +1173,17 @@ cudaError_t krylov_solve(const BsrF& A, KrylovWork& w, const float* b, int metho
                          cudaStream_t s, int* its, double* relres, int* status) {
     if (!w.f.x) return cudaErrorInvalidValue;
     return solve_any(A, w, b, method, rtol, maxit, s, its, relres, status);
+}
+
+cudaError_t krylov_solve_fp32_basis(const BsrDev& A, KrylovWork& w, const double* b, double rtol, int maxit,
+                                    cudaStream_t s, int* its, double* relres, int* status) {
+    if (!w.f.x) return cudaErrorInvalidValue;
+    // the basis-precision preconditioner: the FP64 block-Jacobi inverse rounded to FP32
+    cudaError_t e = vec_cvt_f32(w.d.minv, w.f.minv, A.n_rows * A.dim * A.dim, s);
+    if (e != cudaSuccess) return e;
+    w.launches += 1;
+    if (A.dim == 2) return solve_gmres_t<2, double, double, float>(A, w, b, rtol, maxit, s, its, relres, status);
+    return solve_gmres_t<3, double, double, float>(A, w, b, rtol, maxit, s, its, relres, status);
 }
 
 // ---------------------------------------------------------------------------
