@@ -14,6 +14,8 @@
 // row reading consecutive blocks.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "amg.h"
@@ -40,7 +42,8 @@ __device__ __forceinline__ void group_row(const Mat<TM>& M, int64_t row, bool ac
     for (int r = 0; r < RB; ++r) acc[r] = TA(0);
     if (active) {
         const int beg = M.row_ptr[row], end = M.row_ptr[row + 1];
-        for (int k = beg + lg; k < end; k += G) {
+        // two blocks per lane per step: two independent index -> gather chains in flight
+        auto block = [&](int k) {
             const int64_t col = M.col_idx[k];
             const TM* blk = M.vals + (int64_t)k * (RB * CB);
             TA xc[CB];
@@ -58,7 +61,13 @@ __device__ __forceinline__ void group_row(const Mat<TM>& M, int64_t row, bool ac
             for (int r = 0; r < RB; ++r)
 #pragma unroll
                 for (int c = 0; c < CB; ++c) acc[r] += (TA)bv[r * CB + c] * xc[c];
+        };
+        int k = beg + lg;
+        for (; k + G < end; k += 2 * G) {
+            block(k);
+            block(k + G);
         }
+        if (k < end) block(k);
     }
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1)
@@ -429,10 +438,18 @@ __global__ void k_pw_init(T* x, int64_t n, const uint8_t* mask) {
 static int g_num_sms = 152;
 constexpr int RES_CTAS = 6;
 
-static unsigned rows_grid(int64_t n_rows, int G) {
+static unsigned rows_grid(int64_t n_rows, int G, int res_ctas = RES_CTAS) {
     const int64_t groups_per_cta = AB / G;
     int64_t g = (n_rows + groups_per_cta - 1) / groups_per_cta;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)g_num_sms * RES_CTAS));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)g_num_sms * res_ctas));
+}
+
+// CTAs of AB threads one SM holds for a kernel (its registers and shared memory), asked once
+template <class K>
+static int resident_ctas(K kern) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, AB, 0) != cudaSuccess || n < 1) n = RES_CTAS;
+    return n;
 }
 
 template <class T>
@@ -474,8 +491,9 @@ template <class T>
 static void cheb(int bs, int g, const Mat<T>& A, const T* dinv, const T* b, const T* xi, T* xo, T* d,
                  const float* coef_l, int step, const KrylovRec* rec, cudaStream_t s) {
     const float* cf = coef_l + step * 3;
-#define EP_CHEB(RB) EP_G_SWITCH(g, launch_pdl(k_cheb<RB, GG, T>, dim3(rows_grid(A.n_rows, GG)), dim3(AB), 0, s, A, dinv, \
-                                              b, xi, xo, d, cf, step, rec))
+#define EP_CHEB(RB) EP_G_SWITCH(g, { static const int occ = resident_ctas(k_cheb<RB, GG, T>);                       \
+                                     launch_pdl(k_cheb<RB, GG, T>, dim3(rows_grid(A.n_rows, GG, occ)), dim3(AB), 0, s, \
+                                                A, dinv, b, xi, xo, d, cf, step, rec); })
     switch (bs) {
         case 2: EP_CHEB(2) break;
         case 3: EP_CHEB(3) break;
@@ -485,8 +503,9 @@ static void cheb(int bs, int g, const Mat<T>& A, const T* dinv, const T* b, cons
 }
 template <class T>
 static void resid(int bs, int g, const Mat<T>& A, const T* b, const T* x, T* r, const KrylovRec* rec, cudaStream_t s) {
-#define EP_RESID(RB) EP_G_SWITCH(g, launch_pdl(k_resid<RB, GG, T>, dim3(rows_grid(A.n_rows, GG)), dim3(AB), 0, s, A, b, \
-                                               x, r, rec))
+#define EP_RESID(RB) EP_G_SWITCH(g, { static const int occ = resident_ctas(k_resid<RB, GG, T>);                     \
+                                      launch_pdl(k_resid<RB, GG, T>, dim3(rows_grid(A.n_rows, GG, occ)), dim3(AB), 0, \
+                                                 s, A, b, x, r, rec); })
     switch (bs) {
         case 2: EP_RESID(2) break;
         case 3: EP_RESID(3) break;
@@ -497,8 +516,9 @@ static void resid(int bs, int g, const Mat<T>& A, const T* b, const T* x, T* r, 
 template <class TX, class TY>
 static void mv(const DevPat& p, const float* v, const TX* x, TY* y, int add, const KrylovRec* rec, cudaStream_t s) {
     const Mat<float> M = matf(p, v);
-#define EP_MV(RB, CB) EP_G_SWITCH(p.g, launch_pdl(k_mv<RB, CB, GG, TX, TY>, dim3(rows_grid(M.n_rows, GG)), dim3(AB), 0, \
-                                                  s, M, x, y, add, rec))
+#define EP_MV(RB, CB) EP_G_SWITCH(p.g, { static const int occ = resident_ctas(k_mv<RB, CB, GG, TX, TY>);            \
+                                         launch_pdl(k_mv<RB, CB, GG, TX, TY>, dim3(rows_grid(M.n_rows, GG, occ)),     \
+                                                    dim3(AB), 0, s, M, x, y, add, rec); })
     switch (p.rb * 10 + p.cb) {
         case 23: EP_MV(2, 3) break;
         case 32: EP_MV(3, 2) break;
@@ -546,6 +566,15 @@ static cudaError_t dvec(AmgDev& D, T** p, int64_t n) {
 
 cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
     if (num_sms > 0) g_num_sms = num_sms;
+    // smoothing steps (1 .. AMG_CHEB_DEGREE): level-0 pre, level-0 post, coarse levels; EP_AMG_SMOOTH="pre,post,coarse"
+    if (const char* sm = std::getenv("EP_AMG_SMOOTH")) {
+        int a = 2, b = 2, c = 2;
+        if (std::sscanf(sm, "%d,%d,%d", &a, &b, &c) == 3) {
+            D.deg_pre0 = std::max(1, std::min(AMG_CHEB_DEGREE, a));
+            D.deg_post0 = std::max(1, std::min(AMG_CHEB_DEGREE, b));
+            D.deg_c = std::max(1, std::min(AMG_CHEB_DEGREE, c));
+        }
+    }
     D.n_levels = (int)H.levels.size();
     cudaError_t e;
     std::vector<double> lam(AMG_MAX_LEVELS, 1.0);
@@ -766,6 +795,26 @@ __global__ void __launch_bounds__(AB) k_dense_d(const float* __restrict__ Ainv, 
 }
 
 // The V-cycle on FP32 vectors: x0 = M^-1 b0 (b0 and x0 distinct; level-0 work vectors x2, d, r).
+// Chebyshev smoothing of A x = b by `deg` steps (1 .. AMG_CHEB_DEGREE) ending in `fin`, with `scr` as the
+// other buffer.  From zero (start == nullptr) the first step needs no matrix product.  Returns the
+// buffer the first step reads from (the pre-smoothing "work" buffer for the caller).
+template <class T>
+static void smooth(int bs, int g, const Mat<T>& A, const T* dinv, const T* b, const T* start, T* fin, T* scr, T* d,
+                   const float* coef_l, int deg, const KrylovRec* rec, cudaStream_t s, int& launches) {
+    const T* cur = start;
+    for (int st = 0; st < deg; ++st) {
+        T* nxt = ((deg - st) % 2 == 1) ? fin : scr;
+        if (nxt == cur) nxt = (nxt == fin) ? scr : fin;
+        cheb<T>(bs, g, A, dinv, b, cur, nxt, d, coef_l, st, rec, s);
+        cur = nxt;
+        ++launches;
+    }
+}
+
+// The V-cycle on FP32 vectors: x0 = M^-1 b0 (b0 and x0 distinct; level-0 work vectors x2, d, r).
+// Level l's pre-smoothed, coarse-corrected iterate lives in the buffer from which its post-smoothing
+// ends in the level's result (x0 on level 0, lv[l].x below): the result buffer itself for an even
+// number of post-smoothing steps, the scratch buffer x2 for an odd one.
 template <class T>
 static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* x0, const KrylovRec* rec,
                           cudaStream_t s) {
@@ -774,21 +823,24 @@ static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* 
     const Mat<float> M0 = mat0f(A0, D.K0);
     const int bs0 = A0.dim;
     const float* cf0 = D.coef;
+    auto work_of = [](int dpost, float* fin, float* scr) { return dpost % 2 == 0 ? fin : scr; };
     // level 0: pre-smoothing from zero, residual, restriction
-    cheb<float>(bs0, D.g0, M0, D.minv0, b0, nullptr, l0.x2, l0.d, cf0, 0, rec, s);
-    cheb<float>(bs0, D.g0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
-    resid<float>(bs0, D.g0, M0, b0, x0, l0.r, rec, s);
+    float* w0 = work_of(D.deg_post0, x0, l0.x2);
+    smooth<float>(bs0, D.g0, M0, D.minv0, b0, nullptr, w0, w0 == x0 ? l0.x2 : x0, l0.d, cf0, D.deg_pre0, rec, s,
+                  D.launches);
+    resid<float>(bs0, D.g0, M0, b0, w0, l0.r, rec, s);
     mv<float, float>(l0.R, l0.Rvals, l0.r, D.lv[1].b, 0, rec, s);
-    D.launches += 4;
+    D.launches += 2;
     // coarse levels (FP32), descending
     for (int l = 1; l < L - 1; ++l) {
         AmgDevLevel& v = D.lv[l];
         const Mat<float> A = matf(v.A, v.Avals);
-        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, nullptr, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
-        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
-        resid<float>(v.bs, v.A.g, A, v.b, v.x, v.r, rec, s);
+        float* w = work_of(D.deg_c, v.x, v.x2);
+        smooth<float>(v.bs, v.A.g, A, v.dinv, v.b, nullptr, w, w == v.x ? v.x2 : v.x, v.d,
+                      D.coef + l * AMG_CHEB_DEGREE * 3, D.deg_c, rec, s, D.launches);
+        resid<float>(v.bs, v.A.g, A, v.b, w, v.r, rec, s);
         mv<float, float>(v.R, v.Rvals, v.r, D.lv[l + 1].b, 0, rec, s);
-        D.launches += 4;
+        D.launches += 2;
     }
     {
         AmgDevLevel& c = D.lv[L - 1];
@@ -796,19 +848,19 @@ static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* 
         launch_pdl(k_dense, dim3(g), dim3(AB), 0, s, c.dense_inv, c.n, c.b, c.x, rec);
         D.launches += 1;
     }
-    // ascending
+    // ascending: coarse correction into the work buffer, post-smoothing into the result
     for (int l = L - 2; l >= 1; --l) {
         AmgDevLevel& v = D.lv[l];
         const Mat<float> A = matf(v.A, v.Avals);
-        mv<float, float>(v.P, v.Pvals, D.lv[l + 1].x, v.x, 1, rec, s);
-        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, v.x, v.x2, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 0, rec, s);
-        cheb<float>(v.bs, v.A.g, A, v.dinv, v.b, v.x2, v.x, v.d, D.coef + (l) * AMG_CHEB_DEGREE * 3, 1, rec, s);
-        D.launches += 3;
+        float* w = work_of(D.deg_c, v.x, v.x2);
+        mv<float, float>(v.P, v.Pvals, D.lv[l + 1].x, w, 1, rec, s);
+        smooth<float>(v.bs, v.A.g, A, v.dinv, v.b, w, v.x, v.x2, v.d, D.coef + l * AMG_CHEB_DEGREE * 3, D.deg_c, rec,
+                      s, D.launches);
+        D.launches += 1;
     }
-    mv<float, float>(l0.P, l0.Pvals, D.lv[1].x, x0, 1, rec, s);
-    cheb<float>(bs0, D.g0, M0, D.minv0, b0, x0, l0.x2, l0.d, cf0, 0, rec, s);
-    cheb<float>(bs0, D.g0, M0, D.minv0, b0, l0.x2, x0, l0.d, cf0, 1, rec, s);
-    D.launches += 3;
+    mv<float, float>(l0.P, l0.Pvals, D.lv[1].x, w0, 1, rec, s);
+    smooth<float>(bs0, D.g0, M0, D.minv0, b0, w0, x0, l0.x2, l0.d, cf0, D.deg_post0, rec, s, D.launches);
+    D.launches += 1;
     return cudaGetLastError();
 }
 

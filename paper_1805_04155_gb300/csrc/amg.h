@@ -13,7 +13,7 @@ namespace ep {
 
 constexpr int AMG_COARSE_MAX = 600;    // DOFs of the coarsest level (inverted densely on the host)
 constexpr int AMG_MAX_LEVELS = 10;
-constexpr int AMG_CHEB_DEGREE = 2;     // Chebyshev smoothing steps before and after the coarse correction
+constexpr int AMG_CHEB_DEGREE = 3;     // largest number of Chebyshev smoothing steps on either side of the coarse correction
 
 struct HostBsr {
     int rb = 0, cb = 0;                // block shape
@@ -89,6 +89,8 @@ struct AmgDev {
     const float* minv0 = nullptr;      // their block-Jacobi inverse
     int64_t nnzb0 = 0;
     int g0 = 4;                        // lanes per block row of the level-0 matrix
+    int deg_pre0 = 2, deg_post0 = 2;   // Chebyshev steps on level 0 before / after the coarse correction
+    int deg_c = 2;                     // ... on the coarse levels (both sides)
     double* pw = nullptr;              // power-iteration work [2][n0] (FP64)
     float* pwf = nullptr;              // power-iteration work [2][n1] (FP32)
     double* pw_part = nullptr;

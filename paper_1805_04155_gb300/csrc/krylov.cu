@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrT<TA> A, const TX* __restrict__ 
         for (int r = 0; r < D; ++r) acc[r] = TA(0);
         if (row < A.n_rows) {
             const int beg = A.row_ptr[row], end = A.row_ptr[row + 1];
-            for (int k = beg + lg; k < end; k += G) {
+            auto block = [&](int k) {
                 const int64_t col = A.col_idx[k];
                 const TA* blk = A.vals + (int64_t)k * (D * D);
                 TA bv[D * D];
@@ -138,7 +138,14 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrT<TA> A, const TX* __restrict__ 
                 for (int r = 0; r < D; ++r)
 #pragma unroll
                     for (int c = 0; c < D; ++c) acc[r] += bv[r * D + c] * xc[c];
+            };
+            // two blocks per lane per step: two independent index -> gather chains in flight
+            int k = beg + lg;
+            for (; k + G < end; k += 2 * G) {
+                block(k);
+                block(k + G);
             }
+            if (k < end) block(k);
         }
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1)
