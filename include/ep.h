@@ -182,6 +182,20 @@ void ep_default_opts(ep_opts* opts);
 ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, const ep_bc* bc,
                     int32_t device, void* cuda_stream);
 
+/*
+ * A batch of independent problems in one context (the batched form of the
+ * hot path): n_problems meshes of one element type and dimension, with their
+ * own materials (one model for all; parameters may differ) and boundary
+ * conditions, are concatenated into one mesh (problem p's nodes and elements
+ * follow problem p-1's; fields of ep_get / ep_set are concatenated in that
+ * order).  Every assembly, Krylov solve and commit covers all problems in the
+ * same launches; ep_solve_load_path applies the same load factors to all and
+ * a step converges when every problem's own relative residual reaches
+ * newton_rtol.  Host arrays are copied; errors as ep_create.
+ */
+ep_status ep_create_batch(void** out, int32_t n_problems, const ep_mesh* meshes, const ep_material* mats,
+                          const ep_bc* bcs, int32_t device, void* cuda_stream);
+
 ep_status ep_destroy(void* ctx);
 
 ep_status ep_get_info(const void* ctx, ep_info* info);

@@ -155,18 +155,19 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
         const int e = j / NQ;
         const int64_t ip = ip0 + j;
         const double w = s_w[j];
+        const MatConst& mat = elem_material(a.mesh, e0 + e);
         PointOut<NA> o;
         if (MODEL == 0 && !WANT_F) {
             PointIn<NA> in;
 #pragma unroll
             for (int c = 0; c < NA; ++c) { in.eps[c] = 0.0; in.ep[c] = 0.0; in.beta[c] = 0.0; }
             in.alpha = 0.0;
-            return_map<NA, 0>(a.mat, in, o);
+            return_map<NA, 0>(mat, in, o);
         } else {
             PointIn<NA> in;
             strain_at<D, NP, NA>(s_g + j * NP * D, s_u + e * NP * D, in.eps);
             load_state<NA, MODEL>(a.state, n_int, ip, in);
-            return_map<NA, MODEL>(a.mat, in, o);
+            return_map<NA, MODEL>(mat, in, o);
             if (o.err && a.err_flag) atomicOr(a.err_flag, 1);
         }
         const int plastic = (o.flag != 0);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
         }
         // split mode: an elastic point adds nothing (D - C = 0), its tangent is not formed
         if (DELTA && !plastic) continue;
-        if (DELTA) { o.cV -= a.mat.K; o.cD -= 2.0 * a.mat.G; }
+        if (DELTA) { o.cV -= mat.K; o.cD -= 2.0 * mat.G; }
         if (S::F32) {
             // the tangent from FP64 coefficients rounded once to FP32
             PointTan<NA, KT> t;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
         strain_at<D, NP, NA>(g, u, in.eps);
         load_state<NA, MODEL>(a.state, n_int, ip, in);
         PointOut<NA> o;
-        return_map<NA, MODEL>(a.mat, in, o);
+        return_map<NA, MODEL>(elem_material(a.mesh, e), in, o);
         if (o.err && a.err_flag) atomicOr(a.err_flag, 1);
 #pragma unroll
         for (int c = 0; c < NA; ++c) {

@@ -156,7 +156,17 @@ struct Ctx {
     int num_sms = 152;
     int dim = 0, family = 0, eid = 0, n_p = 0, n_q = 0, n_comp = 0;
     int64_t n_nodes = 0, n_elem = 0, n_int = 0, n_dof = 0, nnzb = 0, hard_len = 0;
-    MatConst mat{};
+    MatConst mat{};                 // material of entry 0 (the model and the symmetry test)
+    MatConst* mat_table = nullptr;  // device [n_mat]
+    int32_t* elem_mat = nullptr;    // device [n_elem] or null (one material)
+    int n_mat = 1;
+    // batch of independent problems: problem p owns DOFs [prob_dof[p], prob_dof[p + 1])
+    int n_prob = 1;
+    std::vector<int64_t> prob_dof;
+    std::vector<int64_t> chunk_prob, chunk_beg, chunk_end;   // residual-norm chunks (host copy)
+    int64_t* d_chunks = nullptr;    // device [3][n_chunks]: problem, begin, end
+    double* d_chunk_norms = nullptr;   // device [3][n_chunks]
+    std::vector<double> h_chunk_norms;
     // mesh and pattern
     double* coords = nullptr;
     int32_t *elem = nullptr, *slots = nullptr, *row_ptr = nullptr, *col_idx = nullptr, *diag_slot = nullptr;
@@ -229,6 +239,8 @@ static MeshDev mesh_dev(const Ctx* c) {
     m.slots = c->slots;
     m.dphi = c->dphi;
     m.wgt = c->wgt;
+    m.mat_table = c->mat_table;
+    m.elem_mat = c->elem_mat;
     return m;
 }
 
@@ -408,11 +420,19 @@ ep_status ep_destroy(void* ctx) {
     return EP_OK;
 }
 
-ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, const ep_bc* bc, int32_t device,
-                    void* cuda_stream) {
+}  // extern "C"
+
+namespace ep {
+// Creation shared by ep_create (one problem) and ep_create_batch (problems concatenated into one
+// mesh): n_mat materials of one model, elem_mat (host, [n_elem], or null) the material of each
+// element, prob_node (host, [n_prob + 1], or null) the node range of each problem.
+static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material* mats, int32_t n_mat,
+                             const int32_t* elem_mat, const int64_t* prob_node, int32_t n_prob, const ep_bc* bc,
+                             int32_t device, void* cuda_stream) {
     if (!out) return EP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!mesh || !mat || !bc || !mesh->coords || !mesh->elem_nodes || !bc->dirichlet_mask) return EP_ERR_INVALID_ARG;
+    if (!mesh || !mats || n_mat < 1 || !bc || !mesh->coords || !mesh->elem_nodes || !bc->dirichlet_mask)
+        return EP_ERR_INVALID_ARG;
     if ((mesh->dim != 2 && mesh->dim != 3) || mesh->elem < 0 || mesh->elem > 3 || mesh->n_nodes <= 0 ||
         mesh->n_elem <= 0 || mesh->n_nodes > INT32_MAX)
         return EP_ERR_INVALID_ARG;
@@ -440,8 +460,33 @@ ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, con
     c->n_elem = mesh->n_elem;
     c->n_int = c->n_elem * c->n_q;
     c->n_dof = c->n_nodes * c->dim;
-    if (!make_matconst(*mat, c->dim, c->mat, c->err)) return fail(EP_ERR_INVALID_ARG);
+    std::vector<MatConst> mtab(n_mat);
+    for (int i = 0; i < n_mat; ++i) {
+        if (!make_matconst(mats[i], c->dim, mtab[i], c->err)) return fail(EP_ERR_INVALID_ARG);
+        if (mtab[i].model != mtab[0].model) {
+            c->err = "batch: every problem must use the same material model";
+            return fail(EP_ERR_INVALID_ARG);
+        }
+    }
+    c->mat = mtab[0];
+    c->n_mat = n_mat;
+    if (elem_mat)
+        for (int64_t e = 0; e < c->n_elem; ++e)
+            if (elem_mat[e] < 0 || elem_mat[e] >= n_mat) {
+                c->err = "batch: element material index out of range";
+                return fail(EP_ERR_INVALID_ARG);
+            }
     c->hard_len = (c->mat.model == 1) ? c->n_int * c->n_comp : c->n_int;
+    // problems and their residual-norm chunks (64 Ki DOFs each)
+    c->n_prob = std::max(1, n_prob);
+    c->prob_dof.assign(c->n_prob + 1, 0);
+    for (int p = 0; p <= c->n_prob; ++p) c->prob_dof[p] = prob_node ? prob_node[p] * c->dim : (p ? c->n_dof : 0);
+    for (int p = 0; p < c->n_prob; ++p)
+        for (int64_t b = c->prob_dof[p]; b < c->prob_dof[p + 1]; b += 65536) {
+            c->chunk_prob.push_back(p);
+            c->chunk_beg.push_back(b);
+            c->chunk_end.push_back(std::min(c->prob_dof[p + 1], b + (int64_t)65536));
+        }
 
     // pattern and slot map (host)
     std::vector<int32_t> row_ptr, col_idx, slots;
@@ -493,6 +538,14 @@ ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, con
     CKF(dalloc(c, &c->f_unit, c->n_dof));
     CKF(dalloc(c, &c->uD_unit, c->n_dof));
     CKF(dalloc(c, &c->free_dof, c->n_dof));
+    CKF(dalloc(c, &c->mat_table, n_mat));
+    if (elem_mat) CKF(dalloc(c, &c->elem_mat, c->n_elem));
+    if (c->n_prob > 1) {
+        const int64_t nc = (int64_t)c->chunk_prob.size();
+        CKF(dalloc(c, &c->d_chunks, 3 * nc));
+        CKF(dalloc(c, &c->d_chunk_norms, 3 * nc));
+        c->h_chunk_norms.resize(3 * nc);
+    }
     CKF(dalloc(c, &c->counter, 1));
     CKF(dalloc(c, &c->err_flag, 1));
     CKF(dalloc(c, &c->norms, 3));
@@ -507,6 +560,20 @@ ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, con
 
     std::vector<uint8_t> freem(c->n_dof);
     for (int64_t i = 0; i < c->n_dof; ++i) freem[i] = bc->dirichlet_mask[i] ? 0 : 1;
+    CKF(cudaMemcpyAsync(c->mat_table, mtab.data(), sizeof(MatConst) * n_mat, cudaMemcpyHostToDevice, s));
+    if (elem_mat)
+        CKF(cudaMemcpyAsync(c->elem_mat, elem_mat, sizeof(int32_t) * c->n_elem, cudaMemcpyHostToDevice, s));
+    if (c->n_prob > 1) {
+        const int64_t nc = (int64_t)c->chunk_prob.size();
+        std::vector<int64_t> ch(3 * nc);
+        for (int64_t i = 0; i < nc; ++i) {
+            ch[i] = c->chunk_prob[i];
+            ch[nc + i] = c->chunk_beg[i];
+            ch[2 * nc + i] = c->chunk_end[i];
+        }
+        CKF(cudaMemcpyAsync(c->d_chunks, ch.data(), sizeof(int64_t) * ch.size(), cudaMemcpyHostToDevice, s));
+        CKF(cudaStreamSynchronize(s));   // ch is a host temporary
+    }
     CKF(cudaMemcpyAsync(c->coords, mesh->coords, sizeof(double) * c->n_nodes * d, cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->elem, mesh->elem_nodes, sizeof(int32_t) * c->n_elem * c->n_p, cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->slots, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, s));
@@ -573,6 +640,64 @@ ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, con
     c->h_free = std::move(freem);
     *out = c;
     return EP_OK;
+}
+}  // namespace ep
+
+extern "C" {
+
+ep_status ep_create(void** out, const ep_mesh* mesh, const ep_material* mat, const ep_bc* bc, int32_t device,
+                    void* cuda_stream) {
+    return create_impl(out, mesh, mat, 1, nullptr, nullptr, 1, bc, device, cuda_stream);
+}
+
+ep_status ep_create_batch(void** out, int32_t n_problems, const ep_mesh* meshes, const ep_material* mats,
+                          const ep_bc* bcs, int32_t device, void* cuda_stream) {
+    if (!out) return EP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_problems < 1 || !meshes || !mats || !bcs) return EP_ERR_INVALID_ARG;
+    const int dim = meshes[0].dim, fam = meshes[0].elem;
+    if ((dim != 2 && dim != 3) || fam < 0 || fam > 3) return EP_ERR_INVALID_ARG;
+    const int n_p = elem_np(elem_id(fam, dim));
+    int64_t nn = 0, ne = 0;
+    std::vector<int64_t> node_off(n_problems + 1, 0);
+    for (int p = 0; p < n_problems; ++p) {
+        const ep_mesh& m = meshes[p];
+        if (m.dim != dim || m.elem != fam || m.n_nodes <= 0 || m.n_elem <= 0 || !m.coords || !m.elem_nodes ||
+            !bcs[p].dirichlet_mask) {
+            g_create_err = "ep_create_batch: problem " + std::to_string(p) + " has a different element type or no data";
+            return EP_ERR_INVALID_ARG;
+        }
+        nn += m.n_nodes;
+        ne += m.n_elem;
+        node_off[p + 1] = nn;
+    }
+    if (nn > INT32_MAX) return EP_ERR_INVALID_ARG;
+    std::vector<double> coords((size_t)nn * dim), uD((size_t)nn * dim, 0.0), fe((size_t)nn * dim, 0.0);
+    std::vector<int32_t> elem((size_t)ne * n_p), emat(ne);
+    std::vector<uint8_t> mask((size_t)nn * dim);
+    int64_t eo = 0;
+    for (int p = 0; p < n_problems; ++p) {
+        const ep_mesh& m = meshes[p];
+        const int64_t no = node_off[p];
+        std::copy(m.coords, m.coords + m.n_nodes * dim, coords.begin() + no * dim);
+        std::copy(bcs[p].dirichlet_mask, bcs[p].dirichlet_mask + m.n_nodes * dim, mask.begin() + no * dim);
+        if (bcs[p].u_D_unit) std::copy(bcs[p].u_D_unit, bcs[p].u_D_unit + m.n_nodes * dim, uD.begin() + no * dim);
+        if (bcs[p].f_ext_unit)
+            std::copy(bcs[p].f_ext_unit, bcs[p].f_ext_unit + m.n_nodes * dim, fe.begin() + no * dim);
+        for (int64_t i = 0; i < m.n_elem * n_p; ++i) {
+            const int32_t v = m.elem_nodes[i];
+            if (v < 0 || v >= m.n_nodes) {
+                g_create_err = "ep_create_batch: problem " + std::to_string(p) + " has a node index out of range";
+                return EP_ERR_INVALID_ARG;
+            }
+            elem[(size_t)(eo * n_p + i)] = (int32_t)(v + no);
+        }
+        std::fill(emat.begin() + eo, emat.begin() + eo + m.n_elem, p);
+        eo += m.n_elem;
+    }
+    const ep_mesh all{dim, fam, nn, ne, coords.data(), elem.data()};
+    const ep_bc bc{mask.data(), uD.data(), fe.data()};
+    return create_impl(out, &all, mats, n_problems, emat.data(), node_off.data(), n_problems, &bc, device, cuda_stream);
 }
 
 // Build the AMG hierarchy from K_elast on first use of preconditioner 2.
@@ -843,6 +968,13 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                             c->kw.nparts, c->norms, s));
             c->launches += 2;
             rep.n_assemble += 1;
+            const int64_t nchunk = (int64_t)c->chunk_prob.size();
+            if (c->n_prob > 1) {
+                CK(vec_chunk_norms(c->f_unit, z, c->F, c->free_dof, c->r, c->d_chunks, nchunk, c->d_chunk_norms, s));
+                CK(cudaMemcpyAsync(c->h_chunk_norms.data(), c->d_chunk_norms, sizeof(double) * 3 * nchunk,
+                                   cudaMemcpyDeviceToHost, s));
+                c->launches += 1;
+            }
             CK(cudaMemcpyAsync(c->norms_host, c->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(c->counter_host, c->counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -868,6 +1000,22 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 break;
             }
             rel = scale > 0.0 ? rnorm / scale : rnorm;
+            if (c->n_prob > 1) {
+                // a batch converges when every problem does, each relative to its own load and forces
+                std::vector<double> pr(c->n_prob, 0.0), pf(c->n_prob, 0.0), pF(c->n_prob, 0.0);
+                for (int64_t i = 0; i < nchunk; ++i) {
+                    const int64_t p = c->chunk_prob[i];
+                    pr[p] += c->h_chunk_norms[i];
+                    pf[p] += c->h_chunk_norms[nchunk + i];
+                    pF[p] += c->h_chunk_norms[2 * nchunk + i];
+                }
+                rel = 0.0;
+                for (int p = 0; p < c->n_prob; ++p) {
+                    const double sc = std::max(std::sqrt(pf[p]), std::sqrt(pF[p]));
+                    const double rp = std::sqrt(pr[p]);
+                    rel = std::max(rel, sc > 0.0 ? rp / sc : rp);
+                }
+            }
             if (rel <= o.newton_rtol || rnorm == 0.0) {
                 converged = true;
                 break;

@@ -63,7 +63,14 @@ struct MeshDev {
     const int32_t* slots;       // [n_elem][n_p*n_p], block index of node pair (p, q)
     const double* dphi;         // [n_int][n_p][dim], physical basis gradients
     const double* wgt;          // [n_int]
+    const MatConst* mat_table;  // material constants, >= 1 entry
+    const int32_t* elem_mat;    // [n_elem] index into mat_table (null: every element uses entry 0)
 };
+
+// The material of element e.
+__host__ __device__ inline const MatConst& elem_material(const MeshDev& m, int64_t e) {
+    return m.mat_table[m.elem_mat ? m.elem_mat[e] : 0];
+}
 
 struct StateDev {
     double* ep;       // [n_comp][n_int]
@@ -220,6 +227,9 @@ cudaError_t krylov_solve_fp32_basis(const BsrDev& A, KrylovWork& w, const double
 cudaError_t vec_residual(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof, double* r,
                          float* r32, int64_t n, double* part, int nparts, double* out3, cudaStream_t s);
 cudaError_t vec_axpy_f32(double* y, const float* x, int64_t n, cudaStream_t s);   // y += x
+// Residual norms per DOF chunk (see k_chunk_norms): out = [r^2 | f^2 | F^2][nc].
+cudaError_t vec_chunk_norms(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof,
+                            const double* r, const int64_t* chunks, int64_t nc, double* out, cudaStream_t s);
 cudaError_t vec_cvt_f32(const double* x, float* y, int64_t n, cudaStream_t s);    // y = (float) x
 cudaError_t vec_cvt_f64(const float* x, double* y, int64_t n, cudaStream_t s);    // y = (double) x
 cudaError_t vec_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);

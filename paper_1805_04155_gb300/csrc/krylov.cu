@@ -1223,6 +1223,39 @@ __global__ void __launch_bounds__(VB) k_residual(const double* __restrict__ f_un
     }
 }
 
+// Per-chunk sums of r^2, (zeta f)^2 on free DOFs and F^2 over DOF chunks [beg, end) (one CTA per
+// chunk; chunks never straddle two problems of a batch).  chunks = [problem | begin | end][nc].
+__global__ void __launch_bounds__(VB) k_chunk_norms(const double* __restrict__ f_unit, double zeta,
+                                                     const double* __restrict__ F, const uint8_t* __restrict__ free_dof,
+                                                     const double* __restrict__ r, const int64_t* __restrict__ chunks,
+                                                     int64_t nc, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int64_t c = blockIdx.x;
+    const int64_t beg = chunks[nc + c], end = chunks[2 * nc + c];
+    double s_r = 0.0, s_f = 0.0, s_F = 0.0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        const double fi = f_unit ? zeta * f_unit[i] : 0.0;
+        s_r += r[i] * r[i];
+        s_f += free_dof[i] ? fi * fi : 0.0;
+        s_F += F[i] * F[i];
+    }
+    const double a = block_sum(s_r, sh);
+    const double b = block_sum(s_f, sh);
+    const double d = block_sum(s_F, sh);
+    if (threadIdx.x == 0) {
+        out[c] = a;
+        out[nc + c] = b;
+        out[2 * nc + c] = d;
+    }
+}
+
+cudaError_t vec_chunk_norms(const double* f_unit, double zeta, const double* F, const uint8_t* free_dof,
+                            const double* r, const int64_t* chunks, int64_t nc, double* out, cudaStream_t s) {
+    if (nc <= 0) return cudaSuccess;
+    k_chunk_norms<<<(unsigned)nc, VB, 0, s>>>(f_unit, zeta, F, free_dof, r, chunks, nc, out);
+    return cudaGetLastError();
+}
+
 __global__ void k_finalize3(const double* part, int nparts, double* out3) {
     __shared__ double sh[32];
     for (int k = 0; k < 3; ++k) {

@@ -30,7 +30,7 @@ EP_FP64, EP_MIXED = range(2)
  EP_K_VALUES, EP_K_ELASTIC, EP_WEIGHT, EP_DPHI, EP_SOLUTION, EP_K_VALUES_F32) = range(14)
 
 EXPORTED = [
-    "ep_default_opts", "ep_create", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set",
+    "ep_default_opts", "ep_create", "ep_create_batch", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set",
     "ep_assemble", "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error",
     "ep_linear_solve_noalloc",
 ]
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_default_opts.argtypes = [C.POINTER(ep_opts)]
     lib.ep_default_opts.restype = None
     lib.ep_create.argtypes = [C.POINTER(vp), C.POINTER(ep_mesh), C.POINTER(ep_material), C.POINTER(ep_bc), i32, vp]
+    lib.ep_create_batch.argtypes = [C.POINTER(vp), i32, C.POINTER(ep_mesh), C.POINTER(ep_material), C.POINTER(ep_bc),
+                                    i32, vp]
     lib.ep_destroy.argtypes = [vp]
     lib.ep_get_info.argtypes = [vp, C.POINTER(ep_info)]
     lib.ep_solve_load_path.argtypes = [vp, i32, dp, C.POINTER(ep_opts), C.POINTER(ep_step_report)]
@@ -102,7 +104,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_status_str.restype = C.c_char_p
     lib.ep_last_error.argtypes = [vp]
     lib.ep_last_error.restype = C.c_char_p
-    for name in ("ep_create", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set", "ep_assemble",
+    for name in ("ep_create", "ep_create_batch", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set", "ep_assemble",
                  "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive"):
         getattr(lib, name).restype = i32
     return lib
@@ -187,6 +189,49 @@ class Context:
         m = problem.mesh
         return cls(m.coords, m.elem, m.elem_type, problem.material, problem.dirichlet, problem.u_D_unit,
                    problem.f_unit, **kw)
+
+    @classmethod
+    def from_batch(cls, problems, device: int = 0, stream=None):
+        """ep_create_batch over problems of one element type; fields are concatenated in order."""
+        n = len(problems)
+        meshes, mats, bcs = (ep_mesh * n)(), (ep_material * n)(), (ep_bc * n)()
+        keep = []
+        for i, pb in enumerate(problems):
+            m = pb.mesh
+            co = np.ascontiguousarray(m.coords, dtype=np.float64)
+            el = np.ascontiguousarray(m.elem, dtype=np.int32)
+            mk = np.ascontiguousarray(pb.dirichlet, dtype=np.uint8)
+            ud = np.ascontiguousarray(pb.u_D_unit, dtype=np.float64)
+            fe = np.ascontiguousarray(pb.f_unit, dtype=np.float64)
+            keep += [co, el, mk, ud, fe]
+            meshes[i] = ep_mesh(co.shape[1], ELEM_IDS[m.elem_type], co.shape[0], el.shape[0], _ptr(co, C.c_double),
+                                _ptr(el, C.c_int32))
+            mats[i] = make_material(pb.material)
+            bcs[i] = ep_bc(_ptr(mk, C.c_uint8), _ptr(ud, C.c_double), _ptr(fe, C.c_double))
+        h = C.c_void_p()
+        st = lib().ep_create_batch(C.byref(h), n, meshes, mats, bcs, int(device), C.c_void_p(_stream_ptr(stream)))
+        if st != EP_OK:
+            raise EPError(st, lib().ep_last_error(None).decode())
+        self = cls.__new__(cls)
+        self._keep = []
+        self.h = h
+        self.material = mats[0]
+        info = ep_info()
+        lib().ep_get_info(h, C.byref(info))
+        self.info = info
+        self.dim = info.dim
+        self.n_dof = info.n_nodes * info.dim
+        self.node_off = np.cumsum([0] + [pb.mesh.n_nodes for pb in problems])
+        self.ip_off = np.cumsum([0] + [pb.mesh.n_elem for pb in problems]) * info.n_q
+        return self
+
+    def split(self, field, arr):
+        """Per-problem views of a concatenated batch field (EP_U, EP_F_INT, or a [n_comp][n_int] field)."""
+        if field in (EP_U, EP_F_INT, EP_SOLUTION):
+            o = self.node_off * self.dim
+            return [arr[o[i]:o[i + 1]] for i in range(len(o) - 1)]
+        o = self.ip_off
+        return [arr[..., o[i]:o[i + 1]] for i in range(len(o) - 1)]
 
     def close(self):
         if getattr(self, "h", None):

@@ -193,6 +193,33 @@ def generic_box(elem_type: str, dim: int, n: int, material: Material, t_max: flo
                    np.zeros(mesh.n_nodes * 3), f_unit, zeta)
 
 
+def batch_problems(seed: int = 1805, n_problems: int = 64, sizes=(16, 96), scale: float = 0.3,
+                   families=None, n_steps: int = 10):
+    """The batched sweep: independent problems with mesh sizes drawn uniformly from `sizes` elements
+    per side and E, nu, Y, H each drawn from [1 - scale, 1 + scale] times the P1-column material;
+    half 2D (P1 and P2 columns), half 3D (Q1 cubes).  Returns {family: [problems]} (one batch per
+    element type), deterministic in `seed`."""
+    g = np.random.default_rng(seed)
+    fams = families or (["P1"] * (n_problems // 4) + ["P2"] * (n_problems // 4)
+                        + ["Q1"] * (n_problems - 2 * (n_problems // 4)))
+    base = vm_iso_material()
+    out: dict = {}
+    for i, fam in enumerate(fams):
+        n = int(g.integers(sizes[0], sizes[1] + 1))
+        f = g.uniform(1 - scale, 1 + scale, 4)
+        nu = min(0.45, base.nu * f[1])
+        mat = Material(VM_ISO, E=base.E * f[0], nu=nu, Y=base.Y * f[2], H=base.H * f[3])
+        if fam == "Q1":
+            p = q1_cube_vm(n=n, n_steps=n_steps)
+            p.material = mat
+        else:
+            t_y = first_yield_traction_vm(mat.E, mat.nu, mat.Y)
+            p = plane_column(fam, n, mat, 1.5 * t_y, n_steps)
+        p.name = f"batch{i}_{fam}_{n}"
+        out.setdefault(fam, []).append(p)
+    return out
+
+
 WORKLOADS = {
     "p1_plane_vm": p1_plane_vm,
     "p2_plane_dp": p2_plane_dp,

@@ -71,3 +71,21 @@ def test_create_rejects_bad_input_without_gpu_work(libpath):
     st = lib.ep_create(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(mat), ctypes.byref(bc), 0, None)
     assert st == ep.EP_ERR_INVALID_ARG      # dim = 4
     assert lib.ep_create(None, None, None, None, 0, None) == ep.EP_ERR_INVALID_ARG
+
+
+def test_batch_rejects_mixed_element_types_without_gpu_work(libpath):
+    """ep_create_batch validates the problems before any CUDA call."""
+    import numpy as np
+    import paper_1805_04155_gb300.ep as ep
+    lib = ep.lib()
+    c2 = np.zeros((3, 2)); e2 = np.array([[0, 1, 2]], dtype=np.int32)
+    c3 = np.zeros((4, 3)); e3 = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    meshes = (ep.ep_mesh * 2)(ep.ep_mesh(2, 0, 3, 1, P(c2, ctypes.c_double), P(e2, ctypes.c_int32)),
+                              ep.ep_mesh(3, 0, 4, 1, P(c3, ctypes.c_double), P(e3, ctypes.c_int32)))
+    mats = (ep.ep_material * 2)(ep.ep_material(0, 1.0, 0.3, 0, 0, 0, 0, 0, 0), ep.ep_material(0, 1.0, 0.3, 0, 0, 0, 0, 0, 0))
+    m2 = np.zeros(6, dtype=np.uint8); m3 = np.zeros(12, dtype=np.uint8)
+    bcs = (ep.ep_bc * 2)(ep.ep_bc(P(m2, ctypes.c_uint8), None, None), ep.ep_bc(P(m3, ctypes.c_uint8), None, None))
+    h = ctypes.c_void_p()
+    assert lib.ep_create_batch(ctypes.byref(h), 2, meshes, mats, bcs, 0, None) == ep.EP_ERR_INVALID_ARG
+    assert b"different element type" in lib.ep_last_error(None)

@@ -212,3 +212,17 @@ def test_newton_quadratic_convergence_von_mises():
     good = [h for h in hist if h > 1e-13]
     ratios = [math.log(good[i + 1]) / math.log(good[i]) for i in range(len(good) - 1) if good[i] < 1e-2]
     assert ratios and max(ratios) > 1.6, hist
+
+
+def test_batch_problem_generator_is_seeded_and_uneven():
+    """The batched sweep's inputs: deterministic in the seed, sizes and materials within range."""
+    from synthetic import batch_problems, vm_iso_material
+    a = batch_problems(seed=1805, n_problems=8, sizes=(2, 5), n_steps=3)
+    b = batch_problems(seed=1805, n_problems=8, sizes=(2, 5), n_steps=3)
+    assert sorted(a) == ["P1", "P2", "Q1"] and sum(len(v) for v in a.values()) == 8
+    base = vm_iso_material()
+    for fam in a:
+        for pa, pb in zip(a[fam], b[fam]):
+            assert pa.mesh.n_elem == pb.mesh.n_elem and pa.material == pb.material
+            assert 0.7 * base.E <= pa.material.E <= 1.3 * base.E
+            assert 0.7 * base.Y <= pa.material.Y <= 1.3 * base.Y
