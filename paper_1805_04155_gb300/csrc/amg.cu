@@ -93,7 +93,7 @@ struct ChebCoef {
 };
 
 __device__ __forceinline__ ChebCoef cheb_coef(double lambda, int step) {
-    const double beta = 1.1 * lambda, alpha = beta / 30.0;
+    const double beta = 1.15 * lambda, alpha = beta / 30.0;
     const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
     const double sigma = theta / delta;
     double rho_prev = 1.0 / sigma, rho = rho_prev;
@@ -394,9 +394,23 @@ __global__ void __launch_bounds__(AB) k_pw_apply(Mat<T> A, const T* __restrict__
     }
 }
 
-// lambda = ||y|| (x had unit norm); x = y / ||y||
+// Start vector of the power iteration: positive pseudo-random entries (splitmix64 of the index),
+// zero on prescribed DOFs.
 template <class T>
-__global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, T* y, T* x, int64_t n, double* lam) {
+__device__ __forceinline__ T pw_start(int64_t i, int64_t n, const uint8_t* mask) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 12345ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double v = (double)(z >> 11) * (1.0 / 9007199254740992.0) + 0.5;
+    return (mask && !mask[i]) ? T(0) : (T)(v / sqrt((double)n));
+}
+
+// lambda = ||y|| (x had unit norm); x = y / ||y||, or the start vector again if ||y|| is zero or
+// not finite (so a warm-started iteration recovers from a bad tangent)
+template <class T>
+__global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, T* y, T* x, int64_t n, double* lam,
+                                                 const uint8_t* mask) {
     __shared__ double tot;
     if (threadIdx.x < 32) {
         double v = 0.0;
@@ -413,20 +427,15 @@ __global__ void __launch_bounds__(AB) k_pw_norm(const double* part, int nparts, 
     }
     __syncthreads();
     const T inv = (T)s_inv;
+    const bool ok = s_inv > 0.0 && isfinite(s_inv);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = y[i] * inv;
+        x[i] = ok ? y[i] * inv : pw_start<T>(i, n, mask);
 }
 
 template <class T>
 __global__ void k_pw_init(T* x, int64_t n, const uint8_t* mask) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 12345ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        const double v = (double)(z >> 11) * (1.0 / 9007199254740992.0) + 0.5;
-        x[i] = (mask && !mask[i]) ? T(0) : (T)(v / sqrt((double)n));
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = pw_start<T>(i, n, mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -621,6 +630,7 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
     if ((e = dvec(D, &D.coef, AMG_MAX_LEVELS * AMG_CHEB_DEGREE * 3)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw, 2)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pwf, 2 * H.levels[0].n)) != cudaSuccess) return e;
+    if ((e = dvec(D, &D.pw0, H.levels[0].n)) != cudaSuccess) return e;
     if ((e = dvec(D, &D.pw_part, D.nparts)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(D.lam, lam.data(), sizeof(double) * AMG_MAX_LEVELS, cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
@@ -634,18 +644,22 @@ void amg_free(AmgDev& D) {
 }
 
 template <class T>
+// Power iteration for rho(D^-1 A): `its` steps from x (a fresh pseudo-random vector when init).
+// The estimate approaches rho from below; the Chebyshev interval adds a safety margin, and a
+// warm start from the previous refresh's vector keeps the level-0 estimate converged although
+// the top eigenvalues of a batch of similar problems are clustered.
 static void power(AmgDev& D, int bs, const Mat<T>& A, const T* dinv, T* x, T* y, int64_t n, const uint8_t* mask,
-                  double* lam, cudaStream_t s) {
-    k_pw_init<T><<<256, 256, 0, s>>>(x, n, mask);
-    for (int it = 0; it < 12; ++it) {
+                  double* lam, cudaStream_t s, bool init = true, int its = 12) {
+    if (init) k_pw_init<T><<<256, 256, 0, s>>>(x, n, mask);
+    for (int it = 0; it < its; ++it) {
         switch (bs) {
             case 2: k_pw_apply<2, 4, T><<<D.nparts, AB, 0, s>>>(A, dinv, x, y, D.pw_part); break;
             case 3: k_pw_apply<3, 8, T><<<D.nparts, AB, 0, s>>>(A, dinv, x, y, D.pw_part); break;
             case 6: k_pw_apply<6, 8, T><<<D.nparts, AB, 0, s>>>(A, dinv, x, y, D.pw_part); break;
         }
-        k_pw_norm<T><<<256, AB, 0, s>>>(D.pw_part, D.nparts, y, x, n, lam);
+        k_pw_norm<T><<<256, AB, 0, s>>>(D.pw_part, D.nparts, y, x, n, lam, mask);
     }
-    D.launches += 25;
+    D.launches += 2 * its + (init ? 1 : 0);
 }
 
 template <class TA>
@@ -709,7 +723,8 @@ static cudaError_t refresh_core(AmgDev& D, const BsrT<T>& A0, int galerkin, cuda
     const int d0 = A0.dim;
     const int64_t n0 = A0.n_rows * d0;
     const Mat<float> M0 = mat0f(A0, D.K0);
-    power<float>(D, d0, M0, D.minv0, D.pwf, D.pwf + n0, n0, A0.free_dof, D.lam + 0, s);
+    power<float>(D, d0, M0, D.minv0, D.pw0, D.pwf, n0, A0.free_dof, D.lam + 0, s, !D.pw0_valid, 16);
+    D.pw0_valid = true;
     if (!galerkin || L < 2) {
         k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
         D.launches += 1;

@@ -93,6 +93,8 @@ struct AmgDev {
     int deg_c = 2;                     // ... on the coarse levels (both sides)
     double* pw = nullptr;              // power-iteration work [2][n0] (FP64)
     float* pwf = nullptr;              // power-iteration work [2][n1] (FP32)
+    float* pw0 = nullptr;              // level-0 eigenvector estimate, kept between refreshes [n0]
+    bool pw0_valid = false;
     double* pw_part = nullptr;
     int nparts = 0;
     std::vector<void*> allocs;

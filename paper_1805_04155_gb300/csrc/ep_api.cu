@@ -1095,8 +1095,11 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 }
                 if (kst != EP_OK && krel < 0.5) kst = EP_OK;   // partial progress: an inexact Newton step
             } else {
+                // inside Newton a solve that needs far more than the usual count is not worth
+                // finishing: its partial progress is taken as an inexact step
+                const int maxit64 = std::min(o.krylov_maxit, std::max(2000, 20 * c->kw.last_its));
                 CK(krylov_precond(A, c->kw, o.precond, s));
-                CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &kits, &krel, &kst));
+                CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &kits, &krel, &kst));
             }
             c->kw.stall_guard = 0;
             CK(cudaEventRecord(c->ev[3], s));
