@@ -52,6 +52,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 def _workload(name: str, full: bool = True, n: int = 0):
     from synthetic import problems as P
     if n:
+        if name == "l_shape_vm":
+            return P.l_shape_vm("Q2", m=n)
         return {"p2_plane_dp": P.p2_plane_dp, "p1_plane_vm": P.p1_plane_vm, "q1_cube_vm": P.q1_cube_vm,
                 "p2_tet_strip_dp": P.p2_tet_strip_dp}[name](n=n)
     if name == "p2_plane_dp":
@@ -62,6 +64,8 @@ def _workload(name: str, full: bool = True, n: int = 0):
         return P.q1_cube_vm() if full else P.q1_cube_vm(n=16)
     if name == "p2_tet_strip_dp":
         return P.p2_tet_strip_dp() if full else P.p2_tet_strip_dp(n=12)
+    if name == "l_shape_vm":
+        return P.l_shape_vm("Q2", m=40) if full else P.l_shape_vm("Q2", m=10)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -491,6 +495,20 @@ def main():
             roof_asm.update({"achieved": fp64_flops / dur / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS})
     dominant = roof_spmv if (roof_spmv and t_spmv >= t_asmk) else roof_asm
+    # the paper's observation (Section 8.2): tangent-assembly time is linear in the number of
+    # plastic points; fit over the timed steps' assemblies (per-step averages)
+    xs = [r.n_plastic_assembled / r.n_assemble for r in reps if r.n_assemble]
+    ys = [1e3 * r.t_assemble_kernel_ms / r.n_assemble for r in reps if r.n_assemble]
+    asm_fit = None
+    if len(set(np.round(xs, 6))) >= 2:
+        A = np.vstack([np.ones(len(xs)), xs]).T
+        (b0, b1), *_ = np.linalg.lstsq(A, np.array(ys), rcond=None)
+        pred = b0 + b1 * np.array(xs)
+        ss = float(np.sum((np.array(ys) - np.mean(ys)) ** 2))
+        asm_fit = {"us_no_plastic": float(b0), "us_per_1k_plastic": float(b1 * 1e3),
+                   "us_all_plastic_extrapolated": float(b0 + b1 * n_int),
+                   "r2": 1.0 - float(np.sum((np.array(ys) - pred) ** 2)) / ss if ss > 0 else None,
+                   "points": len(xs)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -508,6 +526,8 @@ def main():
             "n_plastic_final": int(reps[-1].n_plastic) if reps else 0,
             "max_rel_resid": max(r.rel_resid for r in reps) if reps else None,
             "wall_s": wall}
+    if asm_fit:
+        line["assembly_vs_plastic"] = asm_fit
     if compare:
         line["compare"] = compare
     if e2e:

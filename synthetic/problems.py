@@ -220,9 +220,66 @@ def batch_problems(seed: int = 1805, n_problems: int = 64, sizes=(16, 96), scale
     return out
 
 
+def l_shape_vm(elem_type: str = "Q2", m: int = 20, n_steps: int = 40, f_max: float = 200.0) -> Problem:
+    """The L-shaped body of the von Mises experiment (Section 8.2): [0,10]^2 without the square
+    [0,5)^2, m cells per side of each of its three squares; rollers on the left (x = 0) and bottom
+    (y = 0) sides, a normal traction zeta(t) f_max on the top side, zeta rising linearly from 0 to 1
+    on t in [0, 1], falling to -1 at t = 3 and returning to 0 at t = 4 (n_steps equal time steps);
+    von Mises with linear kinematic hardening a = 1e4, Y = 450 sqrt(2/3), E = 206900, nu = 0.29."""
+    box = structured_mesh(elem_type, 2, (2 * m, 2 * m), (10.0, 10.0))
+    cent = box.coords[box.elem].mean(axis=1)
+    keep = ~((cent[:, 0] < 5.0) & (cent[:, 1] < 5.0))
+    elem = box.elem[keep]
+    used = np.unique(elem)
+    remap = -np.ones(box.n_nodes, dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    mesh = Mesh(elem_type, 2, box.coords[used].copy(), remap[elem].astype(np.int32), box.shape, box.size)
+    dirichlet = _mask(mesh, [(0, "min", 0), (1, "min", 1)])
+    f_unit = traction_load(mesh, (0.0, f_max))
+    t = np.arange(1, n_steps + 1, dtype=np.float64) * (4.0 / n_steps)
+    zeta = np.where(t <= 1.0, t, np.where(t <= 3.0, 2.0 - t, t - 4.0))
+    mat = Material(VM_KIN, E=206900.0, nu=0.29, Y=450.0 * math.sqrt(2.0 / 3.0), H=1e4)
+    p = Problem(f"l_shape_vm_{elem_type}_{m}", mesh, mat, dirichlet, np.zeros(mesh.n_nodes * 2), f_unit, zeta)
+    p.extra["f_max"] = f_max
+    return p
+
+
+def strip_footing_dp(elem_type: str = "P2", n: int = 160, footing: float = 1.0) -> Problem:
+    """The strip-footing benchmark of the Drucker-Prager experiment (Section 8.3): [0,10]^2, rollers
+    on the left, right and bottom sides, a footing of width `footing` at the top-left corner pushed
+    down by the prescribed vertical displacement u_D = zeta (u_D_unit = -1 under the footing, zeta
+    from 0 to 1); associated Drucker-Prager, perfectly plastic, E = 1e7, nu = 0.48, c0 = 450,
+    phi = pi/9.  The default zeta is a uniform path; the paper doubles the increment adaptively
+    (paper_1805_04155_gb300.drivers)."""
+    mesh = structured_mesh(elem_type, 2, (n, n), (10.0, 10.0))
+    dirichlet = _mask(mesh, [(0, "min", 0), (0, "max", 0), (1, "min", 1)]).reshape(-1, 2)
+    u_D = np.zeros((mesh.n_nodes, 2))
+    top = boundary_nodes(mesh, 1, "max")
+    under = top[mesh.coords[top, 0] <= footing + 1e-9]
+    dirichlet[under, 1] = 1
+    u_D[under, 1] = -1.0
+    mat = Material(DP, E=1e7, nu=0.48, c0=450.0, phi=math.pi / 9.0, psi=math.pi / 9.0)
+    zeta = np.linspace(0.001, 0.01, 10)
+    p = Problem(f"strip_footing_dp_{elem_type}_{n}", mesh, mat, dirichlet.ravel(), u_D.ravel(),
+                np.zeros(mesh.n_nodes * 2), zeta)
+    p.extra["footing"] = footing
+    p.extra["footing_nodes"] = under
+    return p
+
+
+def prandtl_nc(phi: float) -> float:
+    """Prandtl's bearing-capacity factor N_c = (N_q - 1) cot(phi), N_q = exp(pi tan phi) tan^2(pi/4 +
+    phi/2): limit pressure c N_c of a smooth strip footing on a weightless Mohr-Coulomb half-space
+    (the classical closed form the strip-footing benchmark approaches)."""
+    nq = math.exp(math.pi * math.tan(phi)) * math.tan(math.pi / 4.0 + phi / 2.0) ** 2
+    return (nq - 1.0) / math.tan(phi)
+
+
 WORKLOADS = {
     "p1_plane_vm": p1_plane_vm,
     "p2_plane_dp": p2_plane_dp,
     "q1_cube_vm": q1_cube_vm,
     "p2_tet_strip_dp": p2_tet_strip_dp,
+    "l_shape_vm": l_shape_vm,
+    "strip_footing_dp": strip_footing_dp,
 }

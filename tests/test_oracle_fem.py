@@ -226,3 +226,37 @@ def test_batch_problem_generator_is_seeded_and_uneven():
             assert pa.mesh.n_elem == pb.mesh.n_elem and pa.material == pb.material
             assert 0.7 * base.E <= pa.material.E <= 1.3 * base.E
             assert 0.7 * base.Y <= pa.material.Y <= 1.3 * base.Y
+
+
+def test_l_shape_and_strip_footing_inputs():
+    """The validation workloads' meshes and loads: L-shape area 75 and total traction; footing nodes."""
+    from synthetic import l_shape_vm, strip_footing_dp
+    p = l_shape_vm("Q2", m=3, n_steps=40)
+    g = Geometry(p.mesh.coords, p.mesh.elem, "Q2", 2)
+    assert abs(g.WEIGHT.sum() - 75.0) < 1e-10
+    np.testing.assert_allclose(p.f_unit.reshape(-1, 2).sum(0), [0.0, 2000.0], rtol=1e-13)
+    assert p.zeta.max() == 1.0 and p.zeta.min() == -1.0 and abs(p.zeta[-1]) < 1e-12
+    q = strip_footing_dp("P2", n=10)
+    xs = q.mesh.coords[q.extra["footing_nodes"]]
+    assert np.all(xs[:, 0] <= 1.0 + 1e-9) and np.all(np.abs(xs[:, 1] - 10.0) < 1e-9)
+    assert len(xs) == 3          # x = 0, 0.5, 1 on a 10x10 P2 mesh
+
+
+def test_prandtl_factor_closed_form():
+    """N_c -> 2 + pi as phi -> 0 (Prandtl's cohesive limit) and N_c(30 deg) = 30.14 (textbook)."""
+    from synthetic import prandtl_nc
+    assert abs(prandtl_nc(1e-6) - (2.0 + math.pi)) < 1e-4
+    assert abs(prandtl_nc(math.radians(30.0)) - 30.14) < 0.01
+
+
+def test_oracle_l_shape_cycle_dissipates():
+    """The oracle on the cyclic L-shape: plastic flow on loading, a residual state after the cycle."""
+    from synthetic import l_shape_vm
+    p = l_shape_vm("Q1", m=2, n_steps=8)
+    s = OracleSolver(p)
+    work = []
+    for z in p.zeta:
+        s.solve_step(float(z), tol=1e-12)
+        work.append(float(p.f_unit @ s.u))
+    assert np.abs(s.ep).max() > 0
+    assert abs(work[-1]) > 1e-3 * max(abs(w) for w in work)
