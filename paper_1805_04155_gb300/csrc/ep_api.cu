@@ -941,20 +941,33 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         c->kw.spmv_ms = 0.0;
         double t_asm_kernel = 0.0;
         const double z = zeta[k];
-        // start iterate
+        ep_status st = EP_OK;
+        double rel = 0.0;
+        int it = 0;
+        bool converged = false;
+        // Start iterate: the last converged u with the new Dirichlet values, plus (warm_start = 1)
+        // the linear extrapolation of the last two steps while the load keeps its direction.  A
+        // step that does not converge from the extrapolated start (a predictor past a change of
+        // the plastic regime) is retried once from the unextrapolated one.
+        for (int attempt = 0; attempt < 2; ++attempt) {
+        bool extrapolated = false;
         CK(cudaMemcpyAsync(c->u_it, c->u, sizeof(double) * c->n_dof, cudaMemcpyDeviceToDevice, s));
-        if (o.warm_start == 1 && c->n_committed >= 2 && c->zeta_last != c->zeta_prev) {
+        if (attempt == 0 && o.warm_start == 1 && c->n_committed >= 2 && c->zeta_last != c->zeta_prev) {
             const double ratio = (z - c->zeta_last) / (c->zeta_last - c->zeta_prev);
-            CK(vec_extrapolate(c->u_it, c->u_prev, ratio, c->n_dof, s));
-            c->launches += 1;
+            if (ratio > 0.0) {
+                CK(vec_extrapolate(c->u_it, c->u_prev, ratio, c->n_dof, s));
+                c->launches += 1;
+                extrapolated = true;
+            }
         }
         CK(vec_set_dirichlet(c->u_it, c->uD_unit, z, c->free_dof, c->n_dof, s));
         c->launches += 1;
         CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
-        ep_status st = EP_OK;
-        double rel = 0.0, rnorm_prev = -1.0;
-        int it = 0;
-        bool converged = false;
+        st = EP_OK;
+        rel = 0.0;
+        it = 0;
+        converged = false;
+        double rnorm_prev = -1.0, rel_best = 1e300;
         bool use32 = false;      // this iteration's tangent and solve in FP32
         bool fp64_step = false;  // the rest of this step in FP64 (an FP32 iteration contracted poorly)
         double eta_prev = 1.0;   // Krylov tolerance of the last solve
@@ -1023,6 +1036,14 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             if (it >= o.newton_maxit) {
                 st = EP_ERR_NEWTON_NO_CONVERGENCE;
                 c->err = "Newton: no convergence in " + std::to_string(o.newton_maxit) + " iterations";
+                break;
+            }
+            // from an extrapolated start, a residual that keeps growing (10x above the best after 5
+            // iterations) ends the attempt early
+            rel_best = std::min(rel_best, rel);
+            if (extrapolated && it >= 5 && rel > 10.0 * rel_best) {
+                st = EP_ERR_NEWTON_NO_CONVERGENCE;
+                c->err = "Newton: diverging from the extrapolated start";
                 break;
             }
             // forcing term
@@ -1143,6 +1164,11 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             t_sol += ms;
             ++it;
         }
+        if (converged || !extrapolated ||
+            (st != EP_ERR_NEWTON_NO_CONVERGENCE && st != EP_ERR_KRYLOV && st != EP_ERR_NAN))
+            break;
+        if (c->verbose) std::fprintf(stderr, "[ep] step %d: retrying from the last converged state\n", k);
+        }   // attempt
         rep.newton_its = it;
         rep.rel_resid = rel;
         rep.t_assemble_ms = t_asm;
