@@ -184,8 +184,11 @@ def _base_flops_per_point(dim, n_p):
 
 
 def run_reference(args):
-    """The CPU oracle, as it stands, on a reduced copy of the workload."""
+    """The CPU oracle, as it stands, on a bounded sample of the workload: a reduced copy of its
+    mesh with the same material, boundary conditions and load path (the line names the workload;
+    cpu_baseline.sample names the sample)."""
     from oracle.newton import OracleSolver
+    full = _workload(args.workload, full=True, n=args.n)
     prob = _workload(args.workload, full=False)
     s = OracleSolver(prob)
     n_path = len(prob.zeta)
@@ -207,7 +210,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _workload_config(args.workload, prob, {"n_int": n_int}), "impl": "reference",
+            "config": _workload_config(args.workload, full, {"n_int": full.mesh.n_elem * (n_int // prob.mesh.n_elem)}),
+            "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -241,6 +245,23 @@ def cpu_baseline(args, budget_s=15.0):
             "sample": f"first {steps} load steps of a reduced copy ({prob.mesh.elem_type} "
                       f"{'x'.join(map(str, prob.mesh.shape))}, {s.geom.n_int} points), splu solves, "
                       f"{dt:.1f} s"}
+
+
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """Replicas (the path does not shard): every rank solves its own copy; the job's time is the
+    slowest rank's.  The only collective is this timing reduction."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def job_value(world: int, n_int: int, assemblies: int, ms: float) -> float:
+    """Whole-job throughput in Gpts/s: the points all ranks assembled over the job's time."""
+    return world * n_int * assemblies / (ms / 1e3) / 1e9
 
 
 def run_batch(args):
@@ -391,13 +412,6 @@ def main():
         wall = time.perf_counter() - t_wall0
         return ms, wall, reps
 
-    def max_over_ranks(ms):
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
-
     if args.no_compare:
         precs = ["mixed" if args.precision == "auto" else args.precision]
     else:
@@ -415,13 +429,13 @@ def main():
     for p_ in precs:
         reset()
         ms_p, wall_p, reps_p = timed(p_, False, args.steps, args.skip)
-        runs[p_] = (max_over_ranks(ms_p), wall_p, reps_p, ctx.get(ep.EP_U) if ends_on_path_end else None)
+        runs[p_] = (max_over_ranks(ms_p, world), wall_p, reps_p, ctx.get(ep.EP_U) if ends_on_path_end else None)
     clk = clocks.stop()
     prec = args.precision if args.precision != "auto" else min(runs, key=lambda k: runs[k][0])
     ms, wall, reps, u_primary = runs[prec]
     assemblies = sum(r.n_assemble for r in reps)
     n_int = info.n_int
-    value = world * n_int * assemblies / (ms / 1e3) / 1e9
+    value = job_value(world, n_int, assemblies, ms)
 
     compare = None
     others = [p_ for p_ in precs if p_ != prec]
@@ -444,7 +458,7 @@ def main():
     if not args.no_e2e:
         reset()
         ms_e2e, _, reps_e2e = timed(prec, True, args.steps, args.skip)
-        ms_e2e = max_over_ranks(ms_e2e)
+        ms_e2e = max_over_ranks(ms_e2e, world)
         a2 = sum(r.n_assemble for r in reps_e2e)
         e2e = {"value": world * n_int * a2 / (ms_e2e / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8,
                "d2h_bytes_per_step": int(ctx.n_dof * 8)}
