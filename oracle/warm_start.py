@@ -7,15 +7,24 @@ Section 4); the build's default start is the linear extrapolation
     u_ex = u_{k-1} + r_k (u_{k-1} - u_{k-2}),  r_k = (zeta_k - zeta_{k-1}) / (zeta_{k-1} - zeta_{k-2}),
 with the Dirichlet values of step k.  The learned start adds a per-node
 correction predicted by a small MLP from the node's recent history:
-    u_L = u_ex + s * y[:dim]  on free DOFs,
-where s is the problem's RMS increment of the last step.  The definitions here
+    u_L = u_ex + s * P(y[:dim])  on free DOFs,
+where s is the problem's RMS increment of the last step and P projects the
+per-node prediction, per problem and displacement component, onto the span of
+the last two increments (least squares over the free DOFs).  The projection
+keeps the correction as smooth as the increments: per-node predictions carry
+independent errors of a few percent, whose roughness the stiffness turns into
+residuals larger than those of the plain extrapolation.  The definitions here
 are the ones the CUDA path must reproduce:
 
   node_plastic_fraction  fraction of the integration points of the elements
                          adjacent to a node that are plastic (flag != 0)
+  yield_proximity        yield-function ratio of a committed stress (1 on the
+                         yield surface), and node_max its maximum over the
+                         points of the adjacent elements
   static_features        material and boundary scalars of a node
   features               the 16 inputs of a node for step k
   targets                the 4 outputs the MLP is trained on after step k converged
+  project_correction     the projection P above
   mlp_forward / mlp_loss / mlp_grad   3 linear layers 16 -> 128 -> 128 -> 4, ReLU,
                          weights rounded to bfloat16, biases and activations
                          kept exact (FP64 here, FP32 on the device)
@@ -34,11 +43,17 @@ and against torch's conversion; forward pass against explicit loops; gradient
 against central finite differences; Adam against the constant-gradient closed
 form; plastic fractions against a brute-force scan; features and targets
 against the homogeneous elastic column, whose equally spaced steps make the
-extrapolation exact.
+extrapolation exact; the proximity against the return mappings (exactly 1 at
+plastic points, below 1 at elastic ones); the projection against fields that
+lie in the span and the orthogonality of what it removes.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
+
+from . import constitutive as C
 
 N_IN, WIDTH, N_OUT = 16, 128, 4
 OFF_W1 = 0
@@ -157,22 +172,61 @@ def node_plastic_fraction(elem, plastic, n_q: int, n_nodes: int) -> np.ndarray:
     return np.where(cnt_ip > 0, cnt_pl / np.maximum(cnt_ip, 1), 0.0)
 
 
+def yield_proximity(material, dim: int, stress, hard) -> np.ndarray:
+    """Per integration point, the ratio of the yield function's stress part to its current limit
+    for a committed stress (stored layout: (11, 22, 12, 33) in 2D, Voigt in 3D), clamped at 0:
+      von Mises, isotropic:  |dev s| / (Y + H alpha)           (Section 2.2, with the extension)
+      von Mises, kinematic:  |dev s - beta| / Y
+      Drucker-Prager:        (|dev s| / sqrt(2) + eta p) / (c + Hc alpha),  p = tr(s)/3  (Section 2.3)
+      elastic:               0
+    with |x|^2 = x11^2 + x22^2 + x33^2 + 2 (x12^2 + x23^2 + x13^2) (tensor norm of a stress-type vector)."""
+    m = material
+    model = int(m.model)
+    S = C.embed_state(np.asarray(stress, dtype=np.float64), dim)
+    n = S.shape[1]
+    if model == 0:
+        return np.zeros(n)
+    mean = (S[0] + S[1] + S[2]) / 3.0
+    dev = S.copy()
+    dev[0:3] -= mean
+    if model == 1:
+        dev = dev - C.embed_state(np.asarray(hard, dtype=np.float64), dim)
+    nrm = np.sqrt(dev[0] ** 2 + dev[1] ** 2 + dev[2] ** 2 + 2.0 * (dev[3] ** 2 + dev[4] ** 2 + dev[5] ** 2))
+    if model == 1:
+        q = nrm / m.Y
+    elif model == 2:
+        q = nrm / (m.Y + m.H * np.asarray(hard, dtype=np.float64))
+    else:
+        eta, c, _ = C.dp_parameters(m.c0, m.phi, m.psi, dim)
+        q = (nrm / math.sqrt(2.0) + eta * mean) / (c + m.Hc * np.asarray(hard, dtype=np.float64))
+    return np.maximum(q, 0.0)
+
+
+def node_max(elem, values, n_q: int, n_nodes: int) -> np.ndarray:
+    """Per node: the largest value over the integration points of the elements containing it."""
+    elem = np.asarray(elem)
+    ve = np.asarray(values).reshape(-1, n_q).max(axis=1)
+    out = np.zeros(n_nodes)
+    for p in range(elem.shape[1]):
+        np.maximum.at(out, elem[:, p], ve)
+    return out
+
+
 def static_features(material, dirichlet, dim: int) -> np.ndarray:
-    """[n_nodes][6]: nu, yield strain x 1e3 (Y/E for von Mises, c0/E for Drucker-Prager), hardening
-    ratio x 10 (H/E or Hc/E), 1 for Drucker-Prager, fraction of prescribed components, 1 in 3D."""
+    """[n_nodes][5]: nu, yield strain x 1e3 (Y/E for von Mises, c0/E for Drucker-Prager), hardening
+    ratio x 10 (H/E or Hc/E), 1 for Drucker-Prager, fraction of prescribed components."""
     mask = np.asarray(dirichlet).reshape(-1, dim)
     n = mask.shape[0]
     m = material
     is_dp = int(m.model) == 3
     ys = (m.c0 if is_dp else m.Y) / m.E * 1e3 if int(m.model) != 0 else 0.0
     hr = ((m.Hc if is_dp else m.H) / m.E * 10.0) if int(m.model) != 0 else 0.0
-    out = np.zeros((n, 6))
+    out = np.zeros((n, 5))
     out[:, 0] = m.nu
     out[:, 1] = ys
     out[:, 2] = hr
     out[:, 3] = 1.0 if is_dp else 0.0
     out[:, 4] = (mask != 0).sum(axis=1) / dim
-    out[:, 5] = 1.0 if dim == 3 else 0.0
     return out
 
 
@@ -182,12 +236,13 @@ def increment_scale(u1, u2) -> float:
     return float(np.sqrt((d * d).mean())) if d.size else 0.0
 
 
-def features(u1, u2, u3, zetas, pf1, pf2, stat, dim: int):
+def features(u1, u2, u3, zetas, pf1, pf2, prox1, stat, dim: int):
     """Inputs for step k [n_nodes][16] and the scale s.
 
     u1, u2, u3 = u_{k-1}, u_{k-2}, u_{k-3}; zetas = (zeta_k, zeta_{k-1}, zeta_{k-2}, zeta_{k-3});
-    pf1, pf2 = plastic fractions after steps k-1 and k-2.  Columns: the last two increments / s
-    (3 each, zero-padded in 2D), r_k, r_{k-1}, pf1, pf1 - pf2, the six static features."""
+    pf1, pf2 = plastic fractions after steps k-1 and k-2; prox1 = node_max of the yield proximity
+    after step k-1.  Columns: the last two increments / s (3 each, zero-padded in 2D), r_k, r_{k-1},
+    pf1, pf1 - pf2, prox1, the five static features."""
     z0, z1, z2, z3 = zetas
     s = increment_scale(u1, u2)
     inv_s = 1.0 / s if s > 0 else 0.0
@@ -201,7 +256,8 @@ def features(u1, u2, u3, zetas, pf1, pf2, stat, dim: int):
     X[:, 7] = (z1 - z2) / (z2 - z3) if z2 != z3 else 0.0
     X[:, 8] = pf1
     X[:, 9] = np.asarray(pf1) - np.asarray(pf2)
-    X[:, 10:16] = stat
+    X[:, 10] = prox1
+    X[:, 11:16] = stat
     return X, s
 
 
@@ -226,6 +282,32 @@ def targets(u_k, u_ex, s: float, pf_k, free, dim: int):
     return T
 
 
+def project_correction(X, y, free, dim: int):
+    """P(y): per displacement component c, the least-squares fit of y[:, c] over the free DOFs by
+    a x1 + b x2 with x1 = X[:, c], x2 = X[:, 3 + c] (the scaled last two increments), from the 2x2
+    normal equations; when they are singular (det <= 1e-12 S11 S22) the fit uses x1 alone, and
+    nothing when x1 vanishes on the free DOFs.  Prescribed DOFs get 0.  Returns [n][dim]."""
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    fr = np.asarray(free).reshape(-1, dim).astype(np.float64)
+    out = np.zeros((X.shape[0], dim))
+    for c in range(dim):
+        x1 = X[:, c] * fr[:, c]
+        x2 = X[:, 3 + c] * fr[:, c]
+        yc = y[:, c] * fr[:, c]
+        s11, s12, s22 = x1 @ x1, x1 @ x2, x2 @ x2
+        b1, b2 = x1 @ yc, x2 @ yc
+        det = s11 * s22 - s12 * s12
+        if det > 1e-12 * s11 * s22 and det > 0:
+            a, b = (s22 * b1 - s12 * b2) / det, (s11 * b2 - s12 * b1) / det
+        elif s11 > 0:
+            a, b = b1 / s11, 0.0
+        else:
+            a, b = 0.0, 0.0
+        out[:, c] = a * x1 + b * x2
+    return out
+
+
 def learned_start(u_ex, y, s: float, free, dim: int):
     """u_L = u_ex + s y[:dim] on free DOFs."""
     u = np.asarray(u_ex, dtype=np.float64).copy()
@@ -246,11 +328,13 @@ def trajectory_samples(problem, zetas, solver_factory, free=None):
     us = [sol.u.copy()]
     zs = [0.0]
     pfs = [np.zeros(n_nodes)]
+    prox = [np.zeros(n_nodes)]
     Xs, Ts = [], []
     for z in zetas:
         z = float(z)
         if len(us) >= 4 and zs[-1] != zs[-2] and (z - zs[-1]) / (zs[-1] - zs[-2]) > 0:
-            X, s = features(us[-1], us[-2], us[-3], (z, zs[-1], zs[-2], zs[-3]), pfs[-1], pfs[-2], stat, dim)
+            X, s = features(us[-1], us[-2], us[-3], (z, zs[-1], zs[-2], zs[-3]), pfs[-1], pfs[-2], prox[-1],
+                            stat, dim)
         else:
             X = None
         sol.solve_step(z, tol=1e-13)
@@ -262,6 +346,8 @@ def trajectory_samples(problem, zetas, solver_factory, free=None):
         us.append(sol.u.copy())
         zs.append(z)
         pfs.append(pf)
+        prox.append(node_max(problem.mesh.elem, yield_proximity(problem.material, dim, sol.stress, sol.hard), n_q,
+                             n_nodes))
     if not Xs:
         return np.zeros((0, N_IN)), np.zeros((0, N_OUT))
     return np.concatenate(Xs), np.concatenate(Ts)

@@ -140,8 +140,10 @@ def test_features_and_targets_on_an_elastic_path(make, dim):
         assert np.all(Xs[:, dim:3] == 0.0) if dim == 2 else True
         assert np.abs(Ts[:, :3]).max() < 1e-8
         assert np.all(Ts[:, 3] == 0.0) and np.all(Xs[:, 8:10] == 0.0)
+        # loaded but elastic: every node sees stress below the yield limit
+        assert np.all(Xs[:, 10] > 0.0) and np.all(Xs[:, 10] < 1.0)
         stat = W.static_features(prob.material, prob.dirichlet, dim)
-        assert np.array_equal(Xs[:, 10:], stat)
+        assert np.array_equal(Xs[:, 11:], stat)
 
 
 def test_static_features_values():
@@ -149,7 +151,7 @@ def test_static_features_values():
     st = W.static_features(prob.material, prob.dirichlet, 2)
     m = prob.material
     assert np.allclose(st[:, 0], m.nu) and np.allclose(st[:, 1], m.Y / m.E * 1e3)
-    assert np.allclose(st[:, 2], m.H / m.E * 10) and np.all(st[:, 3] == 0) and np.all(st[:, 5] == 0)
+    assert np.allclose(st[:, 2], m.H / m.E * 10) and np.all(st[:, 3] == 0) and st.shape[1] == 5
     # node 0 at the origin has both components prescribed, the top-right corner none
     assert st[0, 4] == 1.0 and st[-1, 4] == 0.0
 
@@ -179,3 +181,77 @@ def test_adam_training_reduces_the_loss():
         p, m, v = W.adam_step(p, m, v, g, t, 1e-3)
     assert W.mlp_loss(p.astype(np.float32), X, T) < 0.9 * l0
     assert math.isfinite(l0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_yield_proximity_is_one_on_the_yield_surface(model, dim):
+    """After a return mapping, plastic points lie on the (current) yield surface, so their
+    proximity is 1; elastic points lie inside it (Sections 2.2, 2.3 and the hardening extensions)."""
+    import math as m_
+    from oracle import constitutive as OC
+    from synthetic import Material
+    mats = {0: Material(0, E=206900.0, nu=0.29),
+            1: Material(1, E=206900.0, nu=0.29, Y=450.0 * m_.sqrt(2 / 3), H=1e4),
+            2: Material(2, E=206900.0, nu=0.29, Y=450.0 * m_.sqrt(2 / 3), H=1e4),
+            3: Material(3, E=206900.0, nu=0.29, c0=450.0, phi=m_.radians(30.0), psi=m_.radians(10.0), Hc=1e3)}
+    mat = mats[model]
+    n = 4000
+    rng = np.random.default_rng(40 + model + 10 * dim)
+    ns = 3 if dim == 2 else 6
+    nc = 4 if dim == 2 else 6
+    E = rng.standard_normal((ns, n)) * 4e-3
+    ep = rng.standard_normal((nc, n)) * 5e-4
+    if model == 1:
+        beta6 = OC.DEV @ OC.embed_state(rng.standard_normal((nc, n)) * 40.0, dim)
+        hard = OC.extract_state(beta6, dim)
+    else:
+        hard = np.abs(rng.standard_normal(n)) * 1e-3
+    res = OC.constitutive(mat, dim, E, ep, hard)
+    q = W.yield_proximity(mat, dim, res["S"], res["hard"])
+    pl = res["plastic"] != 0
+    if model == 0:
+        assert np.all(q == 0.0)
+        return
+    assert pl.any() and (~pl).any()
+    assert np.abs(q[pl] - 1.0).max() < 1e-10
+    assert np.all(q[~pl] <= 1.0 + 1e-12)
+    # a stress scaled up by 10 % from an elastic point inside the von Mises cylinder moves outward
+    if model == 2:
+        q2 = W.yield_proximity(mat, dim, 1.1 * res["S"], res["hard"])
+        assert np.all(q2[~pl] > q[~pl] - 1e-15)
+
+
+def test_node_max_brute_force():
+    prob = p1_plane_vm(n=3, n_steps=2)
+    elem = prob.mesh.elem
+    vals = np.random.default_rng(41).uniform(0, 2, elem.shape[0])
+    out = W.node_max(elem, vals, 1, prob.mesh.n_nodes)
+    for node in range(prob.mesh.n_nodes):
+        assert out[node] == max(vals[e] for e in range(elem.shape[0]) if node in list(elem[e]))
+
+
+def test_projection_keeps_fields_in_the_span_and_removes_an_orthogonal_part():
+    rng = np.random.default_rng(42)
+    n, dim = 50, 3
+    X = rng.standard_normal((n, 16))
+    free = np.ones(n * dim, dtype=bool)
+    free[:6] = False
+    fr = free.reshape(n, dim)
+    a, b = rng.standard_normal(dim), rng.standard_normal(dim)
+    y_in = np.stack([a[c] * X[:, c] + b[c] * X[:, 3 + c] for c in range(dim)], 1)
+    P = W.project_correction(X, y_in, free, dim)
+    assert np.allclose(P[fr], y_in[fr], rtol=0, atol=1e-12) and np.all(P[~fr] == 0.0)
+    y = rng.standard_normal((n, 4))
+    P = W.project_correction(X, y, free, dim)
+    for c in range(dim):
+        r = (y[:, c] - P[:, c]) * fr[:, c]
+        assert abs(r @ (X[:, c] * fr[:, c])) < 1e-10 and abs(r @ (X[:, 3 + c] * fr[:, c])) < 1e-10
+    # a vanishing older increment: the fit falls back to the last increment alone
+    X0 = X.copy()
+    X0[:, 3:6] = 0.0
+    P0 = W.project_correction(X0, y, free, dim)
+    for c in range(dim):
+        x1 = X0[:, c] * fr[:, c]
+        assert np.allclose(P0[:, c], (x1 @ (y[:, c] * fr[:, c])) / (x1 @ x1) * x1)
+    assert np.all(W.project_correction(np.zeros((n, 16)), y, free, dim) == 0.0)
