@@ -120,7 +120,9 @@ typedef struct {
     int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks), 2 smoothed-aggregation AMG
                                     (built from K_elast on first use; Chebyshev/block-Jacobi smoothing) */
     int32_t split_elastic_cache; /* 1: K = K_elast + sum over plastic points (eq. (K-split)); 0: K = B^T D B */
-    int32_t warm_start;          /* 0: last converged u; 1: linear extrapolation of the last two steps */
+    int32_t warm_start;          /* 0: last converged u; 1: linear extrapolation of the last two steps;
+                                    2: the extrapolation corrected by the attached warm-start network
+                                    (ep_ws_attach), judged per problem against the plain extrapolation */
     int32_t profile;             /* 1: time the assembly and SpMV kernels with CUDA events (fills t_*_kernel_ms) */
 } ep_opts;
 
@@ -138,6 +140,9 @@ typedef struct {
     double t_spmv_kernel_ms;     /* summed duration of those SpMV launches (profile = 1) */
     int64_t n_plastic_assembled; /* plastic points summed over the step's assemblies (local-tangent work done) */
     int32_t newton_its_fp32;     /* EP_MIXED: Newton iterations of the step that used the FP32 tangent and solve */
+    int32_t start;               /* Newton start used: 0 last converged u, 1 extrapolated, 2 learned (for at
+                                    least one problem of a batch) */
+    int32_t n_learned;           /* warm_start = 2: problems that kept the learned start */
     int32_t reserved;
 } ep_step_report;
 
@@ -156,8 +161,13 @@ typedef enum {
     EP_WEIGHT = 10,          /* double [n_int], |det J| w_q (Section 6.3, WEIGHT) (read only) */
     EP_DPHI = 11,            /* double [n_int][n_p][dim], physical basis gradients (Section 6.1, DPhi) (read only) */
     EP_SOLUTION = 12,        /* double [n_nodes*dim], x of the last ep_linear_solve (read only) */
-    EP_K_VALUES_F32 = 13     /* float [nnz_blocks][dim][dim], K of the last EP_MIXED assembly (read only;
+    EP_K_VALUES_F32 = 13,    /* float [nnz_blocks][dim][dim], K of the last EP_MIXED assembly (read only;
                                 EP_ERR_STATE before the first one) */
+    EP_WS_X = 14,            /* float [n_rows][16], recorded warm-start inputs (read only; EP_ERR_STATE when
+                                not recording; n_rows from ep_ws_samples) */
+    EP_WS_T = 15,            /* float [n_rows][4], recorded warm-start targets (read only, as EP_WS_X) */
+    EP_WS_START = 16         /* double [n_nodes*dim], the learned start u_ex + s P(y) of the last step that
+                                computed one, before the per-problem choice (read only; EP_ERR_STATE before) */
 } ep_field;
 
 /* Sizes of a context: n_int, n_comp, nnz_blocks, n_p, n_q. */
@@ -307,6 +317,69 @@ ep_status ep_linear_solve_noalloc(int32_t dim, int64_t n_nodes, const int32_t* r
                                   const int32_t* diag_slot, const double* vals, const uint8_t* free_dof,
                                   const double* b, double* x, int32_t method, int32_t precond, double rtol,
                                   int32_t maxit, int32_t* iterations, double* rel_resid, void* cuda_stream);
+
+/*
+ * Learned warm start (a per-node network that corrects the extrapolated
+ * Newton start).  The paper starts Newton at step k from the prescribed
+ * values u_{D,k} (ALG-NEWTON, Section 4); warm_start = 1 extrapolates the
+ * last two converged steps, u_ex = u_{k-1} + r_k (u_{k-1} - u_{k-2}) with
+ * r_k = (zeta_k - zeta_{k-1}) / (zeta_{k-1} - zeta_{k-2}).  warm_start = 2
+ * adds s * P(y) on free DOFs, where s is the problem's RMS of
+ * u_{k-1} - u_{k-2}, y [node][0..dim) the output of a network
+ *     16 -> 128 (ReLU) -> 128 (ReLU) -> 4,
+ * (weights rounded to bfloat16; biases, activations and sums in FP32), and P
+ * the least-squares projection of y, per problem and displacement component,
+ * onto the span of the scaled last two increments over the free DOFs (FP64
+ * normal equations; the last increment alone when they are singular).  The 16
+ * inputs of a node: u_{k-1} - u_{k-2} and u_{k-2} - u_{k-3} divided by s (3
+ * each, zero-padded in 2D), r_k, r_{k-1}, the fraction of plastic points of
+ * the adjacent elements after step k-1 and its change since step k-2, the
+ * largest yield proximity of those points after step k-1 (von Mises
+ * |dev s - beta| / (Y + H alpha), Drucker-Prager (|dev s|/sqrt(2) + eta p) /
+ * (c + Hc alpha), clamped at 0), then nu, yield strain x 1e3 (Y/E; c0/E for
+ * Drucker-Prager), hardening ratio x 10 (H/E; Hc/E), 1 for Drucker-Prager, the
+ * fraction of the node's prescribed components.  Output 3 is a logit of the
+ * node's plastic fraction after step k (trained, reported, not used by the
+ * start).  The learned start
+ * needs three converged steps since ep_ws_attach / ep_ws_record and a load
+ * that keeps its direction; each problem of a batch keeps the plain
+ * extrapolation when that has the smaller residual, and a step that fails to
+ * converge from either is retried from the last converged u.
+ *
+ * Parameters: one float32 vector of EP_WS_N_PARAMS entries, W1 [128][16],
+ * b1 [128], W2 [128][128], b2 [128], W3 [4][128], b3 [4] (y = W x + b).
+ * Training loss over n rows (targets t [n][4]):
+ *     (1/n) sum [ sum_{c<3} (y_c - t_c)^2 + 0.1 * (max(y_3,0) - y_3 t_3 + log(1 + exp(-|y_3|))) ];
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on FP32 master
+ * parameters, the bfloat16 copy refreshed after every step.
+ */
+#define EP_WS_N_IN 16
+#define EP_WS_WIDTH 128
+#define EP_WS_N_OUT 4
+#define EP_WS_N_PARAMS 19204
+/* A network on `device`, parameters copied from host `params`; kernels run on cuda_stream. */
+ep_status ep_mlp_create(void** out, const float* params, int32_t device, void* cuda_stream);
+ep_status ep_mlp_destroy(void* mlp);
+/* Current FP32 master parameters into host dst [EP_WS_N_PARAMS]. */
+ep_status ep_mlp_get_params(void* mlp, float* dst);
+/* Y [n][4] = network(X [n][16]); device pointers; returns when the outputs are written. */
+ep_status ep_mlp_forward(void* mlp, const float* X, int64_t n_rows, float* Y);
+/* Loss and its gradient (host loss, host grad [EP_WS_N_PARAMS]) over n rows of device X, T; no update. */
+ep_status ep_mlp_grad(void* mlp, const float* X, const float* T, int64_t n_rows, double* loss, float* grad);
+/* One Adam step with learning rate lr on the n rows of device X [n][16], T [n][4]; *loss (host, may
+ * be NULL) receives the loss before the step. */
+ep_status ep_mlp_train_step(void* mlp, const float* X, const float* T, int64_t n_rows, float lr, double* loss);
+/* Record training rows during ep_solve_load_path: after every converged step with features (three
+ * earlier converged steps, a load keeping its direction), n_nodes rows of inputs and targets
+ * (t_c = (u_k - u_ex)_c / s on free DOFs, 0 on prescribed ones; t_3 the node's plastic fraction after
+ * step k) are appended while max_rows allows.  max_rows = 0 frees the buffers.  Starts the history
+ * the features need (as does ep_ws_attach). */
+ep_status ep_ws_record(void* ctx, int64_t max_rows);
+/* The recorded rows: device pointers X [n][16], T [n][4] owned by the context, valid until the next
+ * ep_ws_record or ep_destroy. */
+ep_status ep_ws_samples(void* ctx, const float** X, const float** T, int64_t* n_rows);
+/* Use `mlp` (not owned; NULL detaches) for warm_start = 2. */
+ep_status ep_ws_attach(void* ctx, void* mlp);
 
 /* Human-readable name of a status code. */
 const char* ep_status_str(int32_t status);

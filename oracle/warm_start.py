@@ -351,3 +351,32 @@ def trajectory_samples(problem, zetas, solver_factory, free=None):
     if not Xs:
         return np.zeros((0, N_IN)), np.zeros((0, N_OUT))
     return np.concatenate(Xs), np.concatenate(Ts)
+
+
+def last_learned_start(problem, zetas, params, solver_factory):
+    """The learned start of the last step of a load path, from the oracle's own trajectory (extrapolated
+    starts; the converged steps do not depend on the start): (u_L, s, P(y)) with P(y) [n][dim], or None
+    when that step has no inputs (fewer than three earlier steps, or a reversed load)."""
+    sol = solver_factory(problem)
+    dim = problem.mesh.dim
+    n_nodes = problem.mesh.n_nodes
+    n_q = sol.geom.n_q
+    free = problem.dirichlet == 0
+    stat = static_features(problem.material, problem.dirichlet, dim)
+    us, zs, pfs, prox = [sol.u.copy()], [0.0], [np.zeros(n_nodes)], [np.zeros(n_nodes)]
+    for z in zetas[:-1]:
+        sol.solve_step(float(z), tol=1e-13)
+        us.append(sol.u.copy())
+        zs.append(float(z))
+        pfs.append(node_plastic_fraction(problem.mesh.elem, sol.plastic, n_q, n_nodes))
+        prox.append(node_max(problem.mesh.elem, yield_proximity(problem.material, dim, sol.stress, sol.hard), n_q,
+                             n_nodes))
+    z = float(zetas[-1])
+    if len(us) < 4 or zs[-1] == zs[-2] or (z - zs[-1]) / (zs[-1] - zs[-2]) <= 0:
+        return None
+    X, s = features(us[-1], us[-2], us[-3], (z, zs[-1], zs[-2], zs[-3]), pfs[-1], pfs[-2], prox[-1], stat, dim)
+    X = X.astype(np.float32)       # the network reads FP32 inputs
+    y, _ = mlp_forward(params, X)
+    P = project_correction(X, y, free, dim)
+    u_ex = extrapolated_start(us[-1], us[-2], (z, zs[-1], zs[-2]), free, problem.u_D_unit)
+    return learned_start(u_ex, P, s, free, dim), s, P

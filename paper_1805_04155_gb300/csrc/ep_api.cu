@@ -149,6 +149,29 @@ constexpr double MIXED_STALL_RATIO = 0.5;
 // iterate (re-assembled), with the FP64 tangent.
 constexpr double MIXED_RHO_FACTOR = 10.0;
 
+// Learned warm start: the history the node features need, and recorded training rows.
+struct WsState {
+    void* mlp = nullptr;            // attached network (warm_start = 2), not owned
+    bool ready = false;             // buffers allocated, history tracked at every commit
+    int hist = 0;                   // converged steps since the history started
+    double* u3 = nullptr;           // u_{k-3}
+    double zeta3 = 0.0;             // zeta_{k-3}
+    int32_t *cnt_ip = nullptr, *cnt_pl = nullptr, *node_prob = nullptr;
+    int64_t* prob_dof = nullptr;    // device [n_prob + 1]
+    float *pf1 = nullptr, *pf2 = nullptr, *pfk = nullptr;   // plastic fractions after k-1, k-2, k
+    float* prox1 = nullptr;         // yield proximity after step k-1
+    float* stat = nullptr;          // [n_nodes][5] static inputs
+    double* uL = nullptr;           // the learned start of the last step that computed one
+    bool uL_valid = false;
+    double* scale = nullptr;        // [2][n_prob]: s_p, 1/s_p
+    float *X = nullptr, *Y = nullptr;   // inputs / outputs of one step when not recording
+    double* u_ex = nullptr;         // the plain extrapolated start
+    uint8_t* take_ex = nullptr;     // device [n_prob]: the problem keeps the plain extrapolation
+    std::vector<uint8_t> h_take;
+    float *rec_X = nullptr, *rec_T = nullptr;   // recorded rows [rec_cap][16], [rec_cap][4]
+    int64_t rec_cap = 0, rec_n = 0;
+};
+
 struct Ctx {
     std::string err;
     int device = 0;
@@ -207,6 +230,9 @@ struct Ctx {
     int64_t amg_np = -1;         // plastic points of the tangent the coarse operators were last built from
     bool mixed_fallback = false; // the mixed path has switched to FP64 for the rest of the load path
     double amg_setup_ms = 0.0;
+    WsState ws;
+    std::vector<float> h_node_static;   // [n_nodes][5] static warm-start inputs (host, built at creation)
+    std::vector<int32_t> h_node_prob;   // [n_nodes] problem of each node (batches only)
     std::vector<void*> allocs;
 };
 
@@ -408,6 +434,8 @@ ep_status ep_destroy(void* ctx) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (void* p : c->allocs) cudaFree(p);
+    if (c->ws.rec_X) cudaFree(c->ws.rec_X);
+    if (c->ws.rec_T) cudaFree(c->ws.rec_T);
     krylov_free(c->kw);
     if (c->norms_host) cudaFreeHost(c->norms_host);
     if (c->counter_host) cudaFreeHost(c->counter_host);
@@ -477,6 +505,35 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
                 return fail(EP_ERR_INVALID_ARG);
             }
     c->hard_len = (c->mat.model == 1) ? c->n_int * c->n_comp : c->n_int;
+    {
+        // static inputs of the warm-start network per node: the material of (any) element holding
+        // it, and its prescribed components
+        std::vector<int32_t> node_mat(c->n_nodes, 0);
+        if (elem_mat)
+            for (int64_t e = 0; e < c->n_elem; ++e)
+                for (int a = 0; a < elem_np(c->eid); ++a) {
+                    const int32_t v = mesh->elem_nodes[e * elem_np(c->eid) + a];
+                    if (v >= 0 && v < c->n_nodes) node_mat[v] = elem_mat[e];
+                }
+        c->h_node_static.assign((size_t)c->n_nodes * 5, 0.f);
+        for (int64_t n = 0; n < c->n_nodes; ++n) {
+            const ep_material& m = mats[node_mat[n]];
+            const bool dp = m.model == EP_DP, el = m.model == EP_ELASTIC;
+            int fixed = 0;
+            for (int k = 0; k < c->dim; ++k) fixed += bc->dirichlet_mask[n * c->dim + k] ? 1 : 0;
+            float* f = &c->h_node_static[(size_t)n * 5];
+            f[0] = (float)m.nu;
+            f[1] = el ? 0.f : (float)((dp ? m.c0 : m.Y) / m.E * 1e3);
+            f[2] = el ? 0.f : (float)((dp ? m.Hc : m.H) / m.E * 10.0);
+            f[3] = dp ? 1.f : 0.f;
+            f[4] = (float)((double)fixed / c->dim);
+        }
+        if (prob_node && n_prob > 1) {
+            c->h_node_prob.assign(c->n_nodes, 0);
+            for (int p = 0; p < n_prob; ++p)
+                for (int64_t n = prob_node[p]; n < prob_node[p + 1] && n < c->n_nodes; ++n) c->h_node_prob[n] = p;
+        }
+    }
     // problems and their residual-norm chunks (64 Ki DOFs each)
     c->n_prob = std::max(1, n_prob);
     c->prob_dof.assign(c->n_prob + 1, 0);
@@ -759,6 +816,15 @@ static ep_status field_ptr(Ctx* c, int32_t field, void** p, size_t* bytes, bool 
         case EP_K_VALUES_F32:
             if (!c->K32) return EP_ERR_STATE;
             *p = c->K32; *bytes = sizeof(float) * c->nnzb * d2; return EP_OK;
+        case EP_WS_X:
+            if (!c->ws.rec_X) return EP_ERR_STATE;
+            *p = c->ws.rec_X; *bytes = sizeof(float) * c->ws.rec_n * EP_WS_N_IN; return EP_OK;
+        case EP_WS_T:
+            if (!c->ws.rec_T) return EP_ERR_STATE;
+            *p = c->ws.rec_T; *bytes = sizeof(float) * c->ws.rec_n * EP_WS_N_OUT; return EP_OK;
+        case EP_WS_START:
+            if (!c->ws.uL_valid) return EP_ERR_STATE;
+            *p = c->ws.uL; *bytes = sizeof(double) * c->n_dof; return EP_OK;
     }
     return EP_ERR_INVALID_ARG;
 }
@@ -770,7 +836,7 @@ ep_status ep_get(void* ctx, int32_t field, void* dst, size_t bytes, int32_t dst_
     size_t want = 0;
     const ep_status fs = field_ptr(c, field, &src, &want, false);
     if (fs != EP_OK) {
-        c->err = fs == EP_ERR_STATE ? "ep_get: the field does not exist yet (no mixed-precision assembly)"
+        c->err = fs == EP_ERR_STATE ? "ep_get: the field does not exist yet (no mixed-precision assembly, or no recording)"
                                     : "ep_get: unknown field";
         return fs;
     }
@@ -802,6 +868,7 @@ ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_
     CK(cudaStreamSynchronize(c->stream));
     if (field == EP_U) {
         c->n_committed = 0;      // no extrapolation history across a reset
+        c->ws.hist = 0;
         c->mixed_fallback = false;
     }
     return EP_OK;
@@ -900,6 +967,114 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
     return (ep_status)status;
 }
 
+// Buffers and history of the learned warm start (first ep_ws_record / ep_ws_attach).  The history
+// starts here: the plastic fractions of the current state, no converged step yet.
+static ep_status ws_setup(Ctx* c) {
+    WsState& w = c->ws;
+    cudaStream_t s = c->stream;
+    if (!w.ready) {
+        CK(dalloc(c, &w.u3, c->n_dof));
+        CK(dalloc(c, &w.cnt_ip, c->n_nodes));
+        CK(dalloc(c, &w.cnt_pl, c->n_nodes));
+        if (!c->h_node_prob.empty()) CK(dalloc(c, &w.node_prob, c->n_nodes));
+        CK(dalloc(c, &w.prob_dof, c->n_prob + 1));
+        CK(dalloc(c, &w.pf1, c->n_nodes));
+        CK(dalloc(c, &w.pf2, c->n_nodes));
+        CK(dalloc(c, &w.pfk, c->n_nodes));
+        CK(dalloc(c, &w.stat, c->n_nodes * 5));
+        CK(dalloc(c, &w.prox1, c->n_nodes));
+        CK(dalloc(c, &w.uL, c->n_dof));
+        CK(dalloc(c, &w.scale, 2 * c->n_prob));
+        CK(dalloc(c, &w.X, c->n_nodes * EP_WS_N_IN));
+        CK(dalloc(c, &w.Y, c->n_nodes * EP_WS_N_OUT));
+        CK(dalloc(c, &w.u_ex, c->n_dof));
+        CK(dalloc(c, &w.take_ex, c->n_prob));
+        w.h_take.assign(c->n_prob, 0);
+        if (w.node_prob)
+            CK(cudaMemcpyAsync(w.node_prob, c->h_node_prob.data(), sizeof(int32_t) * c->n_nodes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.prob_dof, c->prob_dof.data(), sizeof(int64_t) * (c->n_prob + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.stat, c->h_node_static.data(), sizeof(float) * c->n_nodes * 5, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(w.cnt_ip, 0, sizeof(int32_t) * c->n_nodes, s));
+        CK(ws_node_counts(c->elem, c->n_elem, c->n_p, c->n_q, nullptr, w.cnt_ip, s));
+        c->launches += 1;
+        w.ready = true;
+    }
+    CK(cudaMemsetAsync(w.cnt_pl, 0, sizeof(int32_t) * c->n_nodes, s));
+    CK(ws_node_counts(c->elem, c->n_elem, c->n_p, c->n_q, c->flag, w.cnt_pl, s));
+    CK(ws_fraction(w.cnt_pl, w.cnt_ip, c->n_nodes, w.pf1, s));
+    CK(cudaMemcpyAsync(w.pf2, w.pf1, sizeof(float) * c->n_nodes, cudaMemcpyDeviceToDevice, s));
+    CK(ws_proximity(mesh_dev(c), c->sig, c->hard, c->n_p, c->n_q, c->dim, w.prox1, s));
+    CK(cudaStreamSynchronize(s));
+    w.hist = 0;
+    return EP_OK;
+}
+
+// Residual norm ||(zeta f - F(u))_free|| of every problem at a candidate start (an F-only assembly
+// with the committed state).  A return-mapping failure or a non-finite norm reads as +inf.
+static ep_status start_residuals(Ctx* c, const double* u, double z, std::vector<double>& rn) {
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+    ep_status st = assemble(c, u, true, false, false);
+    if (st != EP_OK) return st;
+    CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, nullptr, c->n_dof, c->kw.part, c->kw.nparts, c->norms, s));
+    c->launches += 1;
+    rn.assign(c->n_prob, 0.0);
+    const int64_t nchunk = (int64_t)c->chunk_prob.size();
+    if (c->n_prob > 1) {
+        CK(vec_chunk_norms(c->f_unit, z, c->F, c->free_dof, c->r, c->d_chunks, nchunk, c->d_chunk_norms, s));
+        CK(cudaMemcpyAsync(c->h_chunk_norms.data(), c->d_chunk_norms, sizeof(double) * 3 * nchunk,
+                           cudaMemcpyDeviceToHost, s));
+        c->launches += 1;
+    }
+    CK(cudaMemcpyAsync(c->norms_host, c->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->n_prob > 1)
+        for (int64_t i = 0; i < nchunk; ++i) rn[c->chunk_prob[i]] += c->h_chunk_norms[i];
+    else
+        rn[0] = c->norms_host[0];
+    for (double& v : rn) {
+        v = std::sqrt(v);
+        if (*c->err_host || !std::isfinite(v)) v = HUGE_VAL;
+    }
+    CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+    return EP_OK;
+}
+
+ep_status ep_ws_record(void* ctx, int64_t max_rows) {
+    if (!ctx || max_rows < 0) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->ws.rec_X) cudaFree(c->ws.rec_X);
+    if (c->ws.rec_T) cudaFree(c->ws.rec_T);
+    c->ws.rec_X = c->ws.rec_T = nullptr;
+    c->ws.rec_cap = c->ws.rec_n = 0;
+    if (max_rows == 0) return EP_OK;
+    CK(cudaMalloc((void**)&c->ws.rec_X, sizeof(float) * max_rows * EP_WS_N_IN));
+    CK(cudaMalloc((void**)&c->ws.rec_T, sizeof(float) * max_rows * EP_WS_N_OUT));
+    c->ws.rec_cap = max_rows;
+    return ws_setup(c);
+}
+
+ep_status ep_ws_samples(void* ctx, const float** X, const float** T, int64_t* n_rows) {
+    if (!ctx || !X || !T || !n_rows) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    *X = c->ws.rec_X;
+    *T = c->ws.rec_T;
+    *n_rows = c->ws.rec_n;
+    return EP_OK;
+}
+
+ep_status ep_ws_attach(void* ctx, void* mlp) {
+    if (!ctx) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    cudaSetDevice(c->device);
+    c->ws.mlp = mlp;
+    if (!mlp || c->ws.ready) return EP_OK;
+    return ws_setup(c);
+}
+
 ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, const ep_opts* opts,
                              ep_step_report* reports) {
     if (!ctx || n_steps < 0 || (n_steps > 0 && !zeta)) return EP_ERR_INVALID_ARG;
@@ -909,6 +1084,14 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     else ep_default_opts(&o);
     if (o.precision != EP_FP64 && o.precision != EP_MIXED) {
         c->err = "precision must be EP_FP64 or EP_MIXED";
+        return EP_ERR_INVALID_ARG;
+    }
+    if (o.warm_start < 0 || o.warm_start > 2) {
+        c->err = "warm_start must be 0, 1 or 2";
+        return EP_ERR_INVALID_ARG;
+    }
+    if (o.warm_start == 2 && !c->ws.mlp) {
+        c->err = "warm_start = 2 needs a network (ep_ws_attach)";
         return EP_ERR_INVALID_ARG;
     }
     const bool mixed = o.precision == EP_MIXED;
@@ -945,14 +1128,38 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         double rel = 0.0;
         int it = 0;
         bool converged = false;
-        // Start iterate: the last converged u with the new Dirichlet values, plus (warm_start = 1)
-        // the linear extrapolation of the last two steps while the load keeps its direction.  A
-        // step that does not converge from the extrapolated start (a predictor past a change of
-        // the plastic regime) is retried once from the unextrapolated one.
+        // Inputs of the warm-start network for this step (learned start, or recording): three
+        // converged steps since the history started and a load that keeps its direction.
+        WsState& ws = c->ws;
+        const bool ws_learn = o.warm_start == 2 && ws.mlp;
+        const bool ws_rec = ws.rec_cap - ws.rec_n >= c->n_nodes;
+        bool ws_feat = false;
+        double ws_ratio = 0.0;
+        float* ws_X = ws.X;
+        if (ws.ready && (ws_learn || ws_rec) && ws.hist >= 3 && c->zeta_last != c->zeta_prev) {
+            ws_ratio = (z - c->zeta_last) / (c->zeta_last - c->zeta_prev);
+            if (ws_ratio > 0.0) {
+                const double r_k1 =
+                    c->zeta_prev != ws.zeta3 ? (c->zeta_last - c->zeta_prev) / (c->zeta_prev - ws.zeta3) : 0.0;
+                if (ws_rec) ws_X = ws.rec_X + ws.rec_n * EP_WS_N_IN;
+                CK(ws_scale(c->u, c->u_prev, ws.prob_dof, c->n_prob, ws.scale, s));
+                CK(ws_features(c->u, c->u_prev, ws.u3, ws.node_prob, ws.scale, c->n_prob, c->dim, c->n_nodes, ws_ratio,
+                               r_k1, ws.pf1, ws.pf2, ws.prox1, ws.stat, ws_X, s));
+                c->launches += 2;
+                ws_feat = true;
+            }
+        }
+        // Start iterate: the last converged u with the new Dirichlet values, plus (warm_start >= 1)
+        // the linear extrapolation of the last two steps while the load keeps its direction, plus
+        // (warm_start = 2) the network's correction where it lowers the residual.  A step that
+        // does not converge from the extrapolated start (a predictor past a change of the plastic
+        // regime) is retried once from the unextrapolated one.
         for (int attempt = 0; attempt < 2; ++attempt) {
         bool extrapolated = false;
+        rep.start = 0;
+        rep.n_learned = 0;
         CK(cudaMemcpyAsync(c->u_it, c->u, sizeof(double) * c->n_dof, cudaMemcpyDeviceToDevice, s));
-        if (attempt == 0 && o.warm_start == 1 && c->n_committed >= 2 && c->zeta_last != c->zeta_prev) {
+        if (attempt == 0 && o.warm_start >= 1 && c->n_committed >= 2 && c->zeta_last != c->zeta_prev) {
             const double ratio = (z - c->zeta_last) / (c->zeta_last - c->zeta_prev);
             if (ratio > 0.0) {
                 CK(vec_extrapolate(c->u_it, c->u_prev, ratio, c->n_dof, s));
@@ -962,6 +1169,40 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         }
         CK(vec_set_dirichlet(c->u_it, c->uD_unit, z, c->free_dof, c->n_dof, s));
         c->launches += 1;
+        if (extrapolated) rep.start = 1;
+        if (extrapolated && ws_learn && ws_feat) {
+            // learned start: u_ex + s * P(y) on free DOFs, P the projection of the per-node prediction
+            // onto the span of the last two increments (per problem and component); each problem
+            // keeps whichever start has the smaller residual
+            CK(cudaMemcpyAsync(ws.u_ex, c->u_it, sizeof(double) * c->n_dof, cudaMemcpyDeviceToDevice, s));
+            CK(mlp_sync(ws.mlp));
+            CK(mlp_forward_on(ws.mlp, ws_X, c->n_nodes, ws.Y, s));
+            CK(ws_project(ws_X, ws.Y, c->free_dof, ws.prob_dof, c->n_prob, c->dim, s));
+            CK(ws_apply(c->u_it, ws.Y, ws.node_prob, ws.scale, c->n_prob, c->free_dof, c->dim, c->n_dof, s));
+            CK(cudaMemcpyAsync(ws.uL, c->u_it, sizeof(double) * c->n_dof, cudaMemcpyDeviceToDevice, s));
+            ws.uL_valid = true;
+            c->launches += 3;
+            std::vector<double> r_L, r_ex;
+            st = start_residuals(c, c->u_it, z, r_L);
+            if (st != EP_OK) return st;
+            st = start_residuals(c, ws.u_ex, z, r_ex);
+            if (st != EP_OK) return st;
+            rep.n_assemble += 2;
+            bool any_ex = false, any_L = false;
+            for (int p = 0; p < c->n_prob; ++p) {
+                ws.h_take[p] = r_L[p] <= r_ex[p] ? 0 : 1;
+                any_ex = any_ex || ws.h_take[p];
+                any_L = any_L || !ws.h_take[p];
+            }
+            if (any_ex) {
+                CK(cudaMemcpyAsync(ws.take_ex, ws.h_take.data(), c->n_prob, cudaMemcpyHostToDevice, s));
+                CK(ws_select(c->u_it, ws.u_ex, ws.node_prob, ws.take_ex, c->dim, c->n_dof, s));
+                CK(cudaStreamSynchronize(s));   // h_take is read by the copy
+                c->launches += 1;
+            }
+            if (any_L) rep.start = 2;
+            for (int p = 0; p < c->n_prob; ++p) rep.n_learned += ws.h_take[p] ? 0 : 1;
+        }
         CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
         st = EP_OK;
         rel = 0.0;
@@ -1177,7 +1418,35 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             unsigned long long np = 0;
             st = commit(c, c->u_it, &np);
             rep.n_plastic = (int64_t)np;
-            if (st == EP_OK) {
+            if (st == EP_OK && ws.ready) {
+                // warm-start history: plastic fractions after step k, the recorded targets, then
+                // u_{k-3} <- u_{k-2} <- u_{k-1} <- u_k
+                CK(cudaMemsetAsync(ws.cnt_pl, 0, sizeof(int32_t) * c->n_nodes, s));
+                CK(ws_node_counts(c->elem, c->n_elem, c->n_p, c->n_q, c->flag, ws.cnt_pl, s));
+                CK(ws_fraction(ws.cnt_pl, ws.cnt_ip, c->n_nodes, ws.pfk, s));
+                CK(ws_proximity(mesh_dev(c), c->sig, c->hard, c->n_p, c->n_q, c->dim, ws.prox1, s));
+                c->launches += 3;
+                if (ws_feat && ws_rec) {
+                    CK(ws_targets(c->u_it, c->u, c->u_prev, ws_ratio, ws.node_prob, ws.scale, c->n_prob, c->free_dof,
+                                  ws.pfk, c->dim, c->n_nodes, ws.rec_T + ws.rec_n * EP_WS_N_OUT, s));
+                    c->launches += 1;
+                    ws.rec_n += c->n_nodes;
+                }
+                float* pf = ws.pf2;
+                ws.pf2 = ws.pf1;
+                ws.pf1 = ws.pfk;
+                ws.pfk = pf;
+                double* u3 = ws.u3;
+                ws.u3 = c->u_prev;
+                c->u_prev = c->u;
+                c->u = c->u_it;
+                c->u_it = u3;
+                ws.zeta3 = c->zeta_prev;
+                ws.hist++;
+                c->zeta_prev = c->zeta_last;
+                c->zeta_last = z;
+                c->n_committed++;
+            } else if (st == EP_OK) {
                 std::swap(c->u_prev, c->u);     // u_prev <- u_{k-1}
                 std::swap(c->u, c->u_it);       // u <- u_k
                 c->zeta_prev = c->zeta_last;

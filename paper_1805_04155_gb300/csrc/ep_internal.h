@@ -238,4 +238,45 @@ cudaError_t vec_set_dirichlet(double* u, const double* uD_unit, double zeta, con
 cudaError_t vec_extrapolate(double* u, const double* u_prev, double ratio, int64_t n, cudaStream_t s);
 cudaError_t vec_mask_copy(double* dst, const double* src, const uint8_t* free_dof, int64_t n, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Learned warm start (warm_start.cu): node features, targets and the start correction.
+// node_prob: [n_nodes] problem of each node, or null (one problem).
+// ---------------------------------------------------------------------------
+// cnt[node] += points of the adjacent elements (flag null) or their plastic points (flag != 0);
+// the caller zeroes cnt.
+cudaError_t ws_node_counts(const int32_t* elem, int64_t n_elem, int n_p, int n_q, const uint8_t* flag, int32_t* cnt,
+                           cudaStream_t s);
+// pf = cnt_pl / cnt_ip per node (0 where cnt_ip = 0).
+cudaError_t ws_fraction(const int32_t* cnt_pl, const int32_t* cnt_ip, int64_t n_nodes, float* pf, cudaStream_t s);
+// scale [2][n_prob]: s_p = RMS of (u1 - u2) over the DOFs [prob_dof[p], prob_dof[p+1]) and 1/s_p (0 if s_p = 0).
+cudaError_t ws_scale(const double* u1, const double* u2, const int64_t* prob_dof, int n_prob, double* scale,
+                     cudaStream_t s);
+// X [n_nodes][16]: the network inputs of step k (u1, u2, u3 = u_{k-1}, u_{k-2}, u_{k-3}; pf1, pf2 the
+// plastic fractions after k-1, k-2; prox1 the yield proximity after k-1; stat [n_nodes][5]).
+cudaError_t ws_features(const double* u1, const double* u2, const double* u3, const int32_t* node_prob,
+                        const double* scale, int n_prob, int dim, int64_t n_nodes, double r_k, double r_k1,
+                        const float* pf1, const float* pf2, const float* prox1, const float* stat, float* X,
+                        cudaStream_t s);
+// prox [n_nodes]: the largest yield proximity of the committed state over the points of the adjacent
+// elements (sig [n_comp][n_int], hard [n_int] or [n_comp][n_int]).
+cudaError_t ws_proximity(const MeshDev& mesh, const double* sig, const double* hard, int n_p, int n_q, int dim,
+                         float* prox, cudaStream_t s);
+// Y[:, 0..dim) <- its projection, per problem and component, onto the span of X[:, c], X[:, 3 + c].
+cudaError_t ws_project(const float* X, float* Y, const uint8_t* free_dof, const int64_t* prob_dof, int n_prob,
+                       int dim, cudaStream_t s);
+// u += s_p * Y[node][c] on free DOFs.
+cudaError_t ws_apply(double* u, const float* Y, const int32_t* node_prob, const double* scale, int n_prob,
+                     const uint8_t* free_dof, int dim, int64_t n_dof, cudaStream_t s);
+// T [n_nodes][4]: ((u_k - (u1 + ratio (u1 - u2))) / s_p on free DOFs, 0 elsewhere; pf_k).
+cudaError_t ws_targets(const double* uk, const double* u1, const double* u2, double ratio, const int32_t* node_prob,
+                       const double* scale, int n_prob, const uint8_t* free_dof, const float* pf_k, int dim,
+                       int64_t n_nodes, float* T, cudaStream_t s);
+// u = u_alt on the DOFs of every problem p with take_alt[p] != 0.
+cudaError_t ws_select(double* u, const double* u_alt, const int32_t* node_prob, const uint8_t* take_alt, int dim,
+                      int64_t n_dof, cudaStream_t s);
+// The network (opaque ep_mlp_* handle): Y [n][4] = net(X [n][16]) on stream s.
+cudaError_t mlp_forward_on(void* mlp, const float* X, int64_t n, float* Y, cudaStream_t s);
+// Waits for the network's own stream (its parameters may still be being written by a training step).
+cudaError_t mlp_sync(void* mlp);
+
 }  // namespace ep

@@ -27,12 +27,16 @@ EP_ELASTIC, EP_VM_KIN, EP_VM_ISO, EP_DP = range(4)
 EP_FP64, EP_MIXED = range(2)
 # ep_field
 (EP_U, EP_STRESS, EP_PLASTIC_STRAIN, EP_HARDENING, EP_PLASTIC_FLAG, EP_F_INT, EP_K_ROW_PTR, EP_K_COL_IDX,
- EP_K_VALUES, EP_K_ELASTIC, EP_WEIGHT, EP_DPHI, EP_SOLUTION, EP_K_VALUES_F32) = range(14)
+ EP_K_VALUES, EP_K_ELASTIC, EP_WEIGHT, EP_DPHI, EP_SOLUTION, EP_K_VALUES_F32, EP_WS_X, EP_WS_T,
+ EP_WS_START) = range(17)
+# learned warm start
+EP_WS_N_IN, EP_WS_WIDTH, EP_WS_N_OUT, EP_WS_N_PARAMS = 16, 128, 4, 19204
 
 EXPORTED = [
     "ep_default_opts", "ep_create", "ep_create_batch", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set",
     "ep_assemble", "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error",
-    "ep_linear_solve_noalloc",
+    "ep_linear_solve_noalloc", "ep_mlp_create", "ep_mlp_destroy", "ep_mlp_get_params", "ep_mlp_forward", "ep_mlp_grad",
+    "ep_mlp_train_step", "ep_ws_record", "ep_ws_samples", "ep_ws_attach",
 ]
 EP_NOALLOC_MAX_DOF = 32768
 EP_NOALLOC_MAX_ITERATIONS = 10000
@@ -67,7 +71,8 @@ class ep_step_report(C.Structure):
                 ("t_step_ms", C.c_double), ("status", C.c_int32), ("launches", C.c_int32),
                 ("n_assemble", C.c_int32), ("n_spmv", C.c_int32), ("t_assemble_kernel_ms", C.c_double),
                 ("t_spmv_kernel_ms", C.c_double), ("n_plastic_assembled", C.c_int64),
-                ("newton_its_fp32", C.c_int32), ("reserved", C.c_int32)]
+                ("newton_its_fp32", C.c_int32), ("start", C.c_int32), ("n_learned", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ep_info(C.Structure):
@@ -100,12 +105,24 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_linear_solve_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, vp, i32, i32, C.c_double, i32,
                                             C.POINTER(i32), dp, vp]
     lib.ep_linear_solve_noalloc.restype = i32
+    fp = C.POINTER(C.c_float)
+    lib.ep_mlp_create.argtypes = [C.POINTER(vp), fp, i32, vp]
+    lib.ep_mlp_destroy.argtypes = [vp]
+    lib.ep_mlp_get_params.argtypes = [vp, fp]
+    lib.ep_mlp_forward.argtypes = [vp, vp, i64, vp]
+    lib.ep_mlp_grad.argtypes = [vp, vp, vp, i64, dp, fp]
+    lib.ep_mlp_train_step.argtypes = [vp, vp, vp, i64, C.c_float, dp]
+    lib.ep_ws_record.argtypes = [vp, i64]
+    lib.ep_ws_samples.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
+    lib.ep_ws_attach.argtypes = [vp, vp]
     lib.ep_status_str.argtypes = [i32]
     lib.ep_status_str.restype = C.c_char_p
     lib.ep_last_error.argtypes = [vp]
     lib.ep_last_error.restype = C.c_char_p
     for name in ("ep_create", "ep_create_batch", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set", "ep_assemble",
-                 "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive"):
+                 "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_mlp_create", "ep_mlp_destroy",
+                 "ep_mlp_get_params", "ep_mlp_forward", "ep_mlp_grad", "ep_mlp_train_step", "ep_ws_record",
+                 "ep_ws_samples", "ep_ws_attach"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -263,6 +280,8 @@ class Context:
             EP_K_ELASTIC: ((i.nnz_blocks, i.dim, i.dim), np.float64), EP_WEIGHT: ((i.n_int,), np.float64),
             EP_DPHI: ((i.n_int, i.n_p, i.dim), np.float64), EP_SOLUTION: ((self.n_dof,), np.float64),
             EP_K_VALUES_F32: ((i.nnz_blocks, i.dim, i.dim), np.float32),
+            EP_WS_X: ((self.ws_rows(), EP_WS_N_IN), np.float32), EP_WS_T: ((self.ws_rows(), EP_WS_N_OUT), np.float32),
+            EP_WS_START: ((self.n_dof,), np.float64),
         }[field]
 
     # -- C calls -------------------------------------------------------------------
@@ -322,6 +341,25 @@ class Context:
             self._check(st)
         return out if raise_on_error else (st, out)
 
+    # -- learned warm start --------------------------------------------------------
+    def ws_record(self, max_rows: int):
+        """Record up to max_rows (inputs, targets) rows during later load paths (0 stops and frees)."""
+        self._check(lib().ep_ws_record(self.h, int(max_rows)))
+
+    def ws_samples_ptr(self):
+        """(device address of X [n][16], of T [n][4], n) of the recorded rows."""
+        x, t, n = C.c_void_p(), C.c_void_p(), C.c_int64(0)
+        self._check(lib().ep_ws_samples(self.h, C.byref(x), C.byref(t), C.byref(n)))
+        return x.value or 0, t.value or 0, n.value
+
+    def ws_rows(self) -> int:
+        return self.ws_samples_ptr()[2]
+
+    def ws_attach(self, mlp):
+        """Use `mlp` (an MLP) for warm_start = 2; None detaches."""
+        self._mlp = mlp
+        self._check(lib().ep_ws_attach(self.h, None if mlp is None else mlp.h))
+
     def K_csr(self, elastic=False, f32=False):
         """K as scipy CSR (DOF level) from the block-CSR arrays (f32: the FP32 tangent, as float64)."""
         import scipy.sparse as sp
@@ -330,6 +368,65 @@ class Context:
         field = EP_K_ELASTIC if elastic else (EP_K_VALUES_F32 if f32 else EP_K_VALUES)
         vals = self.get(field).astype(np.float64)
         return sp.bsr_matrix((vals, ci, rp), shape=(self.n_dof, self.n_dof)).tocsr()
+
+
+class MLP:
+    """ep_mlp_* handle: the warm-start network (16 -> 128 -> 128 -> 4) on one device.  X, T, Y are
+    torch CUDA float32 tensors (or device addresses as int)."""
+
+    def __init__(self, params, device: int = 0, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (EP_WS_N_PARAMS,):
+            raise ValueError(f"params must have {EP_WS_N_PARAMS} entries")
+        h = C.c_void_p()
+        st = lib().ep_mlp_create(C.byref(h), _ptr(p, C.c_float), int(device), C.c_void_p(_stream_ptr(stream)))
+        if st != EP_OK:
+            raise EPError(st, lib().ep_last_error(None).decode())
+        self.h = h
+
+    @staticmethod
+    def _addr(a):
+        return a if isinstance(a, int) else a.data_ptr()
+
+    def _check(self, st, what):
+        if st != EP_OK:
+            raise EPError(st, what)
+
+    def params(self) -> np.ndarray:
+        out = np.empty(EP_WS_N_PARAMS, dtype=np.float32)
+        self._check(lib().ep_mlp_get_params(self.h, _ptr(out, C.c_float)), "ep_mlp_get_params")
+        return out
+
+    def forward(self, X, Y, n_rows: int | None = None):
+        n = X.shape[0] if n_rows is None else n_rows
+        self._check(lib().ep_mlp_forward(self.h, C.c_void_p(self._addr(X)), int(n), C.c_void_p(self._addr(Y))),
+                    "ep_mlp_forward")
+
+    def grad(self, X, T, n_rows: int | None = None):
+        n = X.shape[0] if n_rows is None else n_rows
+        loss = C.c_double(0.0)
+        g = np.empty(EP_WS_N_PARAMS, dtype=np.float32)
+        self._check(lib().ep_mlp_grad(self.h, C.c_void_p(self._addr(X)), C.c_void_p(self._addr(T)), int(n),
+                                      C.byref(loss), _ptr(g, C.c_float)), "ep_mlp_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, lr: float, n_rows: int | None = None, want_loss: bool = True):
+        n = X.shape[0] if n_rows is None else n_rows
+        loss = C.c_double(float("nan"))
+        self._check(lib().ep_mlp_train_step(self.h, C.c_void_p(self._addr(X)), C.c_void_p(self._addr(T)), int(n),
+                                            float(lr), C.byref(loss) if want_loss else None), "ep_mlp_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ep_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def linear_solve_noalloc(dim: int, row_ptr, col_idx, diag_slot, vals, free_dof, b, x, method: int = 1,

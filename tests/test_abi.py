@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(ep.ep_mesh) == 4 + 4 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(ep.ep_material) == 8 + 8 * 8
     assert ctypes.sizeof(ep.ep_opts) == 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4
-    assert ctypes.sizeof(ep.ep_step_report) == 4 + 4 + 8 + 8 * 4 + 4 * 4 + 8 * 2 + 8 + 4 + 4
+    assert ctypes.sizeof(ep.ep_step_report) == 4 + 4 + 8 + 8 * 4 + 4 * 4 + 8 * 2 + 8 + 4 * 4
     o = ep.default_opts()   # calls into the library (host only)
     assert o.newton_rtol == 1e-10 and o.precond == 2 and o.split_elastic_cache == 1
 
@@ -89,3 +89,27 @@ def test_batch_rejects_mixed_element_types_without_gpu_work(libpath):
     h = ctypes.c_void_p()
     assert lib.ep_create_batch(ctypes.byref(h), 2, meshes, mats, bcs, 0, None) == ep.EP_ERR_INVALID_ARG
     assert b"different element type" in lib.ep_last_error(None)
+
+
+def test_warm_start_calls_reject_bad_input_without_gpu_work(libpath):
+    """The network and recording entry points validate their arguments before any CUDA call."""
+    import paper_1805_04155_gb300.ep as ep
+    lib = ep.lib()
+    h = ctypes.c_void_p()
+    assert lib.ep_mlp_create(ctypes.byref(h), None, 0, None) == ep.EP_ERR_INVALID_ARG
+    assert lib.ep_mlp_create(None, None, 0, None) == ep.EP_ERR_INVALID_ARG
+    assert lib.ep_mlp_forward(None, None, 4, None) == ep.EP_ERR_INVALID_ARG
+    assert lib.ep_mlp_train_step(None, None, None, 4, 1e-3, None) == ep.EP_ERR_INVALID_ARG
+    assert lib.ep_ws_record(None, 10) == ep.EP_ERR_INVALID_ARG
+    assert lib.ep_ws_attach(None, None) == ep.EP_ERR_INVALID_ARG
+    assert lib.ep_mlp_destroy(None) == ep.EP_OK
+
+
+def test_warm_start_sizes_match_the_oracle():
+    import paper_1805_04155_gb300.ep as ep
+    from oracle import warm_start as W
+    text = open(os.path.join(ROOT, "include", "ep.h")).read()
+    for name, val in (("EP_WS_N_IN", W.N_IN), ("EP_WS_WIDTH", W.WIDTH), ("EP_WS_N_OUT", W.N_OUT),
+                      ("EP_WS_N_PARAMS", W.N_PARAMS)):
+        assert re.search(rf"#define {name} {val}\b", text), name
+        assert getattr(ep, name) == val
