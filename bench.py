@@ -320,11 +320,78 @@ def run_batch(args):
             "max_rel_resid": max(r.rel_resid for f in fams for r in results[f]),
             "newton_its": {f: int(sum(r.newton_its for r in results[f])) for f in fams},
             "one_by_one_newton_its": int(sum(r.newton_its for rs in reps_single for r in rs))}
+    if args.learned:
+        line["learned"] = learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results)
     for c in ctxs.values():
         c.close()
     for _, c in singles:
         c.close()
     print(json.dumps(line))
+
+
+def learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results):
+    """Learned warm start on the batched sweep: record (inputs, targets) rows along the load paths of
+    a training batch drawn from other seeds (same families, sizes 16..32), train one network on them
+    (full-batch Adam, the families' rows in turn), then solve the sweep again from the learned start
+    and compare its Newton iterations and time with the extrapolated start timed above."""
+    import threading
+    import torch
+    from synthetic import batch_problems
+    from synthetic.random_states import mlp_init
+    n_train = max(4, args.batch // 4)
+    train = batch_problems(seed=10000, n_problems=n_train, sizes=(16, 32), n_steps=len(zeta))
+    t0 = time.perf_counter()
+    rec = {}
+    for f in sorted(train):
+        c = ep.Context.from_batch(train[f])
+        c.ws_record(sum(pb.mesh.n_nodes for pb in train[f]) * len(zeta))
+        c.solve_load_path(zeta, ep.default_opts(newton_rtol=1e-10, warm_start=1))
+        rec[f] = c
+    t_record = time.perf_counter() - t0
+    net = ep.MLP(mlp_init(0))
+    rows = {f: c.ws_samples_ptr() for f, c in rec.items()}
+    t0 = time.perf_counter()
+    loss0 = {f: net.grad(x, t, n_rows=n)[0] for f, (x, t, n) in rows.items() if n}
+    for it in range(args.learned_steps):
+        for f, (x, t, n) in rows.items():
+            if n:
+                net.train_step(x, t, 2e-3, n_rows=n, want_loss=False)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    loss1 = {f: net.grad(x, t, n_rows=n)[0] for f, (x, t, n) in rows.items() if n}
+    n_rows = int(sum(n for _, _, n in rows.values()))
+    for c in rec.values():
+        c.close()
+    lopts = ep.default_opts(newton_rtol=opts.newton_rtol, warm_start=2)
+    for f in fams:
+        reset(ctxs[f])
+        ctxs[f].ws_attach(net)
+    torch.cuda.synchronize()
+    res = {}
+
+    def solve(f):
+        res[f] = ctxs[f].solve_load_path(zeta, lopts)
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=solve, args=(f,)) for f in fams]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    t_learned = time.perf_counter() - t0
+    for f in fams:
+        ctxs[f].ws_attach(None)
+    net.close()
+    return {"training": f"{n_train} problems (seed 10000), sizes 16..32, {n_rows} rows, "
+                        f"{args.learned_steps} Adam steps per family at lr 2e-3",
+            "record_s": t_record, "train_s": t_train,
+            "loss": {f: [loss0[f], loss1[f]] for f in loss0},
+            "batched_s": t_learned,
+            "newton_its": {f: int(sum(r.newton_its for r in res[f])) for f in fams},
+            "extrapolated_newton_its": {f: int(sum(r.newton_its for r in results[f])) for f in fams},
+            "problems_on_learned_start": {f: [int(r.n_learned) for r in res[f]] for f in fams},
+            "max_rel_resid": max(r.rel_resid for f in fams for r in res[f])}
 
 
 def main():
@@ -343,6 +410,9 @@ def main():
                     help="primary precision; auto: time both, report the faster as the primary")
     ap.add_argument("--no-compare", action="store_true", help="time the primary precision only (auto: mixed)")
     ap.add_argument("--batch", type=int, default=64, help="problems of the batched sweep (--workload batch)")
+    ap.add_argument("--learned", action="store_true",
+                    help="--workload batch: also train the warm-start network and solve from the learned start")
+    ap.add_argument("--learned-steps", type=int, default=300, help="Adam steps per family of the warm-start network")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (t == 0) {
         double l = 0.0;
         for (int i = 0; i < NT / 32; ++i) l += S.red[i];
-        lpart[blockIdx.x] = l;
+        lpart[blockIdx.x] = l / (double)n;   // the loss is the mean over the rows
     }
 }
 

@@ -76,9 +76,10 @@ def test_network_forward_parity(ep):
     bound = 2 * _gamma(275) * a3
     print(f"\nforward: {X.shape[0]} rows, max err {err.max():.2e}, max err/bound {(err / bound).max():.2e}")
     assert np.all(err <= bound)
-    # weights are used as bfloat16: the unrounded network differs by far more than the bound
+    # weights are used as bfloat16: the GPU is far closer to the rounded network than the unrounded
+    # network is
     y_x, _ = W.mlp_forward(p, X, round_weights=False)
-    assert np.abs(y_x - y_or).max() > 100 * bound.max()
+    assert err.max() < 0.01 * np.abs(y_x - y_or).max()
     net.close()
 
 
@@ -186,9 +187,11 @@ def test_empty_and_invalid_calls(ep):
 
 
 # -- features, targets and learned starts on load paths ------------------------------------------
-def _column(n, scale=(1.0, 1.0, 1.0, 1.0), n_steps=12):
+def _column(n, scale=(1.0, 1.0, 1.0, 1.0), n_steps=13):
     """P1 plane-strain column (von Mises, isotropic hardening) with E, nu, Y, H scaled, loaded to 1.5x
-    its first-yield traction: elastic for two thirds of the path, then plastic throughout."""
+    its first-yield traction: elastic for two thirds of the path, then plastic throughout.  With
+    n_steps not a multiple of 3 no step ends exactly at first yield, where the plastic flag is a tie
+    that rounding decides."""
     base = vm_iso_material()
     mat = Material(VM_ISO, E=base.E * scale[0], nu=min(0.45, base.nu * scale[1]), Y=base.Y * scale[2],
                    H=base.H * scale[3])
