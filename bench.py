@@ -47,6 +47,12 @@ UNIT = "Gpts/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP64 FMA pipe of a GB300: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 FMA of a GB300: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FMAs per row of one training pass of the warm-start network (forward 16*128 + 128*128 + 128*4; backward
+# dW3 + dH2 + dW2 + dH1 + dW1)
+MLP_FMA_FWD = 16 * 128 + 128 * 128 + 128 * 4
+MLP_FMA_TRAIN = MLP_FMA_FWD + 512 + 512 + 128 * 128 + 128 * 128 + 16 * 128
 
 
 def _workload(name: str, full: bool = True, n: int = 0):
@@ -360,6 +366,7 @@ def learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results
     t_train = time.perf_counter() - t0
     loss1 = {f: net.grad(x, t, n_rows=n)[0] for f, (x, t, n) in rows.items() if n}
     n_rows = int(sum(n for _, _, n in rows.values()))
+    train_tflops = args.learned_steps * n_rows * 2 * MLP_FMA_TRAIN / t_train / 1e12
     for c in rec.values():
         c.close()
     lopts = ep.default_opts(newton_rtol=opts.newton_rtol, warm_start=2)
@@ -386,12 +393,55 @@ def learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results
     return {"training": f"{n_train} problems (seed 10000), sizes 16..32, {n_rows} rows, "
                         f"{args.learned_steps} Adam steps per family at lr 2e-3",
             "record_s": t_record, "train_s": t_train,
+            "train_tflops_wall": train_tflops, "train_frac_of_fp32_fma_peak": train_tflops / FP32_PEAK_TFLOPS,
             "loss": {f: [loss0[f], loss1[f]] for f in loss0},
             "batched_s": t_learned,
             "newton_its": {f: int(sum(r.newton_its for r in res[f])) for f in fams},
             "extrapolated_newton_its": {f: int(sum(r.newton_its for r in results[f])) for f in fams},
             "problems_on_learned_start": {f: [int(r.n_learned) for r in res[f]] for f in fams},
             "max_rel_resid": max(r.rel_resid for f in fams for r in res[f])}
+
+
+def run_mlp(args):
+    """Training throughput of the warm-start network alone: Adam steps over n seeded synthetic rows
+    (2^21 by default: 168 MB of inputs and targets, more than L2), timed with CUDA events on the
+    network's stream.  Roofline: FP32 FMA (the layers are dense FP32 loops over shared memory)."""
+    import torch
+    import paper_1805_04155_gb300.ep as ep
+    from synthetic.random_states import mlp_init, mlp_rows
+    n = args.n if args.n else 1 << 21
+    X, T = mlp_rows(n, seed=1805)
+    Xd = torch.from_numpy(X).cuda()
+    Td = torch.from_numpy(T).cuda()
+    stream = torch.cuda.current_stream()
+    net = ep.MLP(mlp_init(0), stream=stream)
+    for _ in range(args.warmup):
+        net.train_step(Xd, Td, 1e-3, want_loss=False)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.train_step(Xd, Td, 1e-3, want_loss=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    loss = net.train_step(Xd, Td, 1e-3)
+    tflops = n * 2 * MLP_FMA_TRAIN / (ms / 1e3) / 1e12
+    net.close()
+    line = {"metric": "warm-start network training: rows per second (forward + backward + Adam)",
+            "value": n / (ms / 1e3), "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32 (bf16 weights)", "data": "synthetic",
+            "config": {"workload": f"{n} rows of 16 inputs / 4 targets, 16-128-128-4 network",
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_mlp<train> + k_mlp_update (one Adam step)",
+                         "flops_per_row": 2 * MLP_FMA_TRAIN,
+                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived)"},
+            "loss_after": loss, "clocks": clk}
+    print(json.dumps(line))
 
 
 def main():
@@ -434,6 +484,9 @@ def main():
 
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "mlp":
+        run_mlp(args)
         return
     prob = _workload(args.workload, n=args.n)
     stream = torch.cuda.current_stream()
