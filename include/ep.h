@@ -343,8 +343,9 @@ ep_status ep_linear_solve_noalloc(int32_t dim, int64_t n_nodes, const int32_t* r
  * start).  The learned start
  * needs three converged steps since ep_ws_attach / ep_ws_record and a load
  * that keeps its direction; each problem of a batch keeps the plain
- * extrapolation when that has the smaller residual, and a step that fails to
- * converge from either is retried from the last converged u.
+ * extrapolation when that has the smaller residual (the network is not run
+ * when the extrapolated start already meets the Newton tolerance), and a step
+ * that fails to converge from either is retried from the last converged u.
  *
  * Parameters: one float32 vector of EP_WS_N_PARAMS entries, W1 [128][16],
  * b1 [128], W2 [128][128], b2 [128], W3 [4][128], b3 [4] (y = W x + b).

@@ -15,6 +15,10 @@ functions only choose the next load factor and read results back:
   state in place); the paper's method has no damping for large increments.
 * external_work: f_max^T u_k, the ordinate of the hysteresis curve of the
   cyclic von Mises experiment (Section 8.2).
+* autotune: picks the fastest solver schedule (precision, Krylov method,
+  preconditioner) for a context by timing each on the first load steps and
+  restoring the state in between (the paper uses one direct solver; the
+  schedule is this implementation's choice, Section 5's linear systems).
 """
 from __future__ import annotations
 
@@ -65,3 +69,51 @@ def strip_footing_path(ctx, problem, u_max: float = 1.0, du0: float = 1e-3, soft
 def external_work(ctx, problem) -> float:
     """f_max^T u_k with f_max the traction load at zeta = 1."""
     return float(problem.f_unit @ ctx.get(ep.EP_U))
+
+
+# -- schedule autotuner ---------------------------------------------------------------------------
+STATE_FIELDS = (ep.EP_U, ep.EP_PLASTIC_STRAIN, ep.EP_HARDENING, ep.EP_STRESS, ep.EP_PLASTIC_FLAG)
+
+
+def schedule_candidates(symmetric: bool, base=None):
+    """Solver schedules to try: precision x (Krylov method, preconditioner).  CG only for a symmetric
+    tangent (von Mises, associated Drucker-Prager); GMRES and BiCGStab otherwise; block Jacobi and
+    the AMG V-cycle as preconditioners.  Returns a list of dicts of ep_opts fields."""
+    methods = [1, 3] if symmetric else [3, 2]
+    out = []
+    for prec in (ep.EP_FP64, ep.EP_MIXED):
+        for m in methods:
+            for pc in (2, 1):
+                d = dict(base or {})
+                d.update(precision=prec, krylov=m, precond=pc)
+                out.append(d)
+    return out
+
+
+def autotune(ctx, zeta, trial_steps: int = 3, candidates=None, base_opts=None):
+    """Time each candidate schedule on the first `trial_steps` load steps from the context's current
+    state, restoring that state after every trial; returns (best opts, [(candidate, seconds or None)]).
+
+    The time of a trial is the sum of its steps' t_step_ms (set-up work done once per context, such as
+    the AMG hierarchy, is outside the steps).  A candidate whose trial fails is skipped; the trial
+    paths of the others converge to the same tolerance, so their solutions agree."""
+    import numpy as np
+    base = dict(newton_rtol=1e-10) if base_opts is None else dict(base_opts)
+    if candidates is None:
+        sym = int(ctx.material.model) != ep.EP_DP or (ctx.material.phi == ctx.material.psi and ctx.material.Hc == 0.0)
+        candidates = schedule_candidates(sym, base)
+    saved = {f: ctx.get(f).copy() for f in STATE_FIELDS}
+    z = np.asarray(zeta, dtype=np.float64)[:max(1, trial_steps)]
+    results = []
+    for cand in candidates:
+        opts = ep.default_opts(**cand)
+        st, reps = ctx.solve_load_path(z, opts, raise_on_error=False)
+        t = sum(r.t_step_ms for r in reps) / 1e3 if st == ep.EP_OK else None
+        results.append((cand, t))
+        for f, v in saved.items():
+            ctx.set(f, v)
+    ok = [(c, t) for c, t in results if t is not None]
+    if not ok:
+        raise ep.EPError(ep.EP_ERR_STATE, "autotune: every candidate schedule failed on the trial steps")
+    best = min(ok, key=lambda ct: ct[1])[0]
+    return ep.default_opts(**best), results
