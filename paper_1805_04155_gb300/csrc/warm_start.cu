@@ -17,10 +17,12 @@
 //                 writes them once (deterministic, no atomics)
 //   k_mlp_update  sums the CTA partials in a fixed order, then an Adam step
 //                 (or only returns the gradient)
-// One CTA of 256 threads per SM (108 KB of shared memory: the tile's inputs,
-// both hidden activations and all bfloat16 weights).  The network is small
-// next to a Newton iteration (about 3.7e4 FMA per row forward), so its layers
-// run as FP32 FMA loops over shared memory rather than tensor-core tiles.
+// One CTA of 256 threads per SM (149 KB of shared memory: the tile's inputs,
+// both hidden activations and FP32 copies of the bfloat16 weights); each
+// thread computes a 4 x 8 tile of the 128-wide layers, 12 shared loads per 32
+// FMA.  The network is small next to a Newton iteration (about 1.9e4 FMA per
+// row forward), so its layers run as FP32 FMA loops over shared memory rather
+// than tensor-core tiles.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -46,12 +48,16 @@ static_assert(NIN == 16 && NW == 128 && NOUT == 4, "the thread mapping below ass
 
 constexpr int TR = 64;          // rows per tile
 constexpr int NT = 256;         // threads per CTA: 8 warps
-constexpr int LX = NIN + 1;     // padded row strides in shared memory (odd: column reads by the
-constexpr int LH = NW + 1;      // 32 lanes of a warp, one row each, hit 32 different banks)
+constexpr int LX = NIN + 1;     // padded row strides in shared memory: odd strides put the 16 column
+constexpr int LH = NW + 1;      // groups of a warp (consecutive rows or columns) in distinct banks
+constexpr int LW1 = NIN + 1;
+constexpr int LW = NW + 1;
 constexpr int LY = NOUT + 1;
 constexpr float LAMBDA_PL = 0.1f;
 constexpr float ADAM_B1 = 0.9f, ADAM_B2 = 0.999f, ADAM_EPS = 1e-8f;
 
+// Weights are kept in shared memory as FP32 copies of their bfloat16 values (exact), so the inner
+// loops are one load per operand and no conversions.
 struct MlpSmem {
     double red[NT / 32];
     float X[TR * LX];
@@ -59,15 +65,14 @@ struct MlpSmem {
     float H2[TR * LH];
     float Y[TR * LY];           // outputs, then their loss gradients
     float b1[NW], b2[NW], b3[NOUT];
-    __nv_bfloat16 W1[NW * NIN], W2[NW * NW], W3[NOUT * NW];
+    float W1[NW * LW1], W2[NW * LW], W3[NOUT * LW];
 };
 
-__device__ __forceinline__ float bf(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// Thread mapping (lane = t % 32, w = t / 32):
-//   activations (r, j): rows r = lane + 32 a (a < 2), columns j = w + 8 m (m < 16)
-//   weight gradient dW2 / dW1 (j, i): j = lane + 32 c (c < 4), i = w + 8 m (m < 16 / m < 2)
-//   dW3 entry e = t + 256 q (q < 2): o = e / 128, i = e % 128
+// Thread mapping: cg = t % 16, rg = t / 16 (two row groups per warp: loads indexed by rg are broadcasts,
+// loads indexed by cg hit 16 distinct banks through the odd strides).
+//   activations (r, j) of the 128-wide layers: r = rg + 16 a (a < 4), j = cg + 16 b (b < 8): 4 x 8 tile
+//   dW2 (j, i): j = cg + 16 b (b < 8), i = rg + 16 a (a < 8); dW1 (j, i): j = cg + 16 b, i = rg
+//   layer 3 and dY (r, o): r = t / 4, o = t % 4; dW3 entry e = t + 256 q (q < 2): o = e / 128, i = e % 128
 template <bool TRAIN>
 __global__ void __launch_bounds__(NT, 1)
     k_mlp(const float* __restrict__ X, const float* __restrict__ T, int64_t n, float inv_n, const float* __restrict__ p,
@@ -76,25 +81,25 @@ __global__ void __launch_bounds__(NT, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    for (int i = t; i < NW * NIN; i += NT) S.W1[i] = pb[OFF_W1 + i];
-    for (int i = t; i < NW * NW; i += NT) S.W2[i] = pb[OFF_W2 + i];
-    for (int i = t; i < NOUT * NW; i += NT) S.W3[i] = pb[OFF_W3 + i];
+    const int cg = t & 15, rg = t >> 4;
+    for (int i = t; i < NW * NIN; i += NT) S.W1[(i / NIN) * LW1 + i % NIN] = __bfloat162float(pb[OFF_W1 + i]);
+    for (int i = t; i < NW * NW; i += NT) S.W2[(i / NW) * LW + i % NW] = __bfloat162float(pb[OFF_W2 + i]);
+    for (int i = t; i < NOUT * NW; i += NT) S.W3[(i / NW) * LW + i % NW] = __bfloat162float(pb[OFF_W3 + i]);
     if (t < NW) {
         S.b1[t] = p[OFF_B1 + t];
         S.b2[t] = p[OFF_B2 + t];
     }
     if (t < NOUT) S.b3[t] = p[OFF_B3 + t];
 
-    float g1[4][2], g2[4][16], g3[2];
-    float gb1 = 0.f, gb2 = 0.f, gb3 = 0.f;
+    float g2[8][8], g1[8], g3[2], gb1[8], gb2[8];
+    float gb3 = 0.f;
     double lsum = 0.0;
     if (TRAIN) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int b = 0; b < 8; ++b) {
 #pragma unroll
-            for (int m = 0; m < 2; ++m) g1[c][m] = 0.f;
-#pragma unroll
-            for (int m = 0; m < 16; ++m) g2[c][m] = 0.f;
+            for (int a = 0; a < 8; ++a) g2[b][a] = 0.f;
+            g1[b] = gb1[b] = gb2[b] = 0.f;
         }
         g3[0] = g3[1] = 0.f;
     }
@@ -111,80 +116,84 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
         // layer 1: H1 = relu(X W1^T + b1)
         {
-            float acc[2][16];
+            float acc[4][8];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) acc[0][m] = acc[1][m] = 0.f;
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 #pragma unroll 4
             for (int i = 0; i < NIN; ++i) {
-                const float x0 = S.X[lane * LX + i], x1 = S.X[(lane + 32) * LX + i];
+                float xv[4], wv[8];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const float wv = bf(S.W1[(w + 8 * m) * NIN + i]);
-                    acc[0][m] = fmaf(wv, x0, acc[0][m]);
-                    acc[1][m] = fmaf(wv, x1, acc[1][m]);
-                }
+                for (int a = 0; a < 4; ++a) xv[a] = S.X[(rg + 16 * a) * LX + i];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) wv[b] = S.W1[(cg + 16 * b) * LW1 + i];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(wv[b], xv[a], acc[a][b]);
             }
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const int j = w + 8 * m;
-                    S.H1[(lane + 32 * a) * LH + j] = fmaxf(acc[a][m] + S.b1[j], 0.f);
+                for (int b = 0; b < 8; ++b) {
+                    const int j = cg + 16 * b;
+                    S.H1[(rg + 16 * a) * LH + j] = fmaxf(acc[a][b] + S.b1[j], 0.f);
                 }
         }
         __syncthreads();
         // layer 2: H2 = relu(H1 W2^T + b2)
         {
-            float acc[2][16];
+            float acc[4][8];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) acc[0][m] = acc[1][m] = 0.f;
-#pragma unroll 4
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
             for (int i = 0; i < NW; ++i) {
-                const float h0 = S.H1[lane * LH + i], h1 = S.H1[(lane + 32) * LH + i];
+                float hv[4], wv[8];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const float wv = bf(S.W2[(w + 8 * m) * NW + i]);
-                    acc[0][m] = fmaf(wv, h0, acc[0][m]);
-                    acc[1][m] = fmaf(wv, h1, acc[1][m]);
-                }
+                for (int a = 0; a < 4; ++a) hv[a] = S.H1[(rg + 16 * a) * LH + i];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) wv[b] = S.W2[(cg + 16 * b) * LW + i];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(wv[b], hv[a], acc[a][b]);
             }
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const int j = w + 8 * m;
-                    S.H2[(lane + 32 * a) * LH + j] = fmaxf(acc[a][m] + S.b2[j], 0.f);
+                for (int b = 0; b < 8; ++b) {
+                    const int j = cg + 16 * b;
+                    S.H2[(rg + 16 * a) * LH + j] = fmaxf(acc[a][b] + S.b2[j], 0.f);
                 }
         }
         __syncthreads();
-        // layer 3: Y = H2 W3^T + b3 (warps 0..3, one output each); in training, the loss and dL/dY
-        if (w < NOUT) {
-            const int o = w;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int r = lane + 32 * a;
-                float acc = 0.f;
+        // layer 3: Y = H2 W3^T + b3, one output per thread; in training, the loss and dL/dY
+        {
+            const int r = t >> 2, o = t & 3;
+            float acc = 0.f;
 #pragma unroll 8
-                for (int i = 0; i < NW; ++i) acc = fmaf(bf(S.W3[o * NW + i]), S.H2[r * LH + i], acc);
-                const float y = acc + S.b3[o];
-                const int64_t row = row0 + r;
-                if (!TRAIN) {
-                    if (row < n) Y[row * NOUT + o] = y;
-                } else {
-                    float dy = 0.f;
-                    if (row < n) {
-                        const float tv = T[row * NOUT + o];
-                        if (o < 3) {
-                            const float d = y - tv;
-                            lsum += (double)d * (double)d;
-                            dy = 2.f * d * inv_n;
-                        } else {
-                            lsum += (double)LAMBDA_PL * (double)(fmaxf(y, 0.f) - y * tv + log1pf(expf(-fabsf(y))));
-                            dy = LAMBDA_PL * (1.f / (1.f + expf(-y)) - tv) * inv_n;
-                        }
+            for (int i = 0; i < NW; ++i) acc = fmaf(S.W3[o * LW + i], S.H2[r * LH + i], acc);
+            const float y = acc + S.b3[o];
+            const int64_t row = row0 + r;
+            if (!TRAIN) {
+                if (row < n) Y[row * NOUT + o] = y;
+            } else {
+                float dy = 0.f;
+                if (row < n) {
+                    const float tv = T[row * NOUT + o];
+                    if (o < 3) {
+                        const float d = y - tv;
+                        lsum += (double)d * (double)d;
+                        dy = 2.f * d * inv_n;
+                    } else {
+                        lsum += (double)LAMBDA_PL * (double)(fmaxf(y, 0.f) - y * tv + log1pf(expf(-fabsf(y))));
+                        dy = LAMBDA_PL * (1.f / (1.f + expf(-y)) - tv) * inv_n;
                     }
-                    S.Y[r * LY + o] = dy;
                 }
+                S.Y[r * LY + o] = dy;
             }
         }
         if (!TRAIN) continue;
@@ -203,102 +212,97 @@ __global__ void __launch_bounds__(NT, 1)
             gb3 += acc;
         }
         __syncthreads();
-        // dH2 = (dY W3) * [H2 > 0], in place of H2
+        // dH2 = (dY W3) * [H2 > 0], in place of H2 (each thread reads and writes only its own entries)
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int r = lane + 32 * a;
+        for (int a = 0; a < 4; ++a) {
+            const int r = rg + 16 * a;
             float dy[NOUT];
 #pragma unroll
             for (int o = 0; o < NOUT; ++o) dy[o] = S.Y[r * LY + o];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                const int i = w + 8 * m;
+            for (int b = 0; b < 8; ++b) {
+                const int i = cg + 16 * b;
                 float v = 0.f;
 #pragma unroll
-                for (int o = 0; o < NOUT; ++o) v = fmaf(dy[o], bf(S.W3[o * NW + i]), v);
+                for (int o = 0; o < NOUT; ++o) v = fmaf(dy[o], S.W3[o * LW + i], v);
                 const float h = S.H2[r * LH + i];
                 S.H2[r * LH + i] = h > 0.f ? v : 0.f;
             }
         }
         __syncthreads();
-        // dW2 += dH2^T H1, db2 += sum dH2
+        // dW2 += dH2^T H1 (rg = 0 threads also sum db2 over the rows)
         for (int r = 0; r < TR; ++r) {
-            float dh[4];
+            float dh[8], hv[8];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) dh[c] = S.H2[r * LH + lane + 32 * c];
+            for (int b = 0; b < 8; ++b) dh[b] = S.H2[r * LH + cg + 16 * b];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                const float h1 = S.H1[r * LH + w + 8 * m];
+            for (int a = 0; a < 8; ++a) hv[a] = S.H1[r * LH + rg + 16 * a];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) g2[c][m] = fmaf(dh[c], h1, g2[c][m]);
+            for (int b = 0; b < 8; ++b)
+#pragma unroll
+                for (int a = 0; a < 8; ++a) g2[b][a] = fmaf(dh[b], hv[a], g2[b][a]);
+            if (rg == 0) {
+#pragma unroll
+                for (int b = 0; b < 8; ++b) gb2[b] += dh[b];
             }
         }
-        if (t < NW) {
-            float acc = 0.f;
-            for (int r = 0; r < TR; ++r) acc += S.H2[r * LH + t];
-            gb2 += acc;
-        }
         __syncthreads();
-        // dH1 = (dH2 W2) * [H1 > 0], in place of H1 (each thread reads and writes only its own H1 entries)
+        // dH1 = (dH2 W2) * [H1 > 0], in place of H1
         {
-            float acc[2][16];
+            float acc[4][8];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) acc[0][m] = acc[1][m] = 0.f;
-#pragma unroll 4
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
             for (int j = 0; j < NW; ++j) {
-                const float d0 = S.H2[lane * LH + j], d1 = S.H2[(lane + 32) * LH + j];
+                float dv[4], wv[8];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const float wv = bf(S.W2[j * NW + w + 8 * m]);
-                    acc[0][m] = fmaf(d0, wv, acc[0][m]);
-                    acc[1][m] = fmaf(d1, wv, acc[1][m]);
-                }
+                for (int a = 0; a < 4; ++a) dv[a] = S.H2[(rg + 16 * a) * LH + j];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) wv[b] = S.W2[j * LW + cg + 16 * b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(dv[a], wv[b], acc[a][b]);
             }
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const int idx = (lane + 32 * a) * LH + w + 8 * m;
-                    S.H1[idx] = S.H1[idx] > 0.f ? acc[a][m] : 0.f;
+                for (int b = 0; b < 8; ++b) {
+                    const int idx = (rg + 16 * a) * LH + cg + 16 * b;
+                    S.H1[idx] = S.H1[idx] > 0.f ? acc[a][b] : 0.f;
                 }
         }
         __syncthreads();
-        // dW1 += dH1^T X, db1 += sum dH1
+        // dW1 += dH1^T X (rg = 0 threads also sum db1)
         for (int r = 0; r < TR; ++r) {
-            float dh[4];
+            const float xv = S.X[r * LX + rg];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) dh[c] = S.H1[r * LH + lane + 32 * c];
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const float x = S.X[r * LX + w + 8 * m];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) g1[c][m] = fmaf(dh[c], x, g1[c][m]);
+            for (int b = 0; b < 8; ++b) {
+                const float dh = S.H1[r * LH + cg + 16 * b];
+                g1[b] = fmaf(dh, xv, g1[b]);
+                if (rg == 0) gb1[b] += dh;
             }
-        }
-        if (t < NW) {
-            float acc = 0.f;
-            for (int r = 0; r < TR; ++r) acc += S.H1[r * LH + t];
-            gb1 += acc;
         }
     }
     if (!TRAIN) return;
     float* gp = gpart + (size_t)blockIdx.x * NPAR;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int j = lane + 32 * c;
+    for (int b = 0; b < 8; ++b) {
+        const int j = cg + 16 * b;
+        gp[OFF_W1 + j * NIN + rg] = g1[b];
 #pragma unroll
-        for (int m = 0; m < 2; ++m) gp[OFF_W1 + j * NIN + w + 8 * m] = g1[c][m];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) gp[OFF_W2 + j * NW + w + 8 * m] = g2[c][m];
+        for (int a = 0; a < 8; ++a) gp[OFF_W2 + j * NW + rg + 16 * a] = g2[b][a];
+        if (rg == 0) {
+            gp[OFF_B1 + j] = gb1[b];
+            gp[OFF_B2 + j] = gb2[b];
+        }
     }
     gp[OFF_W3 + t] = g3[0];
     gp[OFF_W3 + t + NT] = g3[1];
-    if (t < NW) {
-        gp[OFF_B1 + t] = gb1;
-        gp[OFF_B2 + t] = gb2;
-    }
     if (t < NOUT) gp[OFF_B3 + t] = gb3;
-    // the CTA's loss: warp sums, then warp 0
+    // the CTA's loss: warp sums, then thread 0
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
     if (lane == 0) S.red[w] = lsum;
