@@ -360,13 +360,11 @@ struct Mlp {
     std::string err;
 };
 
+// The kernels' shared-memory opt-in (idempotent; contexts on several host threads may race here harmlessly).
 cudaError_t mlp_attr() {
-    static bool done = false;
-    if (done) return cudaSuccess;
     const int bytes = (int)sizeof(MlpSmem);
     cudaError_t e = cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    done = e == cudaSuccess;
     return e;
 }
 
