@@ -11,7 +11,9 @@ solver, update u, and stop.  Readings where the paper leaves a choice:
   * initial iterate: 'previous' = the last converged u with the new Dirichlet
     values (ALG-NEWTON's u_{D,k} extended by the last solution), or
     'extrapolate' = u_{k-1} + (dzeta_k/dzeta_{k-1}) (u_{k-1} - u_{k-2}) with the
-    new Dirichlet values;
+    new Dirichlet values, used only while the load keeps its direction
+    (dzeta_k/dzeta_{k-1} > 0); a step that does not converge from the
+    extrapolated start is solved again from the 'previous' one;
   * after convergence the trial internal variables of the last constitutive
     evaluation become the state of step k (Sections 2.1, 7.1, 7.2).
 """
@@ -80,13 +82,25 @@ class OracleSolver:
         if mode == "extrapolate" and self.u_prev is not None and len(self.zeta_done) >= 2:
             dz_prev = self.zeta_done[-1] - self.zeta_done[-2]
             dz = zeta - self.zeta_done[-1]
-            if dz_prev != 0.0:
+            if dz_prev != 0.0 and dz / dz_prev > 0.0:
                 u = self.u + (dz / dz_prev) * (self.u - self.u_prev)
         fixed = ~self.free
         u[fixed] = zeta * self.p.u_D_unit[fixed]
         return u
 
     def solve_step(self, zeta, tol=None, maxit=50, mode="extrapolate") -> StepReport:
+        rep = self._newton(zeta, tol, maxit, mode)
+        if not rep[-1].converged and mode == "extrapolate":
+            rep = self._newton(zeta, tol, maxit, "previous")
+        u, res, report = rep
+        # commit (state of step k)
+        self.u_prev, self.u = self.u, u
+        self.zeta_done.append(zeta)
+        self.ep, self.hard = res["ep"], res["hard"]
+        self.stress, self.plastic = res["S"], res["plastic"]
+        return report
+
+    def _newton(self, zeta, tol, maxit, mode):
         tol = self.p.newton_rtol if tol is None else tol
         f = zeta * self.p.f_unit
         u = self.start_iterate(zeta, mode)
@@ -114,12 +128,7 @@ class OracleSolver:
             u = u + du
             einc.append(self.energy_norm(du) / max(self.energy_norm(u_old) + self.energy_norm(u), 1e-300))
             it += 1
-        # commit (state of step k)
-        self.u_prev, self.u = self.u, u
-        self.zeta_done.append(zeta)
-        self.ep, self.hard = res["ep"], res["hard"]
-        self.stress, self.plastic = res["S"], res["plastic"]
-        return StepReport(it, hist[-1], int(np.count_nonzero(res["plastic"])), hist, einc, converged)
+        return u, res, StepReport(it, hist[-1], int(np.count_nonzero(res["plastic"])), hist, einc, converged)
 
     def solve_path(self, zetas=None, **kw):
         zetas = self.p.zeta if zetas is None else zetas

@@ -337,7 +337,8 @@ def trajectory_samples(problem, zetas, solver_factory, free=None):
                             stat, dim)
         else:
             X = None
-        sol.solve_step(z, tol=1e-13)
+        if not sol.solve_step(z, tol=1e-13).converged:
+            raise RuntimeError(f"oracle Newton did not converge at zeta = {z}")
         pf = node_plastic_fraction(problem.mesh.elem, sol.plastic, n_q, n_nodes)
         if X is not None:
             u_ex = extrapolated_start(us[-1], us[-2], (z, zs[-1], zs[-2]), free, problem.u_D_unit)
@@ -365,7 +366,8 @@ def last_learned_start(problem, zetas, params, solver_factory):
     stat = static_features(problem.material, problem.dirichlet, dim)
     us, zs, pfs, prox = [sol.u.copy()], [0.0], [np.zeros(n_nodes)], [np.zeros(n_nodes)]
     for z in zetas[:-1]:
-        sol.solve_step(float(z), tol=1e-13)
+        if not sol.solve_step(float(z), tol=1e-13).converged:
+            raise RuntimeError(f"oracle Newton did not converge at zeta = {z}")
         us.append(sol.u.copy())
         zs.append(float(z))
         pfs.append(node_plastic_fraction(problem.mesh.elem, sol.plastic, n_q, n_nodes))
