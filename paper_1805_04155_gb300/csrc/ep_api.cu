@@ -193,6 +193,7 @@ struct Ctx {
     // mesh and pattern
     double* coords = nullptr;
     int32_t *elem = nullptr, *slots = nullptr, *row_ptr = nullptr, *col_idx = nullptr, *diag_slot = nullptr;
+    int32_t* spmv_perm = nullptr;   // SpMV row order: rows grouped by their number of blocks
     double *dphi = nullptr, *wgt = nullptr;
     double *Kel = nullptr, *Kt = nullptr;
     // mixed path (allocated on first use): FP32 tangent, FP32 K_elast, FP32 right-hand side
@@ -282,6 +283,7 @@ static BsrT<T> bsr_dev(const Ctx* c, const T* vals) {
     b.diag_slot = c->diag_slot;
     b.vals = vals;
     b.free_dof = c->free_dof;
+    b.perm = c->spmv_perm;
     return b;
 }
 
@@ -579,6 +581,7 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     CKF(dalloc(c, &c->row_ptr, c->n_nodes + 1));
     CKF(dalloc(c, &c->col_idx, c->nnzb));
     CKF(dalloc(c, &c->diag_slot, c->n_nodes));
+    CKF(dalloc(c, &c->spmv_perm, c->n_nodes));
     CKF(dalloc(c, &c->dphi, c->n_int * c->n_p * d));
     CKF(dalloc(c, &c->wgt, c->n_int));
     CKF(dalloc(c, &c->Kel, c->nnzb * d * d));
@@ -637,6 +640,14 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     CKF(cudaMemcpyAsync(c->row_ptr, row_ptr.data(), sizeof(int32_t) * row_ptr.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->col_idx, col_idx.data(), sizeof(int32_t) * col_idx.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->diag_slot, diag.data(), sizeof(int32_t) * diag.size(), cudaMemcpyHostToDevice, s));
+    // SpMV row order: rows sorted by their number of blocks (stable, so rows of one length keep the
+    // mesh order and their neighbours' x entries stay close)
+    std::vector<int32_t> perm(c->n_nodes);
+    for (int64_t n = 0; n < c->n_nodes; ++n) perm[n] = (int32_t)n;
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+        return row_ptr[a + 1] - row_ptr[a] < row_ptr[b + 1] - row_ptr[b];
+    });
+    CKF(cudaMemcpyAsync(c->spmv_perm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(d_dhat, dhat.data(), sizeof(double) * dhat.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(d_wq, wq.data(), sizeof(double) * wq.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->free_dof, freem.data(), c->n_dof, cudaMemcpyHostToDevice, s));

@@ -149,6 +149,8 @@ struct BsrT {
     const int32_t* diag_slot;  // [n_rows] block index of the diagonal block
     const T* vals;             // [nnzb][dim][dim]
     const uint8_t* free_dof;   // [n_rows*dim], 1 = free
+    const int32_t* perm = nullptr;   // SpMV row order (rows grouped by length, a permutation of
+                                     // 0..n_rows-1), or null for the natural order
 };
 using BsrDev = BsrT<double>;   // the FP64 tangent
 using BsrF = BsrT<float>;      // the FP32 tangent of the mixed path

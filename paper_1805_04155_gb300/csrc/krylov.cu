@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(VB) k_spmv(BsrT<TA> A, const TX* __restrict__ 
     const int lg = lane % G;
     TA dot = TA(0);
     for (int64_t rbase = warp * GPW; rbase < A.n_rows; rbase += nwarps * GPW) {
-        const int64_t row = rbase + lane / G;
+        // the G-lane groups of a warp take consecutive entries of the row order: with rows grouped
+        // by length they run the same number of block steps (no lanes idle on short rows)
+        const int64_t idx = rbase + lane / G;
+        const int64_t row = idx < A.n_rows ? (A.perm ? (int64_t)A.perm[idx] : idx) : A.n_rows;
         TA acc[D];
 #pragma unroll
         for (int r = 0; r < D; ++r) acc[r] = TA(0);
