@@ -51,18 +51,29 @@ def test_noalloc_solve_matches_context_solve(ep, model, method):
     dev = torch.device("cuda:0")
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
     args = [T(rp), T(ci), T(diag), T(vals), T(prob.dirichlet == 0).to(torch.uint8), T(b)]
+    K = ctx.K_csr()
+    first = None
     for call in range(2):            # the second call must not see the first one's workspace
         x = torch.full((prob.n_dof,), float("nan"), dtype=torch.float64, device=dev)
         st, its, rel = ep.linear_solve_noalloc(2, *args, x, method=method, precond=1, rtol=1e-12, maxit=5000)
         torch.cuda.synchronize()
         assert st == ep.EP_OK, ep.lib().ep_last_error(None)
         xh = x.cpu().numpy()
-        # the context's SpMV takes its rows in a length-grouped order and sums the solver's dot
-        # products in that order; the workspace-free solve uses the natural order, so the two differ
-        # in the last bits and their iteration counts by a few at this tolerance
-        assert abs(its - its_ref) <= max(3, its_ref // 50)
         assert np.all(xh[~free] == 0.0)
-        assert np.abs(xh - x_ref).max() <= TOL * np.abs(x_ref).max()
+        # the context's SpMV takes its rows in a length-grouped order and sums the solver's dot
+        # products in that order; the workspace-free solve uses the natural order: both solve the
+        # same system to the same tolerance, so their true residuals meet it, while their iterates
+        # (and iteration counts) differ by rounding, amplified by the system's conditioning
+        true_rel = np.linalg.norm((b - K @ xh)[free]) / np.linalg.norm(b[free])
+        print(f"\nmethod {method}: its {its} (context {its_ref}), true residual {true_rel:.2e}, "
+              f"|x - x_ctx|/|x_ctx| {np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref):.2e}")
+        assert true_rel <= 1e-11
+        assert np.linalg.norm(xh - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
+        assert abs(its - its_ref) <= max(5, its_ref // 10)
+        if first is None:
+            first = (its, xh.copy())
+        else:                        # the workspace-free solve itself is deterministic
+            assert its == first[0] and np.array_equal(xh, first[1])
     ctx.close()
 
 
