@@ -144,7 +144,10 @@ class Clocks:
 # DRAM bytes per 2x2 block of the FP64 plane SpMV (k_spmv<2, 2, double>) from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 187.2 MB for 4 715 521 blocks, P2 column at
 # 320x320 cells; profiles/k_spmv_fp64_p2_plane_dp_n320.md); traffic scales with the blocks.
+# The kernel has since taken its rows in a length-grouped order (a different x-gather order), so
+# the figure no longer describes it and the bench reports no traffic until the next capture.
 SPMV64_2D_DRAM_BYTES_PER_BLOCK = 187.235072e6 / 4715521
+SPMV_COUNTERS_CURRENT = False
 
 
 def _spmv_bytes(info, dim, vb=8):
@@ -601,7 +604,8 @@ def main():
         by = _spmv_bytes(info, dim, 4 if f32 else 8)
         gbs = by / dur / 1e9
         fl = 2.0 * info.nnz_blocks * dim * dim / dur / 1e12
-        traffic = SPMV64_2D_DRAM_BYTES_PER_BLOCK * info.nnz_blocks if (dim == 2 and not f32) else None
+        traffic = (SPMV64_2D_DRAM_BYTES_PER_BLOCK * info.nnz_blocks
+                   if (dim == 2 and not f32 and SPMV_COUNTERS_CURRENT) else None)
         roof_spmv = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": f"k_spmv (masked block-CSR, {'FP32' if f32 else 'FP64'})", "launches": n_spmv,
