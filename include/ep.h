@@ -358,7 +358,10 @@ ep_status ep_linear_solve_noalloc(int32_t dim, int64_t n_nodes, const int32_t* r
 #define EP_WS_WIDTH 128
 #define EP_WS_N_OUT 4
 #define EP_WS_N_PARAMS 19204
-/* A network on `device`, parameters copied from host `params`; kernels run on cuda_stream. */
+/* A network on `device`, parameters copied from host `params`; kernels run on cuda_stream.
+ * Several contexts may read one network at once (forward passes); training it while a context
+ * solves with it is the caller's race to avoid (a context waits for the network's stream before
+ * each forward pass, so a training step enqueued earlier is complete by then). */
 ep_status ep_mlp_create(void** out, const float* params, int32_t device, void* cuda_stream);
 ep_status ep_mlp_destroy(void* mlp);
 /* Current FP32 master parameters into host dst [EP_WS_N_PARAMS]. */

@@ -113,3 +113,11 @@ def test_warm_start_sizes_match_the_oracle():
                       ("EP_WS_N_PARAMS", W.N_PARAMS)):
         assert re.search(rf"#define {name} {val}\b", text), name
         assert getattr(ep, name) == val
+
+
+def test_network_binding_checks_the_parameter_count(libpath):
+    """The binding rejects a parameter vector of the wrong length before calling the library."""
+    import numpy as np
+    import paper_1805_04155_gb300.ep as ep
+    with pytest.raises(ValueError):
+        ep.MLP(np.zeros(ep.EP_WS_N_PARAMS - 1, dtype=np.float32))
