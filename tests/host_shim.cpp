@@ -34,3 +34,70 @@ int shim_reference_tables(int family, int dim, double* dhat, int64_t cap_dhat, d
 }
 
 }  // extern "C"
+
+// -- AMG host setup -------------------------------------------------------------------------------
+#include "../paper_1805_04155_gb300/csrc/amg.h"
+
+extern "C" {
+
+// Runs the smoothed-aggregation setup; returns a heap hierarchy (free with shim_amg_free) or null.
+void* shim_amg_setup(int dim, int64_t n_nodes, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                     const uint8_t* free_dof, const double* coords) {
+    ep::AmgInput in{dim, n_nodes, row_ptr, col_idx, vals, free_dof, coords};
+    auto* H = new ep::AmgHierarchy();
+    std::string err;
+    if (!ep::amg_setup_host(in, *H, err)) {
+        delete H;
+        return nullptr;
+    }
+    return H;
+}
+
+void shim_amg_free(void* h) { delete static_cast<ep::AmgHierarchy*>(h); }
+
+int shim_amg_levels(void* h) { return (int)static_cast<ep::AmgHierarchy*>(h)->levels.size(); }
+
+// bs, n, lambda of level l
+void shim_amg_level(void* h, int l, int* bs, int64_t* n, double* lambda) {
+    const ep::AmgLevel& L = static_cast<ep::AmgHierarchy*>(h)->levels[l];
+    *bs = L.bs;
+    *n = L.n;
+    *lambda = L.lambda;
+}
+
+static const ep::HostBsr& pick(void* h, int l, int which) {
+    const ep::AmgLevel& L = static_cast<ep::AmgHierarchy*>(h)->levels[l];
+    return which == 0 ? L.A : (which == 1 ? L.P : L.R);
+}
+
+// shape of matrix `which` (0 A, 1 P, 2 R) of level l: block rows, block columns, block shape, blocks
+void shim_amg_mat_shape(void* h, int l, int which, int64_t* n_rows, int64_t* n_cols, int* rb, int* cb, int64_t* nnzb) {
+    const ep::HostBsr& M = pick(h, l, which);
+    *n_rows = M.n_rows;
+    *n_cols = M.n_cols;
+    *rb = M.rb;
+    *cb = M.cb;
+    *nnzb = M.row_ptr.empty() ? 0 : M.row_ptr.back();
+}
+
+void shim_amg_mat_copy(void* h, int l, int which, int32_t* row_ptr, int32_t* col_idx, double* vals) {
+    const ep::HostBsr& M = pick(h, l, which);
+    std::copy(M.row_ptr.begin(), M.row_ptr.end(), row_ptr);
+    std::copy(M.col_idx.begin(), M.col_idx.end(), col_idx);
+    std::copy(M.vals.begin(), M.vals.end(), vals);
+}
+
+// sizes of the block-diagonal inverses and of the coarsest dense inverse of level l
+void shim_amg_inv_sizes(void* h, int l, int64_t* n_dinv, int64_t* n_dense) {
+    const ep::AmgLevel& L = static_cast<ep::AmgHierarchy*>(h)->levels[l];
+    *n_dinv = (int64_t)L.dinv.size();
+    *n_dense = (int64_t)L.dense_inv.size();
+}
+
+void shim_amg_inv_copy(void* h, int l, double* dinv, double* dense) {
+    const ep::AmgLevel& L = static_cast<ep::AmgHierarchy*>(h)->levels[l];
+    std::copy(L.dinv.begin(), L.dinv.end(), dinv);
+    std::copy(L.dense_inv.begin(), L.dense_inv.end(), dense);
+}
+
+}  // extern "C"

@@ -27,15 +27,27 @@ def shim(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     out = str(tmp_path_factory.mktemp("shim") / "libhostshim.so")
-    cmd = [nvcc, "-std=c++17", "-O1", "-Xcompiler", "-fPIC", "-shared", "-x", "c++",
+    cmd = [nvcc, "-std=c++17", "-O1", "-Xcompiler", "-fPIC,-fopenmp", "-shared", "-x", "c++",
            os.path.join(ROOT, "tests", "host_shim.cpp"), os.path.join(SRC, "pattern_host.cpp"),
-           os.path.join(SRC, "elements_host.cpp"), "-I", os.path.join(ROOT, "include"), "-o", out]
+           os.path.join(SRC, "elements_host.cpp"), os.path.join(SRC, "amg_host.cpp"), "-I", os.path.join(ROOT, "include"),
+           "-o", out]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     lib = C.CDLL(out)
     lib.shim_build_pattern.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_void_p, C.POINTER(C.c_int64)]
     lib.shim_reference_tables.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
+    lib.shim_amg_setup.argtypes = [C.c_int, C.c_int64] + [C.c_void_p] * 5
+    lib.shim_amg_setup.restype = C.c_void_p
+    lib.shim_amg_free.argtypes = [C.c_void_p]
+    lib.shim_amg_levels.argtypes = [C.c_void_p]
+    lib.shim_amg_level.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double)]
+    lib.shim_amg_mat_shape.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]
+    lib.shim_amg_mat_copy.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.shim_amg_inv_sizes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.shim_amg_inv_copy.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
     return lib
 
 
@@ -94,3 +106,94 @@ def test_reference_tables_match_the_oracle_elements(shim, elem_type, dim):
     want = np.transpose(D, (2, 1, 0)).ravel()        # [n_q][n_p][dim]
     assert np.abs(wq - w).max() <= 1e-15 * np.abs(w).max()
     assert np.abs(dhat - want).max() <= 1e-14 * max(1.0, np.abs(want).max())
+
+
+def _amg_mat(shim, h, level, which):
+    import scipy.sparse as sp
+    nr, nc, rb, cb, nnzb = C.c_int64(), C.c_int64(), C.c_int(), C.c_int(), C.c_int64()
+    shim.shim_amg_mat_shape(h, level, which, C.byref(nr), C.byref(nc), C.byref(rb), C.byref(cb), C.byref(nnzb))
+    rp = np.zeros(nr.value + 1, dtype=np.int32)
+    ci = np.zeros(nnzb.value, dtype=np.int32)
+    v = np.zeros(nnzb.value * rb.value * cb.value)
+    shim.shim_amg_mat_copy(h, level, which, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    return sp.bsr_matrix((v.reshape(-1, rb.value, cb.value), ci, rp),
+                         shape=(nr.value * rb.value, nc.value * cb.value)).tocsr()
+
+
+@pytest.mark.parametrize("make", ["p2_column", "q1_cube"])
+def test_amg_setup_galerkin_hierarchy(shim, make):
+    """Smoothed-aggregation setup on K_elast (from the oracle): every coarse operator is the Galerkin
+    product R A P with R = P^T (coarse DOFs whose near-null column was dropped get an identity row),
+    the stored block-diagonal inverses invert the diagonal blocks, the coarsest dense inverse inverts
+    the coarsest operator, and the spectral bound lies near the largest eigenvalue of D^-1 A."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle import constitutive as OC
+    from oracle.fem import Assembler, Geometry
+    from synthetic import p2_plane_dp, q1_cube_vm
+    prob = p2_plane_dp(n=32, n_steps=2) if make == "p2_column" else q1_cube_vm(n=12, n_steps=2)
+    m = prob.mesh
+    d = m.dim
+    g = Geometry(m.coords, m.elem, m.elem_type, d)
+    K_b, G_b = OC.moduli(prob.material.E, prob.material.nu)
+    Ce = OC.elastic_tangent(K_b, G_b)
+    if d == 2:
+        Ce = Ce[np.ix_(OC.PLANE_INPLANE_IDX, OC.PLANE_INPLANE_IDX)]
+    Kel = Assembler(g, Ce).K_elast.tocsr()
+    st, rp, ci, _ = _pattern(shim, m.n_nodes, m.elem)
+    assert st == 1
+    vals = np.zeros((len(ci), d, d))
+    for n in range(m.n_nodes):
+        for k in range(rp[n], rp[n + 1]):
+            vals[k] = Kel[n * d:(n + 1) * d, ci[k] * d:(ci[k] + 1) * d].toarray()
+    free = (prob.dirichlet == 0).astype(np.uint8)
+    coords = np.ascontiguousarray(m.coords, dtype=np.float64)
+    h = shim.shim_amg_setup(d, m.n_nodes, rp.ctypes.data, ci.ctypes.data, vals.ctypes.data, free.ctypes.data,
+                            coords.ctypes.data)
+    assert h
+    try:
+        nl = shim.shim_amg_levels(h)
+        assert nl >= 2
+        fr = free.astype(bool)
+        A = Kel.multiply(np.outer(fr, fr)).tocsr() + sp.diags((~fr).astype(float))
+        sizes = []
+        for l in range(nl):
+            bs, n, lam = C.c_int(), C.c_int64(), C.c_double()
+            shim.shim_amg_level(h, l, C.byref(bs), C.byref(n), C.byref(lam))
+            sizes.append(n.value)
+            assert A.shape == (n.value, n.value)
+            nd, nden = C.c_int64(), C.c_int64()
+            shim.shim_amg_inv_sizes(h, l, C.byref(nd), C.byref(nden))
+            dinv = np.zeros(max(1, nd.value))
+            dense = np.zeros(max(1, nden.value))
+            shim.shim_amg_inv_copy(h, l, dinv.ctypes.data, dense.ctypes.data)
+            if l == nl - 1:                               # coarsest: dense inverse
+                Ad = A.toarray()
+                assert np.abs(dense.reshape(n.value, n.value) @ Ad - np.eye(n.value)).max() < 1e-8
+                break
+            b = bs.value
+            Dinv = dinv.reshape(-1, b, b)
+            for I in range(0, n.value // b, max(1, n.value // b // 50)):
+                blk = A[I * b:(I + 1) * b, I * b:(I + 1) * b].toarray()
+                assert np.abs(Dinv[I] @ blk - np.eye(b)).max() < 1e-10
+            nb = n.value // b
+            DA = sp.bsr_matrix((Dinv, np.arange(nb), np.arange(nb + 1)), shape=(n.value, n.value)).tocsr() @ A
+            rho = abs(spla.eigs(DA, k=1, which="LM", return_eigenvectors=False)[0])
+            assert 0.8 * rho <= lam.value <= 1.3 * rho, (l, lam.value, rho)
+            P = _amg_mat(shim, h, l, 1)
+            R = _amg_mat(shim, h, l, 2)
+            assert abs(R - P.T).max() == 0.0
+            G = (P.T @ A @ P).tocsr()
+            Anext = _amg_mat(shim, h, l + 1, 0)
+            ident = np.nonzero(G.diagonal() == 0.0)[0]
+            Gf = G.tolil()
+            for i in ident:
+                Gf[i, :] = 0.0
+                Gf[i, i] = 1.0
+            err = abs(Anext - Gf.tocsr()).max() / abs(Anext).max()
+            assert err < 1e-12, (l, err)
+            A = Anext
+        print(f"\n{make}: levels {sizes}")
+        assert all(a > b for a, b in zip(sizes, sizes[1:])) and sizes[-1] <= 600
+    finally:
+        shim.shim_amg_free(h)
