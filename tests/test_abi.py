@@ -121,3 +121,13 @@ def test_network_binding_checks_the_parameter_count(libpath):
     import paper_1805_04155_gb300.ep as ep
     with pytest.raises(ValueError):
         ep.MLP(np.zeros(ep.EP_WS_N_PARAMS - 1, dtype=np.float32))
+
+
+def test_constitutive_with_no_points_returns_ok_without_gpu_work(libpath):
+    """n = 0 is a valid empty call: it returns before touching any pointer or the device."""
+    import paper_1805_04155_gb300.ep as ep
+    lib = ep.lib()
+    mat = ep.ep_material(1, 206900.0, 0.29, 367.4, 1e4, 0, 0, 0, 0)
+    args = [None] * 8
+    assert lib.ep_constitutive(ctypes.byref(mat), 2, 0, *args, None) == ep.EP_OK
+    assert lib.ep_constitutive(ctypes.byref(mat), 4, 0, *args, None) == ep.EP_ERR_INVALID_ARG   # dim
