@@ -30,7 +30,7 @@ def test_replica_timing_is_the_slowest_rank_and_value_counts_all_ranks():
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()     # no fork of this (threaded) test process
     out = mgr.dict()
     mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
     assert out[0][0] == out[1][0] == 150.0
