@@ -260,3 +260,19 @@ def test_oracle_l_shape_cycle_dissipates():
         work.append(float(p.f_unit @ s.u))
     assert np.abs(s.ep).max() > 0
     assert abs(work[-1]) > 1e-3 * max(abs(w) for w in work)
+
+
+def test_oracle_newton_start_across_load_reversals():
+    """Reading R24 of ALG-NEWTON's start: the extrapolation is used only while the load keeps its
+    direction.  With the negative ratio at the second reversal of the 16-step cyclic L-shape (zeta
+    -1 -> -0.75) the extrapolation predicts the loading branch, not the elastic unloading, and Newton
+    did not converge in 50 iterations; with the reading every step converges."""
+    from synthetic import l_shape_vm
+    p = l_shape_vm("Q2", m=3, n_steps=16)
+    s = OracleSolver(p)
+    reps = s.solve_path(tol=1e-13)
+    assert all(r.converged for r in reps)
+    rev = [k for k in range(2, len(p.zeta)) if (p.zeta[k] - p.zeta[k - 1]) * (p.zeta[k - 1] - p.zeta[k - 2]) < 0]
+    assert len(rev) == 2
+    # after the first reversal two elastic unloading steps make the extrapolation exact: 0 iterations
+    assert p.zeta[5] == 0.5 and reps[5].newton_its == 0
