@@ -353,6 +353,13 @@ ep_status ep_linear_solve_noalloc(int32_t dim, int64_t n_nodes, const int32_t* r
  *     (1/n) sum [ sum_{c<3} (y_c - t_c)^2 + 0.1 * (max(y_3,0) - y_3 t_3 + log(1 + exp(-|y_3|))) ];
  * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on FP32 master
  * parameters, the bfloat16 copy refreshed after every step.
+ *
+ * Errors: EP_ERR_INVALID_ARG for a null handle or array, n_rows < 0 (forward;
+ * 0 is an empty call) or <= 0 (grad, train), lr <= 0, and warm_start = 2
+ * without an attached network; EP_ERR_OOM / EP_ERR_CUDA for device failures
+ * (ep_mlp_create's message in ep_last_error(NULL)).  The network's buffers
+ * (parameters, Adam moments, per-CTA gradient partials) are owned by its
+ * handle; the context's recording buffers by the context.
  */
 #define EP_WS_N_IN 16
 #define EP_WS_WIDTH 128
@@ -388,7 +395,8 @@ ep_status ep_ws_attach(void* ctx, void* mlp);
 /* Human-readable name of a status code. */
 const char* ep_status_str(int32_t status);
 /* Message of the last failure of `ctx`; with ctx == NULL, the message of the
- * last failed ep_create or ep_linear_solve_noalloc on the calling thread. */
+ * last failed ep_create, ep_create_batch, ep_mlp_create or ep_linear_solve_noalloc
+ * on the calling thread. */
 const char* ep_last_error(const void* ctx);
 
 #ifdef __cplusplus
