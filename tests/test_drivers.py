@@ -1,4 +1,7 @@
-"""Host logic of the load-stepping drivers (no GPU): the schedule candidates of the autotuner."""
+"""Host logic of the load-stepping drivers (no GPU): the schedule candidates of the autotuner, the
+adaptive displacement path of the strip footing (on a stand-in context), the external work."""
+import numpy as np
+
 from paper_1805_04155_gb300 import drivers as D
 from paper_1805_04155_gb300 import ep
 
@@ -13,3 +16,62 @@ def test_schedule_candidates_cover_precisions_methods_and_preconditioners():
         assert {c["precond"] for c in cs} == {1, 2}
         assert len({tuple(sorted(c.items())) for c in cs}) == len(cs)
     assert all(c["newton_rtol"] == 1e-10 for c in sym)
+
+
+class _FakeFooting:
+    """A context stand-in whose footing pressure follows p(u) = min(k u, p_lim) (rigid-plastic limit),
+    and whose solve fails for increments above `du_fail` (a Newton failure on a too-large step)."""
+
+    def __init__(self, k=100.0, p_lim=5.0, du_fail=0.05, n_nodes=4, dim=2):
+        self.k, self.p_lim, self.du_fail = k, p_lim, du_fail
+        self.u = 0.0
+        self.dim = dim
+        self.n_nodes = n_nodes
+        self.calls = []
+        self.h = None
+
+    def solve_load_path(self, zeta, opts, raise_on_error=True):
+        z = float(zeta[-1])
+        self.calls.append(z - self.u)
+        if z - self.u > self.du_fail:
+            return ep.EP_ERR_NEWTON_NO_CONVERGENCE, []
+        self.u = z
+        return ep.EP_OK, [object()]
+
+    def get(self, field):
+        assert field == ep.EP_F_INT
+        F = np.zeros((self.n_nodes, self.dim))
+        p = min(self.k * self.u, self.p_lim)
+        F[:2, self.dim - 1] = -p * 1.0 / 2      # two footing nodes share the load of a unit-width footing
+        return F.ravel()
+
+
+class _Problem:
+    extra = {"footing_nodes": np.array([0, 1]), "footing": 1.0}
+
+
+def test_strip_footing_path_doubles_on_the_plateau_and_halves_on_failure(monkeypatch):
+    import numpy as np_
+    ctx = _FakeFooting()
+    monkeypatch.setattr(ep, "default_opts", lambda **kw: None)
+    us, ps, _ = D.strip_footing_path(ctx, _Problem(), u_max=0.3, du0=0.01, soft=0.1)
+    steps = np_.diff(np_.concatenate([[0.0], us]))
+    assert abs(us[-1] - 0.3) < 1e-12
+    assert np_.all(np_.diff(ps) >= -1e-12) and abs(ps[-1] - 5.0) < 1e-12
+    assert steps[0] == 0.01
+    # elastic (slope k) until p_lim at u = 0.05: the increment stays 0.01; on the plateau it doubles
+    assert np_.allclose(steps[:5], 0.01)
+    assert steps.max() <= ctx.du_fail + 1e-12      # larger increments failed and were halved
+    assert any(c > ctx.du_fail for c in ctx.calls)  # a failure happened and was recovered
+    assert len(us) < 0.3 / 0.01                     # fewer steps than a uniform path
+
+
+def test_external_work_is_the_load_times_displacement():
+    class P:
+        f_unit = np.array([1.0, -2.0, 0.5])
+
+    class Ctx:
+        def get(self, field):
+            assert field == ep.EP_U
+            return np.array([2.0, 1.0, 4.0])
+    assert D.external_work(Ctx(), P()) == 2.0
