@@ -1,6 +1,7 @@
 """Host logic of the load-stepping drivers (no GPU): the schedule candidates of the autotuner, the
 adaptive displacement path of the strip footing (on a stand-in context), the external work."""
 import numpy as np
+import pytest
 
 from paper_1805_04155_gb300 import drivers as D
 from paper_1805_04155_gb300 import ep
@@ -75,3 +76,63 @@ def test_external_work_is_the_load_times_displacement():
             assert field == ep.EP_U
             return np.array([2.0, 1.0, 4.0])
     assert D.external_work(Ctx(), P()) == 2.0
+
+
+class _FakeTuneCtx:
+    """Stand-in context for the autotuner: each schedule takes a set time per step (or fails), and the
+    state fields are plain arrays that a solve overwrites."""
+
+    class _Mat:
+        model, phi, psi, Hc = ep.EP_VM_ISO, 0.0, 0.0, 0.0
+
+    def __init__(self, times):
+        self.times = times                  # (precision, krylov, precond) -> ms per step, or None (fails)
+        self.material = self._Mat()
+        self.state = {f: np.zeros(3) for f in D.STATE_FIELDS}
+        self.trials = []
+
+    def get(self, field):
+        return self.state[field]
+
+    def set(self, field, value):
+        self.state[field] = np.array(value, copy=True)
+
+    def solve_load_path(self, zeta, opts, raise_on_error=True):
+        key = (opts.precision, opts.krylov, opts.precond)
+        # every trial must start from the saved (zero) state
+        self.trials.append((key, all(np.all(v == 0.0) for v in self.state.values())))
+        for f in self.state:
+            self.state[f] = self.state[f] + 1.0
+        t = self.times.get(key)
+        if t is None:
+            return ep.EP_ERR_KRYLOV, []
+
+        class R:
+            t_step_ms = t
+        return ep.EP_OK, [R() for _ in zeta]
+
+
+@pytest.fixture(scope="module")
+def built():
+    """ep.default_opts and the error messages come from the library (host calls only)."""
+    from paper_1805_04155_gb300 import build as b
+    b.build()
+
+
+def test_autotune_picks_the_fastest_schedule_and_restores_the_state(built):
+    times = {(ep.EP_FP64, 1, 2): 3.0, (ep.EP_FP64, 1, 1): 5.0, (ep.EP_FP64, 3, 2): 2.5, (ep.EP_FP64, 3, 1): None,
+             (ep.EP_MIXED, 1, 2): 2.0, (ep.EP_MIXED, 1, 1): None, (ep.EP_MIXED, 3, 2): 4.0, (ep.EP_MIXED, 3, 1): 9.0}
+    ctx = _FakeTuneCtx(times)
+    best, table = D.autotune(ctx, [0.1, 0.2, 0.3, 0.4], trial_steps=3)
+    assert (best.precision, best.krylov, best.precond) == (ep.EP_MIXED, 1, 2)
+    assert len(table) == 8 and sum(t is None for _, t in table) == 2
+    assert all(fresh for _, fresh in ctx.trials)                 # each trial started from the saved state
+    assert all(np.all(v == 0.0) for v in ctx.state.values())     # and the state is restored at the end
+    assert dict(((c["precision"], c["krylov"], c["precond"]), t) for c, t in table)[(ep.EP_FP64, 3, 2)] == \
+        3 * 2.5 / 1e3
+
+
+def test_autotune_reports_when_every_schedule_fails(built):
+    ctx = _FakeTuneCtx({})
+    with pytest.raises(ep.EPError):
+        D.autotune(ctx, [0.1], trial_steps=1)
