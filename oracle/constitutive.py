@@ -10,20 +10,23 @@ the stress S [6][n], the tangent DS [6][6][n] (row = stress component, column =
 strain component), the plastic flag, and the trial internal variables that
 become the new state once the step has converged.
 
-Models:
+Models (written per point in tensor notation from the closed forms of
+Section 2; Voigt arrays are converted at entry and exit):
   * von Mises, linear kinematic hardening (Section 2.2, eqs. (T_kinematic),
     (DT_kinematic), (T_other)); a = 0 gives perfect plasticity.
   * von Mises, linear isotropic hardening: yield |s| <= Y + H*alpha with
-    alpha incremented by the plastic multiplier; the same radial return with
-    a scalar internal variable (extension; reduces to the kinematic formulas
-    on a virgin state with H = a).
+    alpha incremented by the plastic multiplier (extension; the consistency
+    condition and its derivative are worked out in vm_isotropic's docstring;
+    on a virgin state with H = a it gives the kinematic result).
   * Drucker-Prager (Section 2.3): elastic / smooth / apex cases, here with a
     plastic potential of slope eta_bar (nonassociated when eta_bar != eta)
     and linear cohesion hardening c + Hc*alpha (extension; eta_bar = eta and
     Hc = 0 give the paper's perfect-plastic formulas).  p_tr is the mean
     trial stress K tr(e_tr): the trace I:sigma in Section 2.3's notation list
-    is read as I:sigma/3, which is what the yield function and Section 7.2's
-    listing use.  Apex when CRIT2 > 0, plastic when CRIT1 > 0 (Section 7.2).
+    is read as I:sigma/3, which is what the yield function uses.  A point is
+    plastic when the trial yield function is > 0 and returns to the apex when
+    eta p_tr - c_k - (K eta eta_bar + Hc)|s_tr|/(sqrt(2) G) > 0 (strict, as in
+    Section 7.2; the text of Section 2.3 puts the tie on the apex side).
 """
 from __future__ import annotations
 
@@ -71,73 +74,142 @@ def _tile(M, n):
     return np.repeat(M[:, :, None], n, axis=2)
 
 
+# ----------------------------------------------------------------------------
+# Tensor form.  The return mappings below work on symmetric 3x3 tensors
+# (arrays [n,3,3]) and fourth-order operators (arrays [n,3,3,3,3]) exactly as
+# Section 2 writes them; Voigt vectors enter and leave only at the interface.
+# ----------------------------------------------------------------------------
+
+_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2))   # Voigt index -> tensor index
+_I2 = np.eye(3)
+_II = np.einsum("ij,kl->ijkl", _I2, _I2)                                   # I (x) I
+_I4 = 0.5 * (np.einsum("ik,jl->ijkl", _I2, _I2) + np.einsum("il,jk->ijkl", _I2, _I2))
+_P_DEV = _I4 - _II / 3.0                                                    # I_D on symmetric tensors
+
+
+def _to_tensor(v, strain_type: bool):
+    """Voigt [6][n] -> symmetric tensors [n,3,3]; strain-type shears are halved."""
+    t = np.empty((v.shape[1], 3, 3))
+    for a, (i, j) in enumerate(_PAIRS):
+        x = v[a] * 0.5 if (strain_type and i != j) else v[a]
+        t[:, i, j] = x
+        t[:, j, i] = x
+    return t
+
+
+def _to_voigt(t, strain_type: bool):
+    """Symmetric tensors [n,3,3] -> Voigt [6][n]; strain-type shears are doubled."""
+    return np.stack([t[:, i, j] * (2.0 if (strain_type and i != j) else 1.0) for i, j in _PAIRS])
+
+
+def _to_voigt_operator(T):
+    """Fourth-order operators [n,3,3,3,3] with minor symmetries -> [6][6][n].
+
+    Row I = stress component (i,j), column J = engineering strain component
+    (k,l): since 2 eps_kl = eps_kl + eps_lk, the entry is T_ijkl itself.
+    """
+    return np.stack([np.stack([T[:, i, j, k, l] for (k, l) in _PAIRS]) for (i, j) in _PAIRS])
+
+
+def _trace(t):
+    return np.einsum("nii->n", t)
+
+
+def _dev(t):
+    return t - (_trace(t) / 3.0)[:, None, None] * _I2
+
+
+def _norm(t):
+    """Frobenius norm |t| = sqrt(t:t) (Section 2's |.|)."""
+    return np.sqrt(np.einsum("nij,nij->n", t, t))
+
+
+def _outer(a, b):
+    return np.einsum("nij,nkl->nijkl", a, b)
+
+
+def _hooke(K, G, eps):
+    """C eps = K tr(eps) I + 2G I_D eps (Section 2, eq. (elastic_law))."""
+    return (K * _trace(eps))[:, None, None] * _I2 + 2.0 * G * _dev(eps)
+
+
+def _hooke_operator(K, G, n):
+    return np.broadcast_to(K * _II + 2.0 * G * _P_DEV, (n, 3, 3, 3, 3)).copy()
+
+
 def vm_kinematic(E, Ep_prev, Hard_prev, K, G, a, Y):
-    """Von Mises with linear kinematic hardening (Sections 2.2 and 7.1).
+    """Von Mises with linear kinematic hardening: eqs. (T_kinematic), (DT_kinematic), (T_other).
 
     E, Ep_prev: strain-type [6][n]; Hard_prev: back stress beta (stress-type) [6][n].
-    Returns S, DS, plastic, Ep_new, Hard_new, lam.
+    Returns S, DS, plastic, Ep_new, Hard_new, lam, where lam = (|s_tr| - Y)/(2G + a)
+    is the coefficient the updates of Section 2.2 share.
     """
     n = E.shape[1]
-    E_tr = E - Ep_prev
-    S_tr = 2.0 * G * (DEV @ E_tr) + K * (VOL @ E_tr)
-    SD_tr = DEV @ (2.0 * G * E_tr) - Hard_prev
-    norm_SD = np.sqrt(np.sum(SD_tr[:3] ** 2, axis=0) + 2.0 * np.sum(SD_tr[3:] ** 2, axis=0))
-    CRIT = norm_SD - Y
-    plastic = CRIT > 0
-    S = S_tr.copy()
-    DS = _tile(elastic_tangent(K, G), n)
-    Ep_new, Hard_new = Ep_prev.copy(), Hard_prev.copy()
+    sigma_tr = _hooke(K, G, _to_tensor(E - Ep_prev, True))
+    beta = _to_tensor(Hard_prev, False)
+    s_tr = _dev(sigma_tr) - beta                       # trial relative deviator
+    size = _norm(s_tr)
+    plastic = size > Y                                  # second branch of (T_kinematic)
+    sigma, D = sigma_tr.copy(), _hooke_operator(K, G, n)
+    ep_t, beta_new = _to_tensor(Ep_prev, True), beta.copy()
     lam = np.zeros(n)
     if plastic.any():
-        ip = plastic
-        Nhat = SD_tr[:, ip] / norm_SD[ip]
-        denom = 2.0 * G + a
-        lam[ip] = CRIT[ip] / denom
-        S[:, ip] -= 2.0 * G * lam[ip] * Nhat
-        const = (2.0 * G) ** 2 / denom
-        NN = np.einsum("iq,jq->ijq", Nhat, Nhat)
-        ID = _tile(DEV, int(ip.sum()))
-        DS[:, :, ip] += -const * ID + (const * Y / norm_SD[ip]) * (ID - NN)
-        Hard_new[:, ip] += a * lam[ip] * Nhat
-        Ep_new[:, ip] += lam[ip] * Nhat * SHEAR2[:, None]
-    return S, DS, plastic, Ep_new, Hard_new, lam
+        p = plastic
+        nrm = s_tr[p] / size[p, None, None]             # n_k^tr
+        lam[p] = (size[p] - Y) / (2.0 * G + a)
+        sigma[p] -= (2.0 * G * lam[p])[:, None, None] * nrm
+        k = 4.0 * G * G / (2.0 * G + a)
+        # (DT_kinematic): C - k I_D + k (Y/|s_tr|) (I_D - n (x) n)
+        D[p] += -k * _P_DEV + (k * Y / size[p])[:, None, None, None, None] * (_P_DEV - _outer(nrm, nrm))
+        beta_new[p] += (a * lam[p])[:, None, None] * nrm
+        ep_t[p] += lam[p][:, None, None] * nrm
+    return (_to_voigt(sigma, False), _to_voigt_operator(D), plastic,
+            _to_voigt(ep_t, True), _to_voigt(beta_new, False), lam)
 
 
 def vm_isotropic(E, Ep_prev, alpha_prev, K, G, H, Y):
-    """Von Mises with linear isotropic hardening, yield |s| <= Y + H alpha.
+    """Von Mises with linear isotropic hardening, yield |s| <= Y + H alpha (extension).
 
-    Radial return: lam = (|s_tr| - Y - H alpha_prev)/(2G + H), S = S_tr - 2G lam n,
-    DS = C - 4G^2/(2G+H) n(x)n - 4G^2 lam/|s_tr| (DEV - n(x)n), alpha += lam,
-    Ep += lam n.  Returns S, DS, plastic, Ep_new, alpha_new, lam.
+    The plastic multiplier lam solves the consistency condition
+    |s_tr| - 2G lam - (Y + H (alpha_prev + lam)) = 0; the stress returns along
+    the trial normal n; differentiating sigma = sigma_tr - 2G lam n with
+    dn/deps = 2G/|s_tr| (I_D - n (x) n) gives
+    DS = C - 4G^2/(2G+H) n (x) n - 4G^2 lam/|s_tr| (I_D - n (x) n).
+    Returns S, DS, plastic, Ep_new, alpha_new, lam.
     """
     n = E.shape[1]
-    E_tr = E - Ep_prev
-    S_tr = 2.0 * G * (DEV @ E_tr) + K * (VOL @ E_tr)
-    SD_tr = DEV @ (2.0 * G * E_tr)
-    norm_SD = np.sqrt(np.sum(SD_tr[:3] ** 2, axis=0) + 2.0 * np.sum(SD_tr[3:] ** 2, axis=0))
-    CRIT = norm_SD - (Y + H * alpha_prev)
-    plastic = CRIT > 0
-    S = S_tr.copy()
-    DS = _tile(elastic_tangent(K, G), n)
-    Ep_new, alpha_new = Ep_prev.copy(), alpha_prev.copy()
+    sigma_tr = _hooke(K, G, _to_tensor(E - Ep_prev, True))
+    s_tr = _dev(sigma_tr)
+    size = _norm(s_tr)
+    radius = Y + H * alpha_prev
+    plastic = size > radius
+    sigma, D = sigma_tr.copy(), _hooke_operator(K, G, n)
+    ep_t, alpha_new = _to_tensor(Ep_prev, True), alpha_prev.copy()
     lam = np.zeros(n)
     if plastic.any():
-        ip = plastic
-        Nhat = SD_tr[:, ip] / norm_SD[ip]
-        denom = 2.0 * G + H
-        lam[ip] = CRIT[ip] / denom
-        S[:, ip] -= 2.0 * G * lam[ip] * Nhat
-        NN = np.einsum("iq,jq->ijq", Nhat, Nhat)
-        ID = _tile(DEV, int(ip.sum()))
-        DS[:, :, ip] += -((2.0 * G) ** 2 / denom) * NN - ((2.0 * G) ** 2 * lam[ip] / norm_SD[ip]) * (ID - NN)
-        alpha_new[ip] += lam[ip]
-        Ep_new[:, ip] += lam[ip] * Nhat * SHEAR2[:, None]
-    return S, DS, plastic, Ep_new, alpha_new, lam
+        p = plastic
+        nrm = s_tr[p] / size[p, None, None]
+        lam[p] = (size[p] - radius[p]) / (2.0 * G + H)
+        sigma[p] -= (2.0 * G * lam[p])[:, None, None] * nrm
+        nn = _outer(nrm, nrm)
+        D[p] -= (4.0 * G * G / (2.0 * G + H)) * nn
+        D[p] -= (4.0 * G * G * lam[p] / size[p])[:, None, None, None, None] * (_P_DEV - nn)
+        alpha_new[p] += lam[p]
+        ep_t[p] += lam[p][:, None, None] * nrm
+    return (_to_voigt(sigma, False), _to_voigt_operator(D), plastic,
+            _to_voigt(ep_t, True), alpha_new, lam)
 
 
 def drucker_prager(E, Ep_prev, alpha_prev, K, G, eta, c, eta_bar=None, Hc=0.0):
-    """Drucker-Prager return mapping (Sections 2.3 and 7.2), with the extension above.
+    """Drucker-Prager return mapping (Section 2.3), with the extension of the module header.
 
+    Yield function Psi(sigma, alpha) = |s|/sqrt(2) + eta p - (c + Hc alpha),
+    p = tr(sigma)/3; plastic potential |s|/sqrt(2) + eta_bar p, so the flow
+    direction in stress space is C(n/sqrt(2) + eta_bar/3 I) = sqrt(2) G n + K eta_bar I.
+    Smooth return: the multiplier solves Psi = 0 along that direction,
+    lam = Psi_tr/(G + K eta eta_bar + Hc).  It overshoots the apex (|s| would
+    change sign) exactly when eta p_tr - c_k - (K eta eta_bar + Hc)|s_tr|/(sqrt(2) G) > 0;
+    then the stress is hydrostatic, sigma = p I with eta p = c + Hc (alpha_prev + lam).
     Returns S, DS, plastic (0 elastic, 1 smooth, 2 apex as int8), Ep_new,
     alpha_new, lam, err (1 where the apex is reached but no admissible stress
     exists, i.e. K eta eta_bar + Hc = 0).
@@ -145,56 +217,52 @@ def drucker_prager(E, Ep_prev, alpha_prev, K, G, eta, c, eta_bar=None, Hc=0.0):
     if eta_bar is None:
         eta_bar = eta
     n = E.shape[1]
-    E_tr = E - Ep_prev
-    S_tr = 2.0 * G * (DEV @ E_tr) + K * (VOL @ E_tr)
-    dev_E = DEV @ E_tr
-    norm_E = np.sqrt(np.maximum(0.0, np.sum(E_tr * dev_E, axis=0)))
-    rho_tr = 2.0 * G * norm_E
-    p_tr = K * (IOTA @ E_tr)
+    eps_e = _to_tensor(E - Ep_prev, True)
+    sigma_tr = _hooke(K, G, eps_e)
+    s_tr = _dev(sigma_tr)
+    rho = _norm(s_tr)                                    # varrho_k^tr
+    p_tr = _trace(sigma_tr) / 3.0                        # mean stress (reading of I:sigma)
     c_k = c + Hc * alpha_prev
-    denom_a = K * eta * eta_bar + Hc
-    denom_s = G + denom_a
-    CRIT1 = rho_tr / math.sqrt(2.0) + eta * p_tr - c_k
-    CRIT2 = eta * p_tr - c_k - denom_a * rho_tr / (G * math.sqrt(2.0))
-    IND_s = (CRIT1 > 0) & (CRIT2 <= 0)
-    IND_a = (CRIT1 > 0) & (CRIT2 > 0)
-    S = S_tr.copy()
-    DS = _tile(elastic_tangent(K, G), n)
-    Ep_new, alpha_new = Ep_prev.copy(), alpha_prev.copy()
+    slope = K * eta * eta_bar + Hc                       # d(eta p - c_k)/d lam at the apex
+    psi_tr = rho / math.sqrt(2.0) + eta * p_tr - c_k
+    beyond_apex = eta * p_tr - c_k - slope * rho / (math.sqrt(2.0) * G) > 0
+    smooth = (psi_tr > 0) & ~beyond_apex
+    apex = (psi_tr > 0) & beyond_apex
+    sigma, D = sigma_tr.copy(), _hooke_operator(K, G, n)
+    ep_t, alpha_new = _to_tensor(Ep_prev, True), alpha_prev.copy()
     lam = np.zeros(n)
     err = np.zeros(n, dtype=np.int8)
     flag = np.zeros(n, dtype=np.int8)
-    flag[IND_s] = 1
-    flag[IND_a] = 2
-    if IND_s.any():
-        s = IND_s
-        ls = CRIT1[s] / denom_s
-        lam[s] = ls
-        N_hat = dev_E[:, s] / norm_E[s]
-        M_bar = math.sqrt(2.0) * G * N_hat + K * eta_bar * IOTA[:, None]
-        M = math.sqrt(2.0) * G * N_hat + K * eta * IOTA[:, None]
-        S[:, s] -= ls * M_bar
-        NN = np.einsum("iq,jq->ijq", N_hat, N_hat)
-        MM = np.einsum("iq,jq->ijq", M_bar, M)
-        ID = _tile(DEV, int(s.sum()))
-        DS[:, :, s] += -(2.0 * math.sqrt(2.0) * G * G * ls / rho_tr[s]) * (ID - NN) - MM / denom_s
-        Ep_new[:, s] += ls * (N_hat / math.sqrt(2.0) + (eta_bar / 3.0) * IOTA[:, None]) * SHEAR2[:, None]
-        alpha_new[s] += ls
-    if IND_a.any():
-        a = IND_a
-        if denom_a == 0.0:
-            err[a] = ERR_RETURN_MAP
-            S[:, a] = np.nan
-            DS[:, :, a] = np.nan
+    flag[smooth] = 1
+    flag[apex] = 2
+    if smooth.any():
+        q = smooth
+        nrm = s_tr[q] / rho[q, None, None]
+        lam[q] = psi_tr[q] / (G + slope)
+        flow = math.sqrt(2.0) * G * nrm + K * eta_bar * _I2       # stress-space flow direction
+        grad = math.sqrt(2.0) * G * nrm + K * eta * _I2           # d Psi_tr / d eps
+        sigma[q] -= lam[q][:, None, None] * flow
+        D[q] -= _outer(flow, grad) / (G + slope)
+        D[q] -= (2.0 * math.sqrt(2.0) * G * G * lam[q] / rho[q])[:, None, None, None, None] * (
+            _P_DEV - _outer(nrm, nrm))
+        ep_t[q] += lam[q][:, None, None] * (nrm / math.sqrt(2.0) + (eta_bar / 3.0) * _I2)
+        alpha_new[q] += lam[q]
+    if apex.any():
+        q = apex
+        if slope == 0.0:
+            err[q] = ERR_RETURN_MAP
+            sigma[q] = np.nan
+            D[q] = np.nan
         else:
-            la = (eta * p_tr[a] - c_k[a]) / denom_a
-            lam[a] = la
-            p = p_tr[a] - K * eta_bar * la
-            S[:, a] = IOTA[:, None] * p
-            DS[:, :, a] = (K * Hc / denom_a) * VOL[:, :, None]
-            Ep_new[:, a] = E[:, a] - IOTA[:, None] * (p / (3.0 * K))
-            alpha_new[a] += la
-    return S, DS, flag, Ep_new, alpha_new, lam, err
+            lam[q] = (eta * p_tr[q] - c_k[q]) / slope
+            p = p_tr[q] - K * eta_bar * lam[q]
+            sigma[q] = p[:, None, None] * _I2
+            D[q] = (K * Hc / slope) * _II
+            # all of the total strain beyond the hydrostatic elastic part is plastic
+            ep_t[q] = _to_tensor(E[:, q], True) - (p / (3.0 * K))[:, None, None] * _I2
+            alpha_new[q] += lam[q]
+    return (_to_voigt(sigma, False), _to_voigt_operator(D), flag,
+            _to_voigt(ep_t, True), alpha_new, lam, err)
 
 
 # ----------------------------------------------------------------------------

@@ -1,4 +1,4 @@
-"""Pins for the oracle's return mappings (Sections 2.2, 2.3, 7.1, 7.2 and the extensions).
+"""Pins for the oracle's return mappings (Sections 2.2, 2.3 and the extensions).
 
 Independent checks: tangents equal central differences of the stress map,
 yield-function invariants after the return, Hooke's law with the returned
