@@ -1,26 +1,33 @@
 """Benchmark: incremental elastoplastic load path on one GB300 through the C ABI.
 
-A step is one load step of the workload's load path: semismooth Newton to the
-relative residual tolerance (every iteration: fused return mapping + tangent
-assembly + internal forces, residual and norms, preconditioned Krylov solve,
-update) followed by the state commit.  Step j runs load step (j mod n_steps)
-of the path; the state is reset to virgin when the path wraps.  The default
-K = 40 times exactly one full 40-step load path.
+A step is one whole load path of the workload from the virgin state (ep_reset,
+then every load step: semismooth Newton to the relative residual tolerance --
+each iteration fused return mapping + tangent assembly + internal forces,
+residual and norms, preconditioned Krylov solve, update -- and the state
+commit).  The default workload is the P2 plane-strain Drucker-Prager column
+(256 x 256 cells, 917 504 points, 40 load steps to 0.98 of the limit
+traction), so every step crosses the elastic, the spreading-plastic and the
+nearly-singular fully plastic range.  W warm-up paths, then K timed paths in
+each precision, CUDA events around each path on the context's stream.
 
 value = integration points assembled per second over the timed region
-        (n_int x assemblies / elapsed), i.e. the rate at which the solver
-        drives every integration point through return mapping + tangent
-        assembly, Krylov and update included, for the primary precision.
-        Both precisions are timed on the same load steps from the virgin
-        state: fp64 and mixed (FP32 tangent and inner Krylov while they
-        contract well, FP64 return mapping, residual and update); with
-        --precision auto (default) the faster is the primary and the other
-        is reported under "compare" (value, load-path time, Newton and Krylov
-        iterations, and the difference of the final displacements).
-roofline: the dominant kernel of the step (measured with CUDA events around
-        every launch inside the timed region, on the context's stream).
-e2e:    the same metric through the C ABI with host buffers: each step
-        copies its load factor host->device and reads u_k back to the host.
+        (n_int x assemblies / elapsed): the rate at which the solver drives
+        every integration point through return mapping + tangent assembly,
+        Krylov and update included, for the primary precision.  Both
+        precisions are timed on the same path: fp64 and mixed (FP32 tangent
+        and inner Krylov while they contract well, FP64 return mapping,
+        residual and update); with --precision auto (default) the faster is
+        the primary and the other is reported under "compare".  load_path_s
+        is the median of the K measured path times.
+roofline: the kernel with the largest share of the step among the assembly,
+        the SpMV of the Krylov solves and the AMG level-0 Chebyshev step
+        (CUDA events around every assembly and SpMV launch and around a sample
+        of the smoothing sweeps, inside the timed region), algorithmic bytes
+        per launch over the average launch time; all three under
+        roofline_kernels.
+e2e:    the same metric through the C ABI with host buffers: each path takes
+        its load factors from the host and reads u and sigma back to host
+        buffers.
 
 --impl reference times the CPU oracle (numpy/scipy, FP64) on a reduced copy
 of the workload instead; it is a deliberately slow baseline, not the target.
@@ -141,15 +148,6 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# DRAM bytes per 2x2 block of the FP64 plane SpMV (k_spmv<2, 2, double>) from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum = 187.2 MB for 4 715 521 blocks, P2 column at
-# 320x320 cells; profiles/k_spmv_fp64_p2_plane_dp_n320.md); traffic scales with the blocks.
-# The kernel has since taken its rows in a length-grouped order (a different x-gather order), so
-# the figure no longer describes it and the bench reports no traffic until the next capture.
-SPMV64_2D_DRAM_BYTES_PER_BLOCK = 187.235072e6 / 4715521
-SPMV_COUNTERS_CURRENT = False
-
-
 def _spmv_bytes(info, dim, vb=8):
     """Algorithmic bytes of one masked block-CSR SpMV with vb-byte values and vectors: values +
     column indices + row pointers + x read once + y written once + free mask."""
@@ -158,13 +156,24 @@ def _spmv_bytes(info, dim, vb=8):
     return nnzb * (dim * dim * vb + 4) + (n_rows + 1) * 4 + n * vb * 2 + n
 
 
-def _assembly_bytes(info, dim, n_p, n_comp, kb=8):
-    """Algorithmic bytes of one fused assembly launch (split or full form) with kb-byte K values:
-    cached gradients and weights, connectivity, slot map, displacement gather, state read, F and K
-    block updates (K read and written once)."""
+def _cheb0_bytes(info, dim):
+    """Algorithmic bytes of one level-0 Chebyshev step of the AMG V-cycle (k_cheb, FP32): the
+    matrix (values, column indices, row pointers), its block-Jacobi inverse, the free mask, and the
+    vectors b, x_in, d read and d, x_out written once."""
+    nnzb, n_rows = info.nnz_blocks, info.n_nodes
+    n = n_rows * dim
+    return nnzb * (dim * dim * 4 + 4) + (n_rows + 1) * 4 + n_rows * dim * dim * 4 + n + 5 * 4 * n
+
+
+def _assembly_bytes(info, dim, n_p, n_comp, kb=8, pe=1.0):
+    """Algorithmic bytes of one fused assembly launch in the split form of eq. (K-split), with
+    kb-byte K values and a fraction pe of the elements plastic: cached gradients and weights,
+    connectivity, displacement gather, state read, F read and written once; for the plastic
+    elements the slot map and their share of the K blocks read and written once (the reset of those
+    blocks to K_elast is a separate launch).  pe = 1 gives the full form's bytes."""
     n_int, n_e = info.n_int, info.n_elem
-    return (n_int * (n_p * dim + 1) * 8 + n_e * n_p * 4 + n_e * n_p * n_p * 4 + n_e * n_p * dim * 8
-            + n_int * (n_comp + 1) * 8 + info.n_nodes * dim * 8 * 2 + info.nnz_blocks * dim * dim * kb * 2)
+    return (n_int * (n_p * dim + 1) * 8 + n_e * n_p * 4 + n_e * n_p * dim * 8 + n_int * (n_comp + 1) * 8
+            + info.n_nodes * dim * 8 * 2 + pe * (n_e * n_p * n_p * 4 + info.nnz_blocks * dim * dim * kb * 2))
 
 
 def _tangent_flops_per_point(dim, n_p, sym):
@@ -450,15 +459,13 @@ def run_mlp(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="p2_plane_dp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="cells per side (0: the workload's full size)")
-    ap.add_argument("--skip", type=int, default=0,
-                    help="run the first S load steps untimed before the timed region (bounded profiling)")
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"],
                     help="primary precision; auto: time both, report the faster as the primary")
     ap.add_argument("--no-compare", action="store_true", help="time the primary precision only (auto: mixed)")
@@ -491,155 +498,170 @@ def main():
     if args.workload == "mlp":
         run_mlp(args)
         return
+    run_path(args, ep, local, world, rank)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _roof_hbm(name, launches, total_ms, bytes_per_launch, peaks, peaks_kind, step_ms, **extra):
+    """Roofline entry of an HBM-bound kernel: algorithmic bytes per launch / average launch time."""
+    dur = total_ms / launches / 1e3
+    gbs = bytes_per_launch / dur / 1e9
+    out = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": name, "launches": launches,
+           "avg_us": dur * 1e6, "bytes_per_launch": bytes_per_launch,
+           "peak_source": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)", "share_of_step": total_ms / step_ms}
+    out.update(extra)
+    return out
+
+
+def run_path(args, ep, local, world, rank):
+    """The workload's whole load path from the virgin state, timed as one step (see the module
+    docstring); both precisions, the end-to-end arm, the roofline of the step's kernels."""
+    import torch
     prob = _workload(args.workload, n=args.n)
     stream = torch.cuda.current_stream()
     ctx = ep.Context.from_problem(prob, device=local, stream=stream)
     info = ctx.info
     n_path = len(prob.zeta)
+    zeta = np.ascontiguousarray(prob.zeta, dtype=np.float64)
     prec_of = {"mixed": ep.EP_MIXED, "fp64": ep.EP_FP64}
-    zeros = {f: np.zeros(*ctx.field_shape(f)) for f in (ep.EP_U, ep.EP_PLASTIC_STRAIN, ep.EP_HARDENING,
-                                                          ep.EP_STRESS, ep.EP_PLASTIC_FLAG)}
-
-    def reset():
-        for f, v in zeros.items():
-            ctx.set(f, v)
 
     def opts_for(prec):
         return ep.default_opts(newton_rtol=prob.newton_rtol, profile=1, precision=prec_of[prec])
 
-    def timed(prec, e2e: bool, steps: int, skip: int):
+    u_host = np.empty(ctx.n_dof)
+    s_host = np.empty(ctx.field_shape(ep.EP_STRESS)[0])
+
+    def path(opts, e2e):
+        ctx.reset()
+        reps = ctx.solve_load_path(zeta, opts)
+        if e2e:
+            ctx.get(ep.EP_U, out=u_host)
+            ctx.get(ep.EP_STRESS, out=s_host)
+        return reps
+
+    def timed(prec, e2e: bool, steps: int):
         opts = opts_for(prec)
         reps = []
-        u_host = np.empty(ctx.n_dof) if e2e else None
-        zbuf = np.empty(1)
-        for j in range(skip):
-            zbuf[0] = prob.zeta[j % n_path]
-            ctx.solve_load_path(zbuf, opts)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed")
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t_wall0 = time.perf_counter()
-        ev0.record(stream)
+        evs[0].record(stream)
         for j in range(steps):
-            if j > 0 and (j + skip) % n_path == 0:
-                reset()
-            zbuf[0] = prob.zeta[(j + skip) % n_path]
-            reps.extend(ctx.solve_load_path(zbuf, opts))
-            if e2e:
-                ctx.get(ep.EP_U, out=u_host)
-        ev1.record(stream)
+            reps.append(path(opts, e2e))
+            evs[j + 1].record(stream)
         torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall0
         torch.cuda.nvtx.range_pop()
         if world > 1:
             torch.distributed.barrier()
-        ms = ev0.elapsed_time(ev1)
-        wall = time.perf_counter() - t_wall0
-        return ms, wall, reps
+        per = [evs[j].elapsed_time(evs[j + 1]) for j in range(steps)]
+        return evs[0].elapsed_time(evs[-1]), wall, per, reps
 
     if args.no_compare:
         precs = ["mixed" if args.precision == "auto" else args.precision]
     else:
         precs = ["mixed", "fp64"] if args.precision in ("auto", "mixed") else ["fp64", "mixed"]
-    # warm-up: first W load steps in each precision used, then back to the virgin state
-    for p_ in precs:
-        for j in range(args.warmup):
-            ctx.solve_load_path([prob.zeta[j % n_path]], opts_for(p_))
-        reset()
+    for p_ in precs:                      # warm-up: W whole paths in each precision
+        for _ in range(args.warmup):
+            path(opts_for(p_), False)
+    torch.cuda.synchronize()
 
-    # the timed runs: the same load steps in each precision, from the virgin state
-    ends_on_path_end = (args.skip + args.steps) % n_path == 0
     clocks = Clocks(local)
     runs = {}
     for p_ in precs:
-        reset()
-        ms_p, wall_p, reps_p = timed(p_, False, args.steps, args.skip)
-        runs[p_] = (max_over_ranks(ms_p, world), wall_p, reps_p, ctx.get(ep.EP_U) if ends_on_path_end else None)
+        ms_p, wall_p, per_p, reps_p = timed(p_, False, args.steps)
+        runs[p_] = (max_over_ranks(ms_p, world), wall_p, per_p, reps_p, ctx.get(ep.EP_U))
     clk = clocks.stop()
-    prec = args.precision if args.precision != "auto" else min(runs, key=lambda k: runs[k][0])
-    ms, wall, reps, u_primary = runs[prec]
+    # primary: the precision with the shorter median load-path time (time to solution)
+    prec = args.precision if args.precision != "auto" else min(runs, key=lambda k: statistics.median(runs[k][2]))
+    ms, wall, per, reps_paths, u_primary = runs[prec]
+    reps = [r for rp in reps_paths for r in rp]
     assemblies = sum(r.n_assemble for r in reps)
     n_int = info.n_int
     value = job_value(world, n_int, assemblies, ms)
+
+    def path_summary(prec_, ms_, per_, reps_paths_):
+        rr = [r for rp in reps_paths_ for r in rp]
+        a_ = sum(r.n_assemble for r in rr)
+        last = reps_paths_[-1]
+        return {"precision": prec_, "value": job_value(world, n_int, a_, ms_), "unit": UNIT,
+                "load_path_s_median": statistics.median(per_) / 1e3, "load_path_s_min": min(per_) / 1e3,
+                "paths": len(per_), "newton_its_per_path": int(sum(r.newton_its for r in last)),
+                "newton_its_fp32_per_path": int(sum(r.newton_its_fp32 for r in last)),
+                "krylov_its_per_path": int(sum(r.krylov_its for r in last)),
+                "assemblies_per_path": int(sum(r.n_assemble for r in last)),
+                "n_plastic_final": int(last[-1].n_plastic),
+                "max_rel_resid": max(r.rel_resid for r in rr)}
 
     compare = None
     others = [p_ for p_ in precs if p_ != prec]
     if others:
         other = others[0]
-        ms_o, _, reps_o, u_o = runs[other]
-        a_o = sum(r.n_assemble for r in reps_o)
-        compare = {"precision": other, "value": world * n_int * a_o / (ms_o / 1e3) / 1e9, "unit": UNIT,
-                   "load_path_s": ms_o / 1e3 * n_path / args.steps,
-                   "newton_its": int(sum(r.newton_its for r in reps_o)),
-                   "newton_its_fp32": int(sum(r.newton_its_fp32 for r in reps_o)),
-                   "krylov_its": int(sum(r.krylov_its for r in reps_o)),
-                   "max_rel_resid": max(r.rel_resid for r in reps_o),
-                   "assembly_avg_us": 1e3 * sum(r.t_assemble_kernel_ms for r in reps_o) / max(1, a_o),
-                   "spmv_avg_us": 1e3 * sum(r.t_spmv_kernel_ms for r in reps_o) / max(1, sum(r.n_spmv for r in reps_o))}
-        if u_primary is not None and u_o is not None:
-            compare["u_rel_diff"] = float(np.linalg.norm(u_primary - u_o) / max(np.linalg.norm(u_o), 1e-300))
+        ms_o, _, per_o, reps_o, u_o = runs[other]
+        compare = path_summary(other, ms_o, per_o, reps_o)
+        compare["u_rel_diff"] = float(np.linalg.norm(u_primary - u_o) / max(np.linalg.norm(u_o), 1e-300))
 
     e2e = None
     if not args.no_e2e:
-        reset()
-        ms_e2e, _, reps_e2e = timed(prec, True, args.steps, args.skip)
+        ms_e2e, _, _, reps_e2e = timed(prec, True, args.steps)
         ms_e2e = max_over_ranks(ms_e2e, world)
-        a2 = sum(r.n_assemble for r in reps_e2e)
-        e2e = {"value": world * n_int * a2 / (ms_e2e / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8,
-               "d2h_bytes_per_step": int(ctx.n_dof * 8)}
+        a2 = sum(r.n_assemble for rp in reps_e2e for r in rp)
+        e2e = {"value": job_value(world, n_int, a2, ms_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": int(zeta.nbytes), "d2h_bytes_per_step": int(u_host.nbytes + s_host.nbytes),
+               "what": "per step: the load factors enter from the host, u and sigma of the path's end are "
+                       "read back to host buffers"}
 
-    # roofline of the dominant kernel (the SpMV inside the Krylov solves, or the assembly)
+    # roofline of the step's kernels (CUDA events on the context's stream around every assembly
+    # and SpMV launch, and around a sample of the AMG level-0 Chebyshev sweeps)
     dim = info.dim
     f32 = prec == "mixed"
+    kb = 4 if f32 else 8
     peaks, peaks_kind = _peaks()
     t_spmv = sum(r.t_spmv_kernel_ms for r in reps)
     n_spmv = sum(r.n_spmv for r in reps)
     t_asmk = sum(r.t_assemble_kernel_ms for r in reps)
+    n_sm0 = sum(r.n_smooth0 for r in reps)
+    t_sm0 = sum(r.t_smooth0_kernel_ms for r in reps)
     sym = prob.material.model != 3
     plastic_assembled = sum(r.n_plastic_assembled for r in reps)
-    roof_spmv = roof_asm = None
+    pe_assembled = sum(r.n_plastic_elem_assembled for r in reps)
+    krylov_its = sum(r.krylov_its for r in reps)
+    cands = {}
     if n_spmv:
-        dur = t_spmv / n_spmv / 1e3
-        by = _spmv_bytes(info, dim, 4 if f32 else 8)
-        gbs = by / dur / 1e9
-        fl = 2.0 * info.nnz_blocks * dim * dim / dur / 1e12
-        traffic = (SPMV64_2D_DRAM_BYTES_PER_BLOCK * info.nnz_blocks
-                   if (dim == 2 and not f32 and SPMV_COUNTERS_CURRENT) else None)
-        roof_spmv = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": f"k_spmv (masked block-CSR, {'FP32' if f32 else 'FP64'})", "launches": n_spmv,
-                     "avg_us": dur * 1e6, "bytes_per_launch": by, "tflops": fl,
-                     "peak_source": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)", "share_of_step": t_spmv / ms}
-        if not f32:
-            roof_spmv["fp64_frac"] = fl / FP64_PEAK_TFLOPS
+        # the FP64 operator of the Krylov solves: the mixed path's FP64-tangent iterations use it too
+        cands["spmv"] = _roof_hbm(f"k_spmv (masked block-CSR)", n_spmv, t_spmv,
+                                  _spmv_bytes(info, dim, 8), peaks, peaks_kind, ms)
     if assemblies:
+        pf = plastic_assembled / max(1, assemblies * n_int)
+        pe = pe_assembled / max(1, assemblies * info.n_elem)
+        by = _assembly_bytes(info, dim, info.n_p, info.n_comp, kb, pe)
         dur = t_asmk / assemblies / 1e3
         tan = plastic_assembled * _tangent_flops_per_point(dim, info.n_p, sym) / assemblies
         base = n_int * (_base_flops_per_point(dim, info.n_p) + _return_map_flops(prob.material.model))
         fp64_flops = base + (0 if f32 else tan)
-        by = _assembly_bytes(info, dim, info.n_p, info.n_comp, 4 if f32 else 8)
-        gbs = by / dur / 1e9
-        roof_asm = {"bound": "hbm" if f32 else "alu", "kernel": f"k_assemble (fused, tangent {'FP32' if f32 else 'FP64'})",
-                    "launches": assemblies, "avg_us": dur * 1e6, "traffic": None,
-                    "bytes_per_launch": by, "fp64_flops_per_launch": fp64_flops,
-                    "fp32_flops_per_launch": tan if f32 else 0.0,
-                    "plastic_fraction": plastic_assembled / max(1, assemblies * n_int),
-                    "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
-                    "fp64_tflops": fp64_flops / dur / 1e12, "fp64_frac": fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS,
-                    "assembled_gpts_s": n_int / dur / 1e9, "share_of_step": t_asmk / ms,
-                    "peak_source": (f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)" if f32 else
-                                    "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)")}
-        if f32:
-            roof_asm.update({"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]})
-        else:
-            roof_asm.update({"achieved": fp64_flops / dur / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS})
-    dominant = roof_spmv if (roof_spmv and t_spmv >= t_asmk) else roof_asm
-    # the paper's observation (Section 8.2): tangent-assembly time is linear in the number of
-    # plastic points; fit over the timed steps' assemblies (per-step averages)
-    xs = [r.n_plastic_assembled / r.n_assemble for r in reps if r.n_assemble]
-    ys = [1e3 * r.t_assemble_kernel_ms / r.n_assemble for r in reps if r.n_assemble]
+        cands["assembly"] = _roof_hbm(
+            f"k_assemble (fused, tangent {'FP32' if f32 else 'FP64'})", assemblies, t_asmk, by, peaks, peaks_kind, ms,
+            plastic_fraction=pf, plastic_element_fraction=pe, fp64_flops_per_launch=fp64_flops,
+            fp64_tflops=fp64_flops / dur / 1e12, fp64_frac=fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS,
+            fp64_peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
+            assembled_gpts_s=n_int / dur / 1e9)
+    if n_sm0:
+        # sampled launches; the step's total is estimated as (Krylov iterations + solves) x the
+        # level-0 Chebyshev steps per V-cycle (2 pre + 2 post)
+        avg = t_sm0 / n_sm0
+        est_n = 4 * krylov_its
+        cands["amg_smooth0"] = _roof_hbm("k_cheb (AMG level-0 Chebyshev step, FP32)", n_sm0, t_sm0,
+                                         _cheb0_bytes(info, dim), peaks, peaks_kind, ms,
+                                         share_of_step=avg * est_n / ms, launches_sampled=n_sm0,
+                                         launches_estimated=est_n)
+    dominant = max(cands.values(), key=lambda r: r["share_of_step"]) if cands else None
+    xs = [r.n_plastic_assembled / r.n_assemble for r in reps_paths[-1] if r.n_assemble]
+    ys = [1e3 * r.t_assemble_kernel_ms / r.n_assemble for r in reps_paths[-1] if r.n_assemble]
     asm_fit = None
     if len(set(np.round(xs, 6))) >= 2:
         A = np.vstack([np.ones(len(xs)), xs]).T
@@ -650,22 +672,24 @@ def main():
                    "us_all_plastic_extrapolated": float(b0 + b1 * n_int),
                    "r2": 1.0 - float(np.sum((np.array(ys) - pred) ** 2)) / ss if ss > 0 else None,
                    "points": len(xs)}
+    primary = path_summary(prec, ms, per, reps_paths)
+    if primary["n_plastic_final"] == 0 and prob.material.model != 0:
+        raise SystemExit("bench: the timed load path never left the elastic range")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if f32 else "f64", "data": "synthetic",
             "config": _workload_config(args.workload, prob, {
-                "n_int": n_int, "parallelism": "replicas" if world > 1 else "single GPU", "precision": prec,
+                "n_int": n_int, "step": f"one whole load path ({n_path} load steps from the virgin state)",
+                "parallelism": "replicas" if world > 1 else "single GPU", "precision": prec,
                 "krylov": "GMRES(30)" if prob.material.model == 3 and prob.material.psi != prob.material.phi
                 else "CG", "precond": "smoothed-aggregation AMG, FP32 V-cycle, Galerkin from the tangent",
-                "split_elastic_cache": True, "skip": args.skip}),
-            "roofline": dominant, "roofline_assembly": roof_asm, "roofline_spmv": roof_spmv,
+                "split_elastic_cache": True}),
+            "roofline": dominant, "roofline_kernels": cands,
             "clocks": clk, "gpu_launches": int(sum(r.launches for r in reps)),
-            "load_path_s": ms / 1e3 * n_path / args.steps,
-            "newton_its": int(sum(r.newton_its for r in reps)), "krylov_its": int(sum(r.krylov_its for r in reps)),
-            "newton_its_fp32": int(sum(r.newton_its_fp32 for r in reps)),
-            "n_plastic_final": int(reps[-1].n_plastic) if reps else 0,
-            "max_rel_resid": max(r.rel_resid for r in reps) if reps else None,
+            "load_path_s": primary["load_path_s_median"], "primary": primary,
+            "newton_its": primary["newton_its_per_path"], "krylov_its": primary["krylov_its_per_path"],
+            "n_plastic_final": primary["n_plastic_final"], "max_rel_resid": primary["max_rel_resid"],
             "wall_s": wall}
     if asm_fit:
         line["assembly_vs_plastic"] = asm_fit
@@ -678,8 +702,6 @@ def main():
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
 
 
 if __name__ == "__main__":

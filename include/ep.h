@@ -143,7 +143,11 @@ typedef struct {
     int32_t start;               /* Newton start used: 0 last converged u, 1 extrapolated, 2 learned (for at
                                     least one problem of a batch) */
     int32_t n_learned;           /* warm_start = 2: problems that kept the learned start */
-    int32_t reserved;
+    int32_t n_smooth0;           /* AMG level-0 Chebyshev launches timed (profile = 1; a sample: the pre-smoothing
+                                    sweeps of the first V-cycles of every chunk of Krylov iterations) */
+    double t_smooth0_kernel_ms;  /* their summed duration (profile = 1) */
+    int64_t n_plastic_elem_assembled;   /* elements with a plastic point, summed over the step's assemblies that
+                                           formed a tangent (their blocks are the ones the split form rewrites) */
 } ep_step_report;
 
 /* Fields readable with ep_get / writable with ep_set. */
@@ -221,6 +225,16 @@ ep_status ep_get_info(const void* ctx, ep_info* info);
  */
 ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, const ep_opts* opts,
                              ep_step_report* reports);
+
+/*
+ * Return the context to the virgin state it had after ep_create (the state
+ * before the first load step of a path, Section 4): u = 0, eps^p = 0,
+ * hardening variables 0, stresses 0, plastic flags 0, and no load-path
+ * history (the next step starts like the first one, without extrapolation).
+ * Device memsets on the context's stream, no host transfer and no
+ * synchronisation; the mesh, K_elast and the preconditioner's setup are kept.
+ */
+ep_status ep_reset(void* ctx);
 
 /*
  * Copy a field (ep_field) to `dst` (host, or device when dst_is_device != 0).

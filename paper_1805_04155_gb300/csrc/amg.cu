@@ -315,7 +315,16 @@ __global__ void k_blockinv(DevPat A, const float* __restrict__ Avals, const int3
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= A.n_rows) return;
     float m[BS][BS], inv[BS][BS];
-    const float* src = Avals + (int64_t)diag[row] * (BS * BS);
+    const int64_t dk = diag[row];
+    if (dk < A.row_ptr[row] || dk >= A.row_ptr[row + 1]) {
+        // a row without its diagonal block (the host setup rejects such operators): identity, no read
+#pragma unroll
+        for (int r = 0; r < BS; ++r)
+#pragma unroll
+            for (int c = 0; c < BS; ++c) dinv[row * (BS * BS) + r * BS + c] = (r == c) ? 1.f : 0.f;
+        return;
+    }
+    const float* src = Avals + dk * (BS * BS);
 #pragma unroll
     for (int r = 0; r < BS; ++r)
 #pragma unroll
@@ -586,6 +595,8 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
     }
     D.n_levels = (int)H.levels.size();
     cudaError_t e;
+    for (auto& ev : D.ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
     std::vector<double> lam(AMG_MAX_LEVELS, 1.0);
     for (int l = 0; l < D.n_levels; ++l) {
         const AmgLevel& L = H.levels[l];
@@ -640,6 +651,8 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
 
 void amg_free(AmgDev& D) {
     for (void* p : D.allocs) cudaFree(p);
+    for (auto& ev : D.ev)
+        if (ev) cudaEventDestroy(ev);
     D = AmgDev{};
 }
 
@@ -841,8 +854,11 @@ static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* 
     auto work_of = [](int dpost, float* fin, float* scr) { return dpost % 2 == 0 ? fin : scr; };
     // level 0: pre-smoothing from zero, residual, restriction
     float* w0 = work_of(D.deg_post0, x0, l0.x2);
+    const bool ev_ok = D.profile && D.ev[0] && D.nev + 2 <= (int)(sizeof(D.ev) / sizeof(D.ev[0]));
+    if (ev_ok) cudaEventRecord(D.ev[D.nev++], s);
     smooth<float>(bs0, D.g0, M0, D.minv0, b0, nullptr, w0, w0 == x0 ? l0.x2 : x0, l0.d, cf0, D.deg_pre0, rec, s,
                   D.launches);
+    if (ev_ok) cudaEventRecord(D.ev[D.nev++], s);
     resid<float>(bs0, D.g0, M0, b0, w0, l0.r, rec, s);
     mv<float, float>(l0.R, l0.Rvals, l0.r, D.lv[1].b, 0, rec, s);
     D.launches += 2;
@@ -877,6 +893,17 @@ static cudaError_t vcycle(AmgDev& D, const BsrT<T>& A0, const float* b0, float* 
     smooth<float>(bs0, D.g0, M0, D.minv0, b0, w0, x0, l0.x2, l0.d, cf0, D.deg_post0, rec, s, D.launches);
     D.launches += 1;
     return cudaGetLastError();
+}
+
+void amg_profile_collect(AmgDev& D, int n_valid) {
+    for (int q = 0; q < D.nev / 2 && q < n_valid; ++q) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, D.ev[2 * q], D.ev[2 * q + 1]) == cudaSuccess) {
+            D.smooth0_ms += ms;
+            D.smooth0_n += D.deg_pre0;
+        }
+    }
+    D.nev = 0;
 }
 
 cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* in, double* out, const KrylovRec* rec,

@@ -99,7 +99,18 @@ struct AmgDev {
     int nparts = 0;
     std::vector<void*> allocs;
     int launches = 0;
+    // instrumentation (profile = 1): CUDA events around the level-0 pre-smoothing sweep of the
+    // V-cycles of a chunk of Krylov iterations, as many as ev holds
+    int profile = 0;
+    cudaEvent_t ev[64] = {};
+    int nev = 0;
+    double smooth0_ms = 0.0;           // summed duration of the timed level-0 Chebyshev launches
+    int smooth0_n = 0;                 // their number
 };
+
+// Instrumentation: add the first n_valid timed sweeps (V-cycles that did work) to smooth0_ms /
+// smooth0_n and restart the event list.  Call after the stream has been synchronised.
+void amg_profile_collect(AmgDev& D, int n_valid);
 
 cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms);
 void amg_free(AmgDev& D);

@@ -204,6 +204,13 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
         if ((tid & 31) == 0 && v) atomicAdd(a.n_plastic, (unsigned long long)v);
     }
     __syncthreads();
+    if (a.n_plastic_elem && tid < 32) {
+        unsigned v = 0;
+        for (int e = tid; e < ne; e += 32) v += s_eplast[e] ? 1u : 0u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (tid == 0 && v) atomicAdd(a.n_plastic_elem, (unsigned long long)v);
+    }
 
     // (1b) H_p = (w D) G_p, one thread per (point, node)
     if (a.want_K) {
@@ -301,12 +308,15 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
         const int64_t eg = e0 + e;
         const int64_t slot = a.mesh.slots[eg * (NP * NP) + p * NP + q];
         KT* dst = Kout + slot * (D * D);
+        // split mode: these slots now differ from K_elast; the next split assembly resets them
+        if (DELTA && a.dirty) a.dirty[slot] = 1;
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
             for (int c = 0; c < D; ++c) atomicAdd(dst + r * D + c, k[r][c]);
         if (SYM && p != q) {
             const int64_t slot2 = a.mesh.slots[eg * (NP * NP) + q * NP + p];
+            if (DELTA && a.dirty) a.dirty[slot2] = 1;
             KT* dst2 = Kout + slot2 * (D * D);
 #pragma unroll
             for (int r = 0; r < D; ++r)
@@ -421,6 +431,19 @@ __global__ void __launch_bounds__(256) k_geometry(GeomArgs a) {
             dst[p * D + i] = s;
         }
     a.wgt[ip] = fabs(det) * a.wq[q];
+}
+
+// ---------------------------------------------------------------------------
+// Split-mode reset (eq. (K-split)): blocks moved away from K_elast by the last split assembly get
+// K_elast's values back; one thread per block, the mark cleared as it is read.
+template <class T>
+__global__ void __launch_bounds__(256) k_reset_dirty(uint8_t* __restrict__ dirty, int64_t nnzb, int d2,
+                                                     const T* __restrict__ Kel, T* __restrict__ Kt) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nnzb; b += (int64_t)gridDim.x * blockDim.x) {
+        if (!dirty[b]) continue;
+        dirty[b] = 0;
+        for (int i = 0; i < d2; ++i) Kt[b * d2 + i] = Kel[b * d2 + i];
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -63,4 +63,16 @@ cudaError_t launch_constitutive(int dim, const MatConst& m, int64_t n, const dou
     return cudaGetLastError();
 }
 
+cudaError_t launch_reset_dirty(uint8_t* dirty, int64_t nnzb, int d2, const double* Kel, double* Kt, int grid,
+                               cudaStream_t s) {
+    k_reset_dirty<double><<<grid, 256, 0, s>>>(dirty, nnzb, d2, Kel, Kt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_dirty(uint8_t* dirty, int64_t nnzb, int d2, const float* Kel, float* Kt, int grid,
+                               cudaStream_t s) {
+    k_reset_dirty<float><<<grid, 256, 0, s>>>(dirty, nnzb, d2, Kel, Kt);
+    return cudaGetLastError();
+}
+
 }  // namespace ep

@@ -215,6 +215,11 @@ struct Ctx {
     KrylovWork kw{};
     bool K_valid = false;      // Kt holds the tangent of the last assembly
     bool K32_valid = false;    // K32 holds the tangent of the last assembly
+    // split form (eq. (K-split)): Kt (K32) equals K_elast (Kel32) outside the blocks marked in dirty64
+    // (dirty32); a split assembly resets just those blocks before adding the new plastic terms
+    uint8_t *dirty64 = nullptr, *dirty32 = nullptr;
+    bool split_base64 = false, split_base32 = false;   // the statement above holds
+    int reset_grid = 0;
     int n_committed = 0;
     double zeta_last = 0.0, zeta_prev = 0.0;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -294,6 +299,8 @@ static ep_status ensure_mixed(Ctx* c) {
     const int64_t nk = c->nnzb * c->dim * c->dim;
     CK(dalloc(c, &c->K32, nk));
     CK(dalloc(c, &c->Kel32, nk));
+    CK(dalloc(c, &c->dirty32, c->nnzb));
+    c->split_base32 = false;
     CK(dalloc(c, &c->r32, c->n_dof));
     CK(krylov_alloc_f32(c->kw, c->n_nodes, c->dim));
     CK(vec_cvt_f32(c->Kel, c->Kel32, nk, c->stream));
@@ -306,19 +313,33 @@ static ep_status ensure_mixed(Ctx* c) {
 static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K, bool mixed) {
     cudaStream_t s = c->stream;
     CK(cudaMemsetAsync(c->F, 0, sizeof(double) * c->n_dof, s));
-    CK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->counter, 0, 2 * sizeof(unsigned long long), s));
     if (mixed) {
         ep_status st = ensure_mixed(c);
         if (st != EP_OK) return st;
     }
     const size_t nk = (size_t)c->nnzb * c->dim * c->dim;
-    if (want_K && !mixed) {
-        if (split) CK(cudaMemcpyAsync(c->Kt, c->Kel, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+    const int d2 = c->dim * c->dim;
+    uint8_t* dirty = mixed ? c->dirty32 : c->dirty64;
+    bool& base = mixed ? c->split_base32 : c->split_base64;
+    if (want_K && split) {
+        // eq. (K-split): K = K_elast + sum over plastic elements.  The blocks the last split assembly
+        // moved away from K_elast get K_elast's values back (only those: an elastic tangent costs
+        // nothing here); the first split assembly after a full one copies K_elast whole.
+        if (!base) {
+            if (mixed) CK(cudaMemcpyAsync(c->K32, c->Kel32, sizeof(float) * nk, cudaMemcpyDeviceToDevice, s));
+            else CK(cudaMemcpyAsync(c->Kt, c->Kel, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemsetAsync(dirty, 0, c->nnzb, s));
+        } else {
+            if (mixed) CK(launch_reset_dirty(dirty, c->nnzb, d2, c->Kel32, c->K32, c->reset_grid, s));
+            else CK(launch_reset_dirty(dirty, c->nnzb, d2, c->Kel, c->Kt, c->reset_grid, s));
+            c->launches += 1;
+        }
+        base = true;
+    } else if (want_K) {
+        if (mixed) CK(cudaMemsetAsync(c->K32, 0, sizeof(float) * nk, s));
         else CK(cudaMemsetAsync(c->Kt, 0, sizeof(double) * nk, s));
-    }
-    if (want_K && mixed) {
-        if (split) CK(cudaMemcpyAsync(c->K32, c->Kel32, sizeof(float) * nk, cudaMemcpyDeviceToDevice, s));
-        else CK(cudaMemsetAsync(c->K32, 0, sizeof(float) * nk, s));
+        base = false;
     }
     AsmArgs a{};
     a.mesh = mesh_dev(c);
@@ -333,6 +354,8 @@ static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K, 
     a.elastic_only = 0;
     a.n_plastic = c->counter;
     a.err_flag = c->err_flag;
+    a.dirty = (want_K && split) ? dirty : nullptr;
+    a.n_plastic_elem = want_K ? c->counter + 1 : nullptr;
     if (c->profile) CK(cudaEventRecord(c->ev[4], s));
     CK(launch_assemble(c->eid, a, s));
     if (c->profile) CK(cudaEventRecord(c->ev[5], s));
@@ -586,6 +609,8 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     CKF(dalloc(c, &c->wgt, c->n_int));
     CKF(dalloc(c, &c->Kel, c->nnzb * d * d));
     CKF(dalloc(c, &c->Kt, c->nnzb * d * d));
+    CKF(dalloc(c, &c->dirty64, c->nnzb));
+    c->reset_grid = c->num_sms * 8;
     CKF(dalloc(c, &c->ep, c->n_int * c->n_comp));
     CKF(dalloc(c, &c->hard, c->hard_len));
     CKF(dalloc(c, &c->sig, c->n_int * c->n_comp));
@@ -606,14 +631,14 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
         CKF(dalloc(c, &c->d_chunk_norms, 3 * nc));
         c->h_chunk_norms.resize(3 * nc);
     }
-    CKF(dalloc(c, &c->counter, 1));
+    CKF(dalloc(c, &c->counter, 2));   // plastic points, plastic elements of the last assembly
     CKF(dalloc(c, &c->err_flag, 1));
     CKF(dalloc(c, &c->norms, 3));
     CKF(dalloc(c, &d_dhat, dhat.size()));
     CKF(dalloc(c, &d_wq, wq.size()));
     CKF(dalloc(c, &bad, 1));
     CKF(cudaMallocHost(&c->norms_host, 3 * sizeof(double)));
-    CKF(cudaMallocHost(&c->counter_host, sizeof(unsigned long long)));
+    CKF(cudaMallocHost(&c->counter_host, 2 * sizeof(unsigned long long)));
     CKF(cudaMallocHost(&c->err_host, sizeof(int)));
     for (auto& e : c->ev) CKF(cudaEventCreate(&e));
     CKF(krylov_alloc(c->kw, c->n_nodes, d, 20000, c->num_sms));
@@ -885,6 +910,26 @@ ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_
     return EP_OK;
 }
 
+ep_status ep_reset(void* ctx) {
+    if (!ctx) return EP_ERR_INVALID_ARG;
+    Ctx* c = static_cast<Ctx*>(ctx);
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->u, 0, sizeof(double) * c->n_dof, s));
+    CK(cudaMemsetAsync(c->u_prev, 0, sizeof(double) * c->n_dof, s));
+    CK(cudaMemsetAsync(c->ep, 0, sizeof(double) * c->n_int * c->n_comp, s));
+    CK(cudaMemsetAsync(c->hard, 0, sizeof(double) * c->hard_len, s));
+    CK(cudaMemsetAsync(c->sig, 0, sizeof(double) * c->n_int * c->n_comp, s));
+    CK(cudaMemsetAsync(c->flag, 0, c->n_int, s));
+    CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+    c->n_committed = 0;
+    c->zeta_last = c->zeta_prev = 0.0;
+    c->ws.hist = 0;
+    c->ws.uL_valid = false;
+    c->mixed_fallback = false;
+    return EP_OK;
+}
+
 static ep_status load_u(Ctx* c, const double* u, int32_t u_is_device) {
     CK(cudaMemcpyAsync(c->u_it, u, sizeof(double) * c->n_dof,
                        u_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -1136,6 +1181,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     const BsrF Af = bsr_dev(c, (const float*)c->K32);
     c->profile = o.profile;
     c->kw.profile = o.profile;
+    c->amg.profile = o.profile;
     c->kw.verbose = c->verbose;
     for (int k = 0; k < n_steps; ++k) {
         const auto t_step0 = std::chrono::steady_clock::now();
@@ -1146,6 +1192,8 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         c->amg.launches = 0;
         c->kw.spmv_n = 0;
         c->kw.spmv_ms = 0.0;
+        c->amg.smooth0_ms = 0.0;
+        c->amg.smooth0_n = 0;
         double t_asm_kernel = 0.0;
         const double z = zeta[k];
         ep_status st = EP_OK;
@@ -1243,10 +1291,13 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         bool use32 = false;      // this iteration's tangent and solve in FP32
         bool fp64_step = false;  // the rest of this step in FP64 (an FP32 iteration contracted poorly)
         double eta_prev = 1.0;   // Krylov tolerance of the last solve
+        // The last solve aimed at the Newton tolerance itself and Newton contracted well: the iterate
+        // is expected to converge, so F is evaluated alone first and the tangent only if it does not.
+        bool f_first = false;
         for (;;) {
             use32 = mixed && !c->mixed_fallback && !fp64_step;
             CK(cudaEventRecord(c->ev[0], s));
-            st = assemble(c, c->u_it, split, true, use32);
+            st = assemble(c, c->u_it, split, !f_first, use32);
             if (st != EP_OK) break;
             CK(cudaEventRecord(c->ev[1], s));
             CK(vec_residual(c->f_unit, z, c->F, c->free_dof, c->r, use32 ? c->r32 : nullptr, c->n_dof, c->kw.part,
@@ -1262,7 +1313,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             }
             CK(cudaMemcpyAsync(c->norms_host, c->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(c->counter_host, c->counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->counter_host, c->counter, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
@@ -1271,7 +1322,8 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 CK(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
                 t_asm_kernel += ms;
             }
-            rep.n_plastic_assembled += (int64_t)*c->counter_host;
+            rep.n_plastic_assembled += (int64_t)c->counter_host[0];
+            if (!f_first) rep.n_plastic_elem_assembled += (int64_t)c->counter_host[1];
             if (*c->err_host) {
                 c->err = "return mapping: apex reached with K*eta*eta_bar + Hc = 0 (no admissible stress)";
                 st = EP_ERR_RETURN_MAP;
@@ -1304,6 +1356,10 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             if (rel <= o.newton_rtol || rnorm == 0.0) {
                 converged = true;
                 break;
+            }
+            if (f_first) {   // not converged after all: the same iterate again, with the tangent
+                f_first = false;
+                continue;
             }
             if (it >= o.newton_maxit) {
                 st = EP_ERR_NEWTON_NO_CONVERGENCE;
@@ -1351,6 +1407,10 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             const bool basis32 = mixed && !use32 && m_it == 3;
             // an FP32 inner solve cannot go much below FP32 rounding; Newton (FP64 residual) refines further
             if (use32 || basis32) eta = std::max(eta, MIXED_ETA_MIN);
+            // this solve aims at the final tolerance (its forcing term is the floor eta_min) after a
+            // strongly contracting iteration: expect convergence at the next iterate
+            f_first = o.krylov_rtol <= 0.0 && eta * rnorm <= 0.5000001 * o.newton_rtol * scale &&
+                      rnorm_prev > 0.0 && rnorm < 0.1 * rnorm_prev;
             rnorm_prev = rnorm;
             eta_prev = eta;
             CK(cudaEventRecord(c->ev[2], s));
@@ -1491,6 +1551,8 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         rep.launches = c->launches + c->kw.launches + c->amg.launches;
         rep.n_spmv = c->kw.spmv_n;
         rep.t_spmv_kernel_ms = c->kw.spmv_ms;
+        rep.n_smooth0 = c->amg.smooth0_n;
+        rep.t_smooth0_kernel_ms = c->amg.smooth0_ms;
         rep.t_assemble_kernel_ms = t_asm_kernel;
         if (reports) reports[k] = rep;
         if (st != EP_OK) return st;

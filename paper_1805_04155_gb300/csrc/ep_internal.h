@@ -95,8 +95,18 @@ struct AsmArgs {
     int elastic_only;          // 1: D = C everywhere (K_elast assembly), u/state ignored
     unsigned long long* n_plastic;  // device counter (may be null)
     int* err_flag;             // device error word (return-map failures)
+    // split mode with want_K: every slot a plastic element adds to is marked 1 here (may be null)
+    uint8_t* dirty;
+    unsigned long long* n_plastic_elem;   // device counter of elements with a plastic point (may be null)
 };
 cudaError_t launch_assemble(int elem_id, const AsmArgs& a, cudaStream_t s);
+
+// Split-mode reset of eq. (K-split): Kt[b] = Kel[b] for every block b marked in dirty (blocks of d2
+// values), and the marks cleared.
+cudaError_t launch_reset_dirty(uint8_t* dirty, int64_t nnzb, int d2, const double* Kel, double* Kt, int grid,
+                               cudaStream_t s);
+cudaError_t launch_reset_dirty(uint8_t* dirty, int64_t nnzb, int d2, const float* Kel, float* Kt, int grid,
+                               cudaStream_t s);
 
 struct CommitArgs {
     MeshDev mesh;

@@ -667,6 +667,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
         const int first = it;
         const int stop = std::min(it + chunk, a.maxit + 1);
         int nev = 0;
+        if (a.amg) w.amg->nev = 0;
         for (; it < stop; ++it) {
             // profiling events: as many iterations of the chunk as the event array holds
             const bool ev_ok = w.profile && nev + (bicg ? 4 : 2) <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
@@ -708,6 +709,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
             // SpMVs of iterations before the converged one did work; later ones exited at once
             const int done_at = w.rec_host->done ? w.rec_host->its : it;
             const int per = bicg ? 2 : 1;
+            if (a.amg) amg_profile_collect(*w.amg, per * std::max(0, done_at - first));
             for (int j = 0; j < nev / 2; ++j) {
                 if (first + j / per >= done_at) break;
                 float ms = 0.f;
@@ -1094,6 +1096,7 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
             const auto t0 = std::chrono::steady_clock::now();
             const int j1 = std::min(a.m, j0 + chunk);
             int nev = 0;
+            if (use_amg) w.amg->nev = 0;
             for (int j = j0; j < j1; ++j) {
                 if (use_amg) amg_apply_t(w, A, a.V + (int64_t)j * w.n, a.z, w.rec, s);
                 else launch_pdl(k_gm_prec<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j);
@@ -1119,6 +1122,7 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
             t_wait += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
             last = *w.rec_host;
             if (w.profile) {
+                if (use_amg) amg_profile_collect(*w.amg, std::max(0, std::min(j1, last.its) - j0));
                 for (int q = 0; q < nev / 2 && j0 + q < last.its; ++q) {
                     float ms = 0.f;
                     if (cudaEventElapsedTime(&ms, w.ev[2 * q], w.ev[2 * q + 1]) == cudaSuccess) {

@@ -34,6 +34,7 @@ EP_WS_N_IN, EP_WS_WIDTH, EP_WS_N_OUT, EP_WS_N_PARAMS = 16, 128, 4, 19204
 
 EXPORTED = [
     "ep_default_opts", "ep_create", "ep_create_batch", "ep_destroy", "ep_get_info", "ep_solve_load_path", "ep_get", "ep_set",
+    "ep_reset",
     "ep_assemble", "ep_assemble_prec", "ep_commit", "ep_linear_solve", "ep_constitutive", "ep_status_str", "ep_last_error",
     "ep_linear_solve_noalloc", "ep_mlp_create", "ep_mlp_destroy", "ep_mlp_get_params", "ep_mlp_forward", "ep_mlp_grad",
     "ep_mlp_train_step", "ep_ws_record", "ep_ws_samples", "ep_ws_attach",
@@ -72,7 +73,8 @@ class ep_step_report(C.Structure):
                 ("n_assemble", C.c_int32), ("n_spmv", C.c_int32), ("t_assemble_kernel_ms", C.c_double),
                 ("t_spmv_kernel_ms", C.c_double), ("n_plastic_assembled", C.c_int64),
                 ("newton_its_fp32", C.c_int32), ("start", C.c_int32), ("n_learned", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("n_smooth0", C.c_int32), ("t_smooth0_kernel_ms", C.c_double),
+                ("n_plastic_elem_assembled", C.c_int64)]
 
 
 class ep_info(C.Structure):
@@ -97,6 +99,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.ep_solve_load_path.argtypes = [vp, i32, dp, C.POINTER(ep_opts), C.POINTER(ep_step_report)]
     lib.ep_get.argtypes = [vp, i32, vp, sz, i32]
     lib.ep_set.argtypes = [vp, i32, vp, sz, i32]
+    lib.ep_reset.argtypes = [vp]
     lib.ep_assemble.argtypes = [vp, vp, i32, i32, C.POINTER(i64)]
     lib.ep_assemble_prec.argtypes = [vp, vp, i32, i32, i32, C.POINTER(i64)]
     lib.ep_commit.argtypes = [vp, vp, i32]
@@ -302,6 +305,10 @@ class Context:
             self._check(lib().ep_set(self.h, field, a.ctypes.data, a.nbytes, 0))
         else:
             self._check(lib().ep_set(self.h, field, src.data_ptr(), src.numel() * src.element_size(), 1))
+
+    def reset(self):
+        """ep_reset: back to the virgin state (device memsets on the context's stream)."""
+        self._check(lib().ep_reset(self.h))
 
     def _vec_arg(self, v):
         if isinstance(v, np.ndarray):

@@ -88,6 +88,52 @@ def test_fed_iterate_assembly(ep, elem, dim, model):
     ctx.close()
 
 
+@pytest.mark.parametrize("model,elem,dim", [(DP, "P2", 2), (VM_ISO, "Q1", 3), (VM_KIN, "P1", 2), (DP, "P2", 3)])
+def test_split_reset_follows_changing_plastic_sets(ep, model, elem, dim):
+    """Eq. (K-split) across a sequence of split assemblies whose plastic sets differ: each one resets
+    only the blocks the previous one moved away from K_elast, so every K must still equal the
+    oracle's K_elast + sum over the current plastic points (large set, small set, none, large)."""
+    prob = small_problem(elem, dim, SIZES[(elem, dim)] + 1, model, seed=7)
+    u, ep_, hard = fed_iterate(prob, seed=8, dilate=(1.5e-3 if model == DP else 0.0))
+    ctx = ep.Context.from_problem(prob)
+    ctx.set(ep.EP_PLASTIC_STRAIN, ep_)
+    ctx.set(ep.EP_HARDENING, hard)
+    counts = []
+    for scale in (1.0, 0.35, 0.0, 1.0, 0.6):
+        us = u * scale
+        ref = oracle_eval(prob, us, ep_, hard, split=True)
+        n_pl = ctx.assemble(us, split=True)
+        counts.append(n_pl)
+        assert n_pl == int(np.count_nonzero(ref["res"]["plastic"]))
+        assert rel_fro(ctx.K_csr(), ref["K"]) < TOL
+        assert rel_max(ctx.get(ep.EP_F_INT), ref["F"]) < TOL
+    assert counts[0] > counts[1] and len(set(counts)) >= 3, counts
+    # a full assembly in between, then split again (the next split starts from a whole copy)
+    ctx.assemble(u, split=False)
+    ref = oracle_eval(prob, u * 0.35, ep_, hard, split=True)
+    ctx.assemble(u * 0.35, split=True)
+    assert rel_fro(ctx.K_csr(), ref["K"]) < TOL
+    ctx.close()
+
+
+def test_reset_returns_to_the_virgin_state(ep):
+    """ep_reset: state fields zero, and a load path solved after it equals one from a new context."""
+    from synthetic import p1_plane_vm
+    prob = p1_plane_vm(n=8, n_steps=6)
+    opts = ep.default_opts(newton_rtol=1e-12)
+    ctx = ep.Context.from_problem(prob)
+    ctx.solve_load_path(prob.zeta, opts)
+    u1, s1 = ctx.get(ep.EP_U), ctx.get(ep.EP_STRESS)
+    assert np.count_nonzero(ctx.get(ep.EP_PLASTIC_FLAG)) > 0
+    ctx.reset()
+    for f in (ep.EP_U, ep.EP_STRESS, ep.EP_PLASTIC_STRAIN, ep.EP_HARDENING, ep.EP_PLASTIC_FLAG):
+        assert not np.any(ctx.get(f))
+    reps = ctx.solve_load_path(prob.zeta, opts)
+    assert reps[0].start == 0          # no extrapolation from the path before the reset
+    assert rel_max(ctx.get(ep.EP_U), u1) < TOL and rel_max(ctx.get(ep.EP_STRESS), s1) < TOL
+    ctx.close()
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("model", MODELS)
 def test_constitutive_fuzz(ep, dim, model):
