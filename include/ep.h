@@ -124,6 +124,16 @@ typedef struct {
                                     2: the extrapolation corrected by the attached warm-start network
                                     (ep_ws_attach), judged per problem against the plain extrapolation */
     int32_t profile;             /* 1: time the assembly and SpMV kernels with CUDA events (fills t_*_kernel_ms) */
+    int32_t deterministic;       /* 1: bit-reproducible runs.  Elements are coloured at ep_create (no two elements
+                                    of a colour share a node) and the assembly runs one launch per colour with
+                                    plain adds into F and K instead of atomics; the AMG Galerkin products sum in
+                                    a fixed order; the preconditioner's spectral estimate and coarse operators are
+                                    rebuilt from the tangent at the first Newton iteration of every load step, so
+                                    a step depends only on its start state (a run resumed with ep_set from a saved
+                                    state repeats the uninterrupted run bit for bit when warm_start = 0).  The
+                                    setting stays with the context: later ep_assemble / ep_commit calls follow
+                                    the last ep_solve_load_path or ep_linear_solve that passed it (n_steps = 0
+                                    sets it without solving). */
 } ep_opts;
 
 typedef struct {
@@ -148,6 +158,9 @@ typedef struct {
     double t_smooth0_kernel_ms;  /* their summed duration (profile = 1) */
     int64_t n_plastic_elem_assembled;   /* elements with a plastic point, summed over the step's assemblies that
                                            formed a tangent (their blocks are the ones the split form rewrites) */
+    int32_t precise;             /* 1: the step's preconditioner used the precise V-cycle (FP64 coarse correction;
+                                    switched on for the rest of the path when GMRES stalled with the FP32 one) */
+    int32_t reserved;
 } ep_step_report;
 
 /* Fields readable with ep_get / writable with ep_set. */

@@ -181,15 +181,15 @@ __global__ void __launch_bounds__(AB) k_resid(Mat<T> A, const T* __restrict__ b,
     ROW_LOOP_END
 }
 
-// y = M x (add = 0) or y += M x (add = 1); FP32 matrix, FP32 accumulation
-template <int RB, int CB, int G, class TX, class TY>
+// y = M x (add = 0) or y += M x (add = 1); FP32 matrix, accumulation in TACC
+template <int RB, int CB, int G, class TX, class TY, class TACC = float>
 __global__ void __launch_bounds__(AB) k_mv(Mat<float> M, const TX* __restrict__ x, TY* __restrict__ y, int add,
                                             const KrylovRec* rec) {
     pdl_enter();
     if (rec && rec->done) return;
     ROW_LOOP_BEGIN(M.n_rows)
-    float acc[RB];
-    group_row<RB, CB, G, float, TX, float>(M, row, active, lg, x, acc);
+    TACC acc[RB];
+    group_row<RB, CB, G, float, TX, TACC>(M, row, active, lg, x, acc);
     if (active && lg == 0) {
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
@@ -215,6 +215,53 @@ __global__ void __launch_bounds__(AB) k_dense(const float* __restrict__ Ainv, in
     if (lane == 0) x[warp] = s;
 }
 
+// x = Ainv b, dense FP64 (coarsest level of the precise mode); one warp per row
+__global__ void __launch_bounds__(AB) k_dense64(const double* __restrict__ Ainv, int64_t n,
+                                                 const double* __restrict__ b, double* __restrict__ x,
+                                                 const KrylovRec* rec) {
+    pdl_enter();
+    if (rec && rec->done) return;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += Ainv[warp * n + j] * b[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) x[warp] = s;
+}
+
+// r = b - A x (masked) with FP64 A, b, r and an FP32 iterate x (the precise mode's level-0 residual
+// after the FP32 pre-smoothing)
+template <int RB, int G>
+__global__ void __launch_bounds__(AB) k_resid_mx(Mat<double> A, const double* __restrict__ b,
+                                                  const float* __restrict__ x, double* __restrict__ r,
+                                                  const KrylovRec* rec) {
+    pdl_enter();
+    if (rec && rec->done) return;
+    ROW_LOOP_BEGIN(A.n_rows)
+    double acc[RB];
+    group_row<RB, RB, G, double, float, double>(A, row, active, lg, x, acc);
+    if (active && lg == 0) {
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            const int64_t i = row * RB + q;
+            const bool fr = A.mask ? A.mask[i] != 0 : true;
+            r[i] = fr ? b[i] - acc[q] : 0.0;
+        }
+    }
+    ROW_LOOP_END
+}
+
+// out = x + e (FP64 iterate plus the FP32 correction)
+__global__ void k_add_mx(const double* __restrict__ x, const float* __restrict__ e, double* __restrict__ out, int64_t n,
+                         const KrylovRec* rec) {
+    pdl_enter();
+    if (rec && rec->done) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] + (double)e[i];
+}
+
 // ---------------------------------------------------------------------------
 // Galerkin products with fixed patterns: T = A P, A_next = R T.  One warp per
 // output block row; the row is accumulated in shared memory (FP32), each lane
@@ -230,36 +277,42 @@ __device__ __forceinline__ int find_col(const int32_t* cols, int len, int c) {
     return (lo < len && cols[lo] == c) ? lo : -1;
 }
 
-template <int RA, int CA, int CP, class TA>
-__global__ void __launch_bounds__(AB) k_rap_ap(Mat<TA> A, Mat<float> P, DevPat T, float* __restrict__ Tvals,
-                                                int max_row) {
-    extern __shared__ float sm[];
+template <int RA, int CA, int CP, class TA, class TO>
+__global__ void __launch_bounds__(AB) k_rap_ap(Mat<TA> A, Mat<float> P, DevPat T, TO* __restrict__ Tvals,
+                                                int max_row, int det) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    TO* sm = reinterpret_cast<TO*>(sm_raw);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float* acc = sm + (size_t)wib * max_row * (RA * CP);
+    TO* acc = sm + (size_t)wib * max_row * (RA * CP);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n_rows; i += nwarps) {
         const int tb = T.row_ptr[i], tlen = T.row_ptr[i + 1] - tb;
         const int32_t* tcols = T.col_idx + tb;
-        for (int e = lane; e < tlen * RA * CP; e += 32) acc[e] = 0.f;
+        for (int e = lane; e < tlen * RA * CP; e += 32) acc[e] = TO(0);
         __syncwarp();
-        for (int k = A.row_ptr[i] + lane; k < A.row_ptr[i + 1]; k += 32) {
+        // default: lanes take the row's blocks in turn and add with shared-memory atomics; det: every
+        // lane walks the whole row in order and adds only to the output blocks it owns (pos mod 32),
+        // so each sum has a fixed order
+        const int k0 = det ? A.row_ptr[i] : A.row_ptr[i] + lane, kstep = det ? 1 : 32;
+        for (int k = k0; k < A.row_ptr[i + 1]; k += kstep) {
             const int64_t j = A.col_idx[k];
-            float a[RA * CA];
+            TO a[RA * CA];
 #pragma unroll
-            for (int e = 0; e < RA * CA; ++e) a[e] = (float)A.vals[(int64_t)k * (RA * CA) + e];
+            for (int e = 0; e < RA * CA; ++e) a[e] = (TO)A.vals[(int64_t)k * (RA * CA) + e];
             for (int kp = P.row_ptr[j]; kp < P.row_ptr[j + 1]; ++kp) {
                 const int pos = find_col(tcols, tlen, P.col_idx[kp]);
-                if (pos < 0) continue;
+                if (pos < 0 || (det && (pos & 31) != lane)) continue;
                 const float* p = P.vals + (int64_t)kp * (CA * CP);
-                float* dst = acc + pos * (RA * CP);
+                TO* dst = acc + pos * (RA * CP);
 #pragma unroll
                 for (int r = 0; r < RA; ++r)
 #pragma unroll
                     for (int c = 0; c < CP; ++c) {
-                        float s = 0.f;
+                        TO s = TO(0);
 #pragma unroll
-                        for (int m = 0; m < CA; ++m) s += a[r * CA + m] * p[m * CP + c];
-                        atomicAdd(dst + r * CP + c, s);
+                        for (int m = 0; m < CA; ++m) s += a[r * CA + m] * (TO)p[m * CP + c];
+                        if (det) dst[r * CP + c] += s;
+                        else atomicAdd(dst + r * CP + c, s);
                     }
             }
         }
@@ -269,36 +322,39 @@ __global__ void __launch_bounds__(AB) k_rap_ap(Mat<TA> A, Mat<float> P, DevPat T
     }
 }
 
-template <int RR, int CR, int CT>
-__global__ void __launch_bounds__(AB) k_rap_rt(Mat<float> R, Mat<float> T, DevPat An, float* __restrict__ Anvals,
-                                                int max_row) {
-    extern __shared__ float sm[];
+template <int RR, int CR, int CT, class TO>
+__global__ void __launch_bounds__(AB) k_rap_rt(Mat<float> R, Mat<TO> T, DevPat An, TO* __restrict__ Anvals,
+                                                int max_row, int det) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    TO* sm = reinterpret_cast<TO*>(sm_raw);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float* acc = sm + (size_t)wib * max_row * (RR * CT);
+    TO* acc = sm + (size_t)wib * max_row * (RR * CT);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < R.n_rows; a += nwarps) {
         const int ab = An.row_ptr[a], alen = An.row_ptr[a + 1] - ab;
         const int32_t* acols = An.col_idx + ab;
-        for (int e = lane; e < alen * RR * CT; e += 32) acc[e] = 0.f;
+        for (int e = lane; e < alen * RR * CT; e += 32) acc[e] = TO(0);
         __syncwarp();
-        for (int k = R.row_ptr[a] + lane; k < R.row_ptr[a + 1]; k += 32) {
+        const int k0 = det ? R.row_ptr[a] : R.row_ptr[a] + lane, kstep = det ? 1 : 32;
+        for (int k = k0; k < R.row_ptr[a + 1]; k += kstep) {
             const int64_t i = R.col_idx[k];
-            float rb[RR * CR];
+            TO rb[RR * CR];
 #pragma unroll
-            for (int e = 0; e < RR * CR; ++e) rb[e] = R.vals[(int64_t)k * (RR * CR) + e];
+            for (int e = 0; e < RR * CR; ++e) rb[e] = (TO)R.vals[(int64_t)k * (RR * CR) + e];
             for (int kt = T.row_ptr[i]; kt < T.row_ptr[i + 1]; ++kt) {
                 const int pos = find_col(acols, alen, T.col_idx[kt]);
-                if (pos < 0) continue;
-                const float* t = T.vals + (int64_t)kt * (CR * CT);
-                float* dst = acc + pos * (RR * CT);
+                if (pos < 0 || (det && (pos & 31) != lane)) continue;
+                const TO* t = T.vals + (int64_t)kt * (CR * CT);
+                TO* dst = acc + pos * (RR * CT);
 #pragma unroll
                 for (int r = 0; r < RR; ++r)
 #pragma unroll
                     for (int c = 0; c < CT; ++c) {
-                        float s = 0.f;
+                        TO s = TO(0);
 #pragma unroll
                         for (int m = 0; m < CR; ++m) s += rb[r * CR + m] * t[m * CT + c];
-                        atomicAdd(dst + r * CT + c, s);
+                        if (det) dst[r * CT + c] += s;
+                        else atomicAdd(dst + r * CT + c, s);
                     }
             }
         }
@@ -309,61 +365,61 @@ __global__ void __launch_bounds__(AB) k_rap_rt(Mat<float> R, Mat<float> T, DevPa
 }
 
 // inverses of the BS x BS diagonal blocks (Gauss-Jordan with partial pivoting; identity if singular)
-template <int BS>
-__global__ void k_blockinv(DevPat A, const float* __restrict__ Avals, const int32_t* __restrict__ diag,
-                           float* __restrict__ dinv) {
+template <int BS, class T>
+__global__ void k_blockinv(DevPat A, const T* __restrict__ Avals, const int32_t* __restrict__ diag,
+                           T* __restrict__ dinv) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= A.n_rows) return;
-    float m[BS][BS], inv[BS][BS];
+    T m[BS][BS], inv[BS][BS];
     const int64_t dk = diag[row];
     if (dk < A.row_ptr[row] || dk >= A.row_ptr[row + 1]) {
         // a row without its diagonal block (the host setup rejects such operators): identity, no read
 #pragma unroll
         for (int r = 0; r < BS; ++r)
 #pragma unroll
-            for (int c = 0; c < BS; ++c) dinv[row * (BS * BS) + r * BS + c] = (r == c) ? 1.f : 0.f;
+            for (int c = 0; c < BS; ++c) dinv[row * (BS * BS) + r * BS + c] = (r == c) ? T(1) : T(0);
         return;
     }
-    const float* src = Avals + dk * (BS * BS);
+    const T* src = Avals + dk * (BS * BS);
 #pragma unroll
     for (int r = 0; r < BS; ++r)
 #pragma unroll
         for (int c = 0; c < BS; ++c) {
             m[r][c] = src[r * BS + c];
-            inv[r][c] = (r == c) ? 1.f : 0.f;
+            inv[r][c] = (r == c) ? T(1) : T(0);
         }
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < BS; ++c) {
         int piv = c;
-        float best = fabsf(m[c][c]);
+        T best = fabs(m[c][c]);
 #pragma unroll
         for (int r = c + 1; r < BS; ++r)
-            if (fabsf(m[r][c]) > best) { best = fabsf(m[r][c]); piv = r; }
-        if (!(best > 0.f)) { ok = false; break; }
+            if (fabs(m[r][c]) > best) { best = fabs(m[r][c]); piv = r; }
+        if (!(best > T(0))) { ok = false; break; }
         if (piv != c) {
 #pragma unroll
             for (int k = 0; k < BS; ++k) {
-                float t = m[c][k]; m[c][k] = m[piv][k]; m[piv][k] = t;
+                T t = m[c][k]; m[c][k] = m[piv][k]; m[piv][k] = t;
                 t = inv[c][k]; inv[c][k] = inv[piv][k]; inv[piv][k] = t;
             }
         }
-        const float dd = 1.f / m[c][c];
+        const T dd = T(1) / m[c][c];
 #pragma unroll
         for (int k = 0; k < BS; ++k) { m[c][k] *= dd; inv[c][k] *= dd; }
 #pragma unroll
         for (int r = 0; r < BS; ++r) {
             if (r == c) continue;
-            const float f = m[r][c];
+            const T f = m[r][c];
 #pragma unroll
             for (int k = 0; k < BS; ++k) { m[r][k] -= f * m[c][k]; inv[r][k] -= f * inv[c][k]; }
         }
     }
-    float* dst = dinv + row * (BS * BS);
+    T* dst = dinv + row * (BS * BS);
 #pragma unroll
     for (int r = 0; r < BS; ++r)
 #pragma unroll
-        for (int c = 0; c < BS; ++c) dst[r * BS + c] = ok ? inv[r][c] : (r == c ? 1.f : 0.f);
+        for (int c = 0; c < BS; ++c) dst[r * BS + c] = ok ? inv[r][c] : (r == c ? T(1) : T(0));
 }
 
 // ---------------------------------------------------------------------------
@@ -531,11 +587,23 @@ static void resid(int bs, int g, const Mat<T>& A, const T* b, const T* x, T* r, 
     }
 #undef EP_RESID
 }
-template <class TX, class TY>
+static void resid_mx(int bs, int g, const Mat<double>& A, const double* b, const float* x, double* r,
+                     const KrylovRec* rec, cudaStream_t s) {
+#define EP_RMX(RB) EP_G_SWITCH(g, { static const int occ = resident_ctas(k_resid_mx<RB, GG>);                      \
+                                    launch_pdl(k_resid_mx<RB, GG>, dim3(rows_grid(A.n_rows, GG, occ)), dim3(AB), 0, s, \
+                                               A, b, x, r, rec); })
+    switch (bs) {
+        case 2: EP_RMX(2) break;
+        case 3: EP_RMX(3) break;
+        case 6: EP_RMX(6) break;
+    }
+#undef EP_RMX
+}
+template <class TX, class TY, class TACC = float>
 static void mv(const DevPat& p, const float* v, const TX* x, TY* y, int add, const KrylovRec* rec, cudaStream_t s) {
     const Mat<float> M = matf(p, v);
-#define EP_MV(RB, CB) EP_G_SWITCH(p.g, { static const int occ = resident_ctas(k_mv<RB, CB, GG, TX, TY>);            \
-                                         launch_pdl(k_mv<RB, CB, GG, TX, TY>, dim3(rows_grid(M.n_rows, GG, occ)),     \
+#define EP_MV(RB, CB) EP_G_SWITCH(p.g, { static const int occ = resident_ctas(k_mv<RB, CB, GG, TX, TY, TACC>);      \
+                                         launch_pdl(k_mv<RB, CB, GG, TX, TY, TACC>, dim3(rows_grid(M.n_rows, GG, occ)), \
                                                     dim3(AB), 0, s, M, x, y, add, rec); })
     switch (p.rb * 10 + p.cb) {
         case 23: EP_MV(2, 3) break;
@@ -609,6 +677,7 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
         if (l > 0) {
             if ((e = up_pat(D, d.A, L.A)) != cudaSuccess) return e;
             if ((e = up_f(D, &d.Avals, L.A.vals, L.A.vals.size())) != cudaSuccess) return e;
+            d.a_vals = (int64_t)L.A.vals.size();
             if ((e = up(D, &d.diag, L.diag)) != cudaSuccess) return e;
             // one bs x bs block per row of A on every coarse level (the coarsest too, unused there)
             if ((e = up_f(D, &d.dinv, L.dinv, (size_t)L.A.n_rows * L.bs * L.bs)) != cudaSuccess) return e;
@@ -626,7 +695,8 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
             if ((e = up_pat(D, d.R, L.R)) != cudaSuccess) return e;
             if ((e = up_f(D, &d.Rvals, L.R.vals, L.R.vals.size())) != cudaSuccess) return e;
             if ((e = up_pat(D, d.T, L.T)) != cudaSuccess) return e;
-            if ((e = dvec(D, &d.Tvals, (int64_t)L.T.col_idx.size() * L.T.rb * L.T.cb)) != cudaSuccess) return e;
+            d.t_vals = (int64_t)L.T.col_idx.size() * L.T.rb * L.T.cb;
+            if ((e = dvec(D, &d.Tvals, d.t_vals)) != cudaSuccess) return e;
         }
         if (!L.dense_inv.empty() && (e = up_f(D, &d.dense_inv, L.dense_inv, L.dense_inv.size())) != cudaSuccess)
             return e;
@@ -675,14 +745,20 @@ static void power(AmgDev& D, int bs, const Mat<T>& A, const T* dinv, T* x, T* y,
     D.launches += 2 * its + (init ? 1 : 0);
 }
 
-template <class TA>
+// Galerkin refresh of level l + 1: T = A_l P_l, A_{l+1} = R_l T, and the block inverses of A_{l+1}
+// (not on the coarsest level), accumulated and stored in TO (float, or double in precise mode).
+template <class TA, class TO>
 static cudaError_t rap_level(AmgDev& D, int l, const Mat<TA>& A, cudaStream_t s) {
     AmgDevLevel& L = D.lv[l];
     AmgDevLevel& N = D.lv[l + 1];
+    constexpr bool F64 = sizeof(TO) == 8;
+    TO* Tv = F64 ? (TO*)L.Tvals64 : (TO*)L.Tvals;
+    TO* Nv = F64 ? (TO*)N.Avals64 : (TO*)N.Avals;
+    TO* Nd = F64 ? (TO*)N.dinv64 : (TO*)N.dinv;
     const int bs = L.bs, k = N.bs;
     // one warp per output row; as many warps per CTA as 160 KB of shared accumulators allow
-    const size_t per_ap = (size_t)std::max(1, L.max_t_row) * bs * k * sizeof(float);
-    const size_t per_rt = (size_t)std::max(1, L.max_next_row) * k * k * sizeof(float);
+    const size_t per_ap = (size_t)std::max(1, L.max_t_row) * bs * k * sizeof(TO);
+    const size_t per_rt = (size_t)std::max(1, L.max_next_row) * k * k * sizeof(TO);
     const size_t budget = 160 * 1024;
     if (per_ap > budget || per_rt > budget) return cudaErrorInvalidConfiguration;
     const int w_ap = (int)std::min<size_t>(AB / 32, budget / per_ap);
@@ -692,23 +768,23 @@ static cudaError_t rap_level(AmgDev& D, int l, const Mat<TA>& A, cudaStream_t s)
     const unsigned g_rt = (unsigned)std::max<int64_t>(1, std::min<int64_t>((L.R.n_rows + w_rt - 1) / w_rt, 152 * 64));
     const Mat<float> P = matf(L.P, L.Pvals);
     const Mat<float> R = matf(L.R, L.Rvals);
-    const Mat<float> Tm = matf(L.T, L.Tvals);
+    const Mat<TO> Tm{L.T.n_rows, L.T.row_ptr, L.T.col_idx, Tv, nullptr};
     cudaError_t e = cudaSuccess;
 #define EP_AP(RA, CP)                                                                                        \
     {                                                                                                         \
-        auto kern = k_rap_ap<RA, RA, CP, TA>;                                                                 \
+        auto kern = k_rap_ap<RA, RA, CP, TA, TO>;                                                             \
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ap)) !=       \
             cudaSuccess)                                                                                      \
             return e;                                                                                         \
-        kern<<<g_ap, 32 * w_ap, sm_ap, s>>>(A, P, L.T, L.Tvals, L.max_t_row);                                        \
+        kern<<<g_ap, 32 * w_ap, sm_ap, s>>>(A, P, L.T, Tv, L.max_t_row, D.deterministic);                                       \
     }
 #define EP_RT(RR, CR)                                                                                        \
     {                                                                                                         \
-        auto kern = k_rap_rt<RR, CR, RR>;                                                                     \
+        auto kern = k_rap_rt<RR, CR, RR, TO>;                                                                 \
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rt)) !=       \
             cudaSuccess)                                                                                      \
             return e;                                                                                         \
-        kern<<<g_rt, 32 * w_rt, sm_rt, s>>>(R, Tm, N.A, N.Avals, L.max_next_row);                                    \
+        kern<<<g_rt, 32 * w_rt, sm_rt, s>>>(R, Tm, N.A, Nv, L.max_next_row, D.deterministic);                                   \
     }
     switch (bs * 10 + k) {
         case 23: EP_AP(2, 3) EP_RT(3, 2) break;
@@ -721,44 +797,21 @@ static cudaError_t rap_level(AmgDev& D, int l, const Mat<TA>& A, cudaStream_t s)
 #undef EP_RT
     if (l + 1 < D.n_levels - 1) {   // block inverses feed the smoother; the coarsest level is inverted densely
         const unsigned gb = (unsigned)((N.A.n_rows + 127) / 128);
-        if (k == 3) k_blockinv<3><<<gb, 128, 0, s>>>(N.A, N.Avals, N.diag, N.dinv);
-        else k_blockinv<6><<<gb, 128, 0, s>>>(N.A, N.Avals, N.diag, N.dinv);
+        if (k == 3) k_blockinv<3, TO><<<gb, 128, 0, s>>>(N.A, Nv, N.diag, Nd);
+        else k_blockinv<6, TO><<<gb, 128, 0, s>>>(N.A, Nv, N.diag, Nd);
         D.launches += 1;
     }
     D.launches += 2;
     return cudaGetLastError();
 }
 
-// Common part of the refresh: level 0 is (A0's pattern, D.K0, D.minv0).
-template <class T>
-static cudaError_t refresh_core(AmgDev& D, const BsrT<T>& A0, int galerkin, cudaStream_t s) {
-    const int L = D.n_levels;
-    const int d0 = A0.dim;
-    const int64_t n0 = A0.n_rows * d0;
-    const Mat<float> M0 = mat0f(A0, D.K0);
-    power<float>(D, d0, M0, D.minv0, D.pw0, D.pwf, n0, A0.free_dof, D.lam + 0, s, !D.pw0_valid, 16);
-    D.pw0_valid = true;
-    if (!galerkin || L < 2) {
-        k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
-        D.launches += 1;
-        return cudaGetLastError();
-    }
-    cudaError_t e;
-    for (int l = 0; l + 1 < L; ++l) {
-        if (l == 0) e = rap_level<float>(D, 0, M0, s);
-        else e = rap_level<float>(D, l, matf(D.lv[l].A, D.lv[l].Avals), s);
-        if (e != cudaSuccess) return e;
-        AmgDevLevel& N = D.lv[l + 1];
-        if (l + 1 < L - 1)
-            power<float>(D, N.bs, matf(N.A, N.Avals), N.dinv, D.pwf, D.pwf + N.n, N.n, nullptr, D.lam + l + 1, s);
-    }
-    k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
-    D.launches += 1;
-    // coarsest: dense inverse on the host
-    AmgDevLevel& C = D.lv[L - 1];
+// Dense inverse of the coarsest operator (values TV on the device) on the host, stored as TI.
+template <class TV, class TI>
+static cudaError_t coarsest_inverse(AmgDevLevel& C, const TV* vals, TI* inv_dev, cudaStream_t s) {
     const int64_t nb = C.A.n_rows, bs = C.bs, n = C.n;
     std::vector<int32_t> rp(nb + 1), ci;
-    std::vector<float> v;
+    std::vector<TV> v;
+    cudaError_t e;
     if ((e = cudaMemcpyAsync(rp.data(), C.A.row_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
         return e;
@@ -768,7 +821,7 @@ static cudaError_t refresh_core(AmgDev& D, const BsrT<T>& A0, int galerkin, cuda
     if ((e = cudaMemcpyAsync(ci.data(), C.A.col_idx, sizeof(int32_t) * ci.size(), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaMemcpyAsync(v.data(), C.Avals, sizeof(float) * v.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(v.data(), vals, sizeof(TV) * v.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     std::vector<double> dense((size_t)n * n, 0.0);
@@ -776,13 +829,92 @@ static cudaError_t refresh_core(AmgDev& D, const BsrT<T>& A0, int galerkin, cuda
         for (int32_t b = rp[I]; b < rp[I + 1]; ++b)
             for (int r = 0; r < bs; ++r)
                 for (int c = 0; c < bs; ++c)
-                    dense[(size_t)(I * bs + r) * n + (size_t)ci[b] * bs + c] = v[((size_t)b * bs + r) * bs + c];
+                    dense[(size_t)(I * bs + r) * n + (size_t)ci[b] * bs + c] = (double)v[((size_t)b * bs + r) * bs + c];
     if (!amg_invert_dense(dense, (int)n)) return cudaErrorInvalidValue;
-    std::vector<float> inv(dense.begin(), dense.end());
-    if ((e = cudaMemcpyAsync(C.dense_inv, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
+    std::vector<TI> inv(dense.begin(), dense.end());
+    if ((e = cudaMemcpyAsync(inv_dev, inv.data(), sizeof(TI) * inv.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
     return cudaStreamSynchronize(s);
+}
+
+// FP64 arrays of the precise mode, on first use.
+static cudaError_t ensure_precise(AmgDev& D) {
+    if (D.precise_ready) return cudaSuccess;
+    cudaError_t e;
+    for (int l = 0; l < D.n_levels; ++l) {
+        AmgDevLevel& v = D.lv[l];
+        if (l == 0) {
+            if ((e = dvec(D, &v.x64, v.n)) != cudaSuccess) return e;
+            if ((e = dvec(D, &v.r64, v.n)) != cudaSuccess) return e;
+        } else {
+            double** dv[] = {&v.b64, &v.x64, &v.x2_64, &v.d64, &v.r64};
+            for (double** q : dv)
+                if ((e = dvec(D, q, v.n)) != cudaSuccess) return e;
+            if ((e = dvec(D, &v.Avals64, v.a_vals)) != cudaSuccess) return e;
+            if ((e = dvec(D, &v.dinv64, v.A.n_rows * v.bs * v.bs)) != cudaSuccess) return e;
+        }
+        if (l + 1 < D.n_levels && (e = dvec(D, &v.Tvals64, v.t_vals)) != cudaSuccess) return e;
+        if (l == D.n_levels - 1 && (e = dvec(D, &v.dense_inv64, v.n * v.n)) != cudaSuccess) return e;
+    }
+    if ((e = dvec(D, &D.pwd, 2 * (D.n_levels > 1 ? D.lv[1].n : 1))) != cudaSuccess) return e;
+    D.precise_ready = true;
+    return cudaSuccess;
+}
+
+// Common part of the refresh: level 0 is (A0's pattern, D.K0, D.minv0).  K64 (may be null): A0's
+// FP64 values, from which the precise mode builds FP64 coarse operators.
+template <class T>
+static cudaError_t refresh_core(AmgDev& D, const BsrT<T>& A0, const double* K64, int galerkin, cudaStream_t s) {
+    const int L = D.n_levels;
+    const int d0 = A0.dim;
+    const int64_t n0 = A0.n_rows * d0;
+    const Mat<float> M0 = mat0f(A0, D.K0);
+    power<float>(D, d0, M0, D.minv0, D.pw0, D.pwf, n0, A0.free_dof, D.lam + 0, s, !D.pw0_valid, 16);
+    D.pw0_valid = true;
+    const bool precise = D.precise && K64 && L >= 2;
+    if (precise && !D.precise_valid) galerkin = 1;   // the FP64 coarse operators do not exist yet
+    if (!galerkin || L < 2) {
+        k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
+        D.launches += 1;
+        return cudaGetLastError();
+    }
+    cudaError_t e;
+    if (precise) {
+        if ((e = ensure_precise(D)) != cudaSuccess) return e;
+        const Mat<double> M0d{A0.n_rows, A0.row_ptr, A0.col_idx, K64, A0.free_dof};
+        for (int l = 0; l + 1 < L; ++l) {
+            if (l == 0) e = rap_level<double, double>(D, 0, M0d, s);
+            else {
+                const Mat<double> Al{D.lv[l].A.n_rows, D.lv[l].A.row_ptr, D.lv[l].A.col_idx, D.lv[l].Avals64, nullptr};
+                e = rap_level<double, double>(D, l, Al, s);
+            }
+            if (e != cudaSuccess) return e;
+            AmgDevLevel& N = D.lv[l + 1];
+            if (l + 1 < L - 1) {
+                const Mat<double> An{N.A.n_rows, N.A.row_ptr, N.A.col_idx, N.Avals64, nullptr};
+                power<double>(D, N.bs, An, N.dinv64, D.pwd, D.pwd + N.n, N.n, nullptr, D.lam + l + 1, s);
+            }
+        }
+        k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
+        D.launches += 1;
+        AmgDevLevel& C = D.lv[L - 1];
+        if ((e = coarsest_inverse<double, double>(C, C.Avals64, C.dense_inv64, s)) != cudaSuccess) return e;
+        D.precise_valid = true;
+        return cudaSuccess;
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        if (l == 0) e = rap_level<float, float>(D, 0, M0, s);
+        else e = rap_level<float, float>(D, l, matf(D.lv[l].A, D.lv[l].Avals), s);
+        if (e != cudaSuccess) return e;
+        AmgDevLevel& N = D.lv[l + 1];
+        if (l + 1 < L - 1)
+            power<float>(D, N.bs, matf(N.A, N.Avals), N.dinv, D.pwf, D.pwf + N.n, N.n, nullptr, D.lam + l + 1, s);
+    }
+    k_cheb_setup<<<1, 1, 0, s>>>(D.lam, L, D.coef);
+    D.launches += 1;
+    D.precise_valid = false;   // the FP64 coarse operators (if any) no longer follow the tangent
+    AmgDevLevel& C = D.lv[L - 1];
+    return coarsest_inverse<float, float>(C, C.Avals, C.dense_inv, s);
 }
 
 cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s) {
@@ -798,13 +930,13 @@ cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int ga
     D.launches += 2;
     D.K0 = D.K32;
     D.minv0 = D.minv32;
-    return refresh_core(D, A0, galerkin, s);
+    return refresh_core(D, A0, A0.vals, galerkin, s);
 }
 
 cudaError_t amg_refresh(AmgDev& D, const BsrF& A0, const float* minv0, int galerkin, cudaStream_t s) {
     D.K0 = A0.vals;
     D.minv0 = minv0;
-    return refresh_core(D, A0, galerkin, s);
+    return refresh_core(D, A0, (const double*)nullptr, galerkin, s);
 }
 
 // 1-level hierarchy: out = Ainv in, FP32 inverse applied to FP64 vectors
@@ -906,9 +1038,73 @@ void amg_profile_collect(AmgDev& D, int n_valid) {
     D.nev = 0;
 }
 
+// Precise V-cycle, x = M^-1 b with FP64 b, x: near a limit load the tangent's softest modes sit at
+// FP32 rounding level relative to its largest entries (eigenvalue ratios of 1e-8 and below), so
+// FP32 coarse operators and FP32 residuals misplace them and GMRES stalls.  Here only the level-0
+// smoothing runs in FP32, and always on an equation whose right-hand side is an FP64 residual:
+//   x1 = S(b) (FP32, from zero);  r = b - K x1 (FP64);  x2 = x1 + P C^-1 R r (FP64 coarse levels);
+//   r2 = b - K x2 (FP64);  x = x2 + S(r2) (FP32 smoothing from zero, FP64 sum).
+static cudaError_t vcycle_precise(AmgDev& D, const BsrDev& A0, const double* b, double* x, const KrylovRec* rec,
+                                  cudaStream_t s) {
+    const int L = D.n_levels;
+    AmgDevLevel& l0 = D.lv[0];
+    const Mat<float> M0 = mat0f(A0, D.K0);
+    const Mat<double> K64{A0.n_rows, A0.row_ptr, A0.col_idx, A0.vals, A0.free_dof};
+    const int bs0 = A0.dim;
+    const float* cf0 = D.coef;
+    const int64_t n0 = l0.n;
+    auto work_of = [](int dpost, auto* fin, auto* scr) { return dpost % 2 == 0 ? fin : scr; };
+    // level 0: FP32 pre-smoothing from zero, FP64 residual, restriction (FP64 sums)
+    launch_pdl(k_cvt<double, float>, dim3(cvt_grid(n0)), dim3(256), 0, s, b, l0.b, n0, rec);
+    const bool ev_ok = D.profile && D.ev[0] && D.nev + 2 <= (int)(sizeof(D.ev) / sizeof(D.ev[0]));
+    if (ev_ok) cudaEventRecord(D.ev[D.nev++], s);
+    smooth<float>(bs0, D.g0, M0, D.minv0, l0.b, nullptr, l0.x, l0.x2, l0.d, cf0, D.deg_pre0, rec, s, D.launches);
+    if (ev_ok) cudaEventRecord(D.ev[D.nev++], s);
+    resid_mx(bs0, D.g0, K64, b, l0.x, l0.r64, rec, s);
+    mv<double, double, double>(l0.R, l0.Rvals, l0.r64, D.lv[1].b64, 0, rec, s);
+    D.launches += 3;
+    // coarse levels (FP64), descending
+    for (int l = 1; l < L - 1; ++l) {
+        AmgDevLevel& v = D.lv[l];
+        const Mat<double> A{v.A.n_rows, v.A.row_ptr, v.A.col_idx, v.Avals64, nullptr};
+        double* w = work_of(D.deg_c, v.x64, v.x2_64);
+        smooth<double>(v.bs, v.A.g, A, v.dinv64, v.b64, nullptr, w, w == v.x64 ? v.x2_64 : v.x64, v.d64,
+                       D.coef + l * AMG_CHEB_DEGREE * 3, D.deg_c, rec, s, D.launches);
+        resid<double>(v.bs, v.A.g, A, v.b64, w, v.r64, rec, s);
+        mv<double, double, double>(v.R, v.Rvals, v.r64, D.lv[l + 1].b64, 0, rec, s);
+        D.launches += 2;
+    }
+    {
+        AmgDevLevel& c = D.lv[L - 1];
+        const unsigned g = (unsigned)((c.n * 32 + AB - 1) / AB);
+        launch_pdl(k_dense64, dim3(g), dim3(AB), 0, s, c.dense_inv64, c.n, c.b64, c.x64, rec);
+        D.launches += 1;
+    }
+    // ascending
+    for (int l = L - 2; l >= 1; --l) {
+        AmgDevLevel& v = D.lv[l];
+        const Mat<double> A{v.A.n_rows, v.A.row_ptr, v.A.col_idx, v.Avals64, nullptr};
+        double* w = work_of(D.deg_c, v.x64, v.x2_64);
+        mv<double, double, double>(v.P, v.Pvals, D.lv[l + 1].x64, w, 1, rec, s);
+        smooth<double>(v.bs, v.A.g, A, v.dinv64, v.b64, w, v.x64, v.x2_64, v.d64, D.coef + l * AMG_CHEB_DEGREE * 3,
+                       D.deg_c, rec, s, D.launches);
+        D.launches += 1;
+    }
+    // level 0: x2 = x1 + P e (FP64), r2 = b - K x2 (FP64), FP32 smoothing of the correction, sum
+    launch_pdl(k_cvt<float, double>, dim3(cvt_grid(n0)), dim3(256), 0, s, l0.x, l0.x64, n0, rec);
+    mv<double, double, double>(l0.P, l0.Pvals, D.lv[1].x64, l0.x64, 1, rec, s);
+    resid<double>(bs0, D.g0, K64, b, l0.x64, l0.r64, rec, s);
+    launch_pdl(k_cvt<double, float>, dim3(cvt_grid(n0)), dim3(256), 0, s, l0.r64, l0.r, n0, rec);
+    smooth<float>(bs0, D.g0, M0, D.minv0, l0.r, nullptr, l0.x, l0.x2, l0.d, cf0, D.deg_post0, rec, s, D.launches);
+    launch_pdl(k_add_mx, dim3(cvt_grid(n0)), dim3(256), 0, s, (const double*)l0.x64, (const float*)l0.x, x, n0, rec);
+    D.launches += 5;
+    return cudaGetLastError();
+}
+
 cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* in, double* out, const KrylovRec* rec,
                       cudaStream_t s) {
     AmgDevLevel& l0 = D.lv[0];
+    if (D.precise && D.precise_valid && D.n_levels > 1) return vcycle_precise(D, A0, in, out, rec, s);
     if (D.n_levels == 1) {
         const unsigned g = (unsigned)((l0.n * 32 + AB - 1) / AB);
         launch_pdl(k_dense_d, dim3(g), dim3(AB), 0, s, l0.dense_inv, l0.n, in, out, rec);

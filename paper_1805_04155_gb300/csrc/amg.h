@@ -76,6 +76,12 @@ struct AmgDevLevel {
     float* dense_work = nullptr;       // coarsest level: [n][2n] Gauss-Jordan work
     int max_t_row = 0, max_next_row = 0;
     float *b = nullptr, *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr;   // work vectors (all levels)
+    // FP64 coarse correction (precise mode, allocated on first use): the operator, its block
+    // inverses, the product A P of the Galerkin refresh, the coarsest dense inverse and work vectors;
+    // level 0 uses x64 (iterate) and r64 (residual) only
+    double *Avals64 = nullptr, *dinv64 = nullptr, *Tvals64 = nullptr, *dense_inv64 = nullptr;
+    double *b64 = nullptr, *x64 = nullptr, *x2_64 = nullptr, *d64 = nullptr, *r64 = nullptr;
+    int64_t a_vals = 0, t_vals = 0;    // value counts of A (levels >= 1) and of A P
 };
 
 struct AmgDev {
@@ -99,6 +105,13 @@ struct AmgDev {
     int nparts = 0;
     std::vector<void*> allocs;
     int launches = 0;
+    // precise mode: levels >= 1, their Galerkin operators, the coarsest inverse and the level-0
+    // residuals in FP64, the level-0 smoothing in FP32 on the residual equation (see amg_apply)
+    int precise = 0;
+    int deterministic = 0;             // 1: Galerkin products summed in a fixed order (no shared atomics)
+    bool precise_ready = false;        // FP64 arrays allocated
+    bool precise_valid = false;        // the FP64 coarse operators follow the last Galerkin refresh
+    double* pwd = nullptr;             // FP64 power-iteration work [2][n1]
     // instrumentation (profile = 1): CUDA events around the level-0 pre-smoothing sweep of the
     // V-cycles of a chunk of Krylov iterations, as many as ev holds
     int profile = 0;
@@ -119,10 +132,15 @@ void amg_free(AmgDev& D);
 // inverses, spectral estimates and the coarsest dense inverse).  The FP64 overload first rounds A0
 // and minv0 to FP32 copies; the FP32 overload (mixed path) uses the given arrays, which must stay
 // valid until the next refresh.
+// In precise mode (D.precise != 0) the FP64 overload builds the coarse operators in FP64 from A0's
+// FP64 values.
 cudaError_t amg_refresh(AmgDev& D, const BsrDev& A0, const double* minv0, int galerkin, cudaStream_t s);
 cudaError_t amg_refresh(AmgDev& D, const BsrF& A0, const float* minv0, int galerkin, cudaStream_t s);
 // One V-cycle: out = M^-1 in (level 0 uses the operator of the last refresh; A0 gives its pattern
-// and free-DOF mask).
+// and free-DOF mask).  The FP64 overload in precise mode: FP32 pre-smoothing from zero, the FP64
+// residual with A0's FP64 values, the FP64 coarse correction, the FP64 residual again, FP32
+// smoothing of the correction equation from zero, and the sum in FP64; a refresh in precise mode
+// must precede it.
 // rec (may be null): the calling solver's record; every launch exits at once once rec->done is set.
 cudaError_t amg_apply(AmgDev& D, const BsrDev& A0, const double* in, double* out, const KrylovRec* rec,
                       cudaStream_t s);

@@ -47,7 +47,7 @@ struct AsmShape {
     static constexpr int OFF_GK = OFF_H + NIP * NP * NS * D;
     static constexpr int N_KT = OFF_GK + (F32 ? NIP * NP * D : 0);
     static constexpr size_t BYTES_KT = (sizeof(KT) * N_KT + 7) / 8 * 8;
-    static constexpr size_t SMEM = sizeof(double) * N_DBL + BYTES_KT + sizeof(int) * (EPC * NP + EPC + NIP);
+    static constexpr size_t SMEM = sizeof(double) * N_DBL + BYTES_KT + sizeof(int) * (EPC * NP + 2 * EPC + NIP);
 };
 
 // Load the stored state of one point into active components.
@@ -119,19 +119,26 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
     int* s_node = reinterpret_cast<int*>(reinterpret_cast<char*>(s_kt) + S::BYTES_KT);   // [EPC][NP]
     int* s_eplast = s_node + EPC * NP;                        // [EPC]
     int* s_ipflag = s_eplast + EPC;                           // [NIP]
+    int* s_eid = s_ipflag + S::NIP;                           // [EPC] global element ids
     KT* Kout = S::F32 ? reinterpret_cast<KT*>(a.Kvals32) : reinterpret_cast<KT*>(a.Kvals);
 
     const int tid = threadIdx.x;
-    const int64_t n_elem = a.mesh.n_elem, n_int = a.mesh.n_int;
+    const int64_t n_int = a.mesh.n_int;
+    const bool listed = a.elem_list != nullptr;   // deterministic form: one colour, plain stores
+    const int64_t n_elem = listed ? a.list_n : a.mesh.n_elem;
     const int64_t e0 = (int64_t)blockIdx.x * EPC;
     const int ne = (int)min((int64_t)EPC, n_elem - e0);
     const int nip = ne * NQ;
     const int64_t ip0 = e0 * NQ;
 
     // (0) stage connectivity, gradients, weights and displacements
-    for (int i = tid; i < ne * NP; i += ASM_THREADS) s_node[i] = a.mesh.elem_nodes[e0 * NP + i];
-    for (int i = tid; i < EPC; i += ASM_THREADS) s_eplast[i] = 0;
-    {
+    for (int i = tid; i < EPC; i += ASM_THREADS) {
+        s_eplast[i] = 0;
+        s_eid[i] = listed ? (i < ne ? a.elem_list[e0 + i] : 0) : (int)(e0 + i);
+    }
+    if (listed) __syncthreads();
+    if (!listed) {
+        for (int i = tid; i < ne * NP; i += ASM_THREADS) s_node[i] = a.mesh.elem_nodes[e0 * NP + i];
         const double* src = a.mesh.dphi + ip0 * (NP * D);
         for (int i = tid; i < nip * NP * D; i += ASM_THREADS) {
             const double g = src[i];
@@ -139,6 +146,17 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
             if (S::F32) const_cast<KT*>(s_gk)[i] = (KT)g;
         }
         for (int i = tid; i < nip; i += ASM_THREADS) s_w[i] = a.mesh.wgt[ip0 + i];
+    } else {
+        // elements of one colour: each element's connectivity, gradients and weights are contiguous
+        for (int i = tid; i < ne * NP; i += ASM_THREADS)
+            s_node[i] = a.mesh.elem_nodes[(int64_t)s_eid[i / NP] * NP + i % NP];
+        constexpr int PER = NQ * NP * D;
+        for (int i = tid; i < nip * NP * D; i += ASM_THREADS) {
+            const double g = a.mesh.dphi[(int64_t)s_eid[i / PER] * PER + i % PER];
+            s_g[i] = g;
+            if (S::F32) const_cast<KT*>(s_gk)[i] = (KT)g;
+        }
+        for (int i = tid; i < nip; i += ASM_THREADS) s_w[i] = a.mesh.wgt[(int64_t)s_eid[i / NQ] * NQ + i % NQ];
     }
     __syncthreads();
     if (MODEL != 0 || WANT_F) {
@@ -153,9 +171,9 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
     unsigned my_plastic = 0;
     for (int j = tid; j < nip; j += ASM_THREADS) {
         const int e = j / NQ;
-        const int64_t ip = ip0 + j;
+        const int64_t ip = (int64_t)s_eid[e] * NQ + j % NQ;
         const double w = s_w[j];
-        const MatConst& mat = elem_material(a.mesh, e0 + e);
+        const MatConst& mat = elem_material(a.mesh, s_eid[e]);
         PointOut<NA> o;
         if (MODEL == 0 && !WANT_F) {
             PointIn<NA> in;
@@ -262,8 +280,13 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
                 }
             }
             const int64_t node = s_node[t];
+            if (listed) {   // one colour: this element is the node's only contributor in the launch
 #pragma unroll
-            for (int c = 0; c < D; ++c) atomicAdd(a.F + node * D + c, f[c]);
+                for (int c = 0; c < D; ++c) a.F[node * D + c] += f[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < D; ++c) atomicAdd(a.F + node * D + c, f[c]);
+            }
         }
     }
     if (!a.want_K) return;
@@ -305,23 +328,37 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
                 }
             }
         }
-        const int64_t eg = e0 + e;
+        const int64_t eg = s_eid[e];
         const int64_t slot = a.mesh.slots[eg * (NP * NP) + p * NP + q];
         KT* dst = Kout + slot * (D * D);
         // split mode: these slots now differ from K_elast; the next split assembly resets them
         if (DELTA && a.dirty) a.dirty[slot] = 1;
+        if (listed) {   // one colour: no other element of the launch owns this node pair
 #pragma unroll
-        for (int r = 0; r < D; ++r)
+            for (int r = 0; r < D; ++r)
 #pragma unroll
-            for (int c = 0; c < D; ++c) atomicAdd(dst + r * D + c, k[r][c]);
+                for (int c = 0; c < D; ++c) dst[r * D + c] += k[r][c];
+        } else {
+#pragma unroll
+            for (int r = 0; r < D; ++r)
+#pragma unroll
+                for (int c = 0; c < D; ++c) atomicAdd(dst + r * D + c, k[r][c]);
+        }
         if (SYM && p != q) {
             const int64_t slot2 = a.mesh.slots[eg * (NP * NP) + q * NP + p];
             if (DELTA && a.dirty) a.dirty[slot2] = 1;
             KT* dst2 = Kout + slot2 * (D * D);
+            if (listed) {
 #pragma unroll
-            for (int r = 0; r < D; ++r)
+                for (int r = 0; r < D; ++r)
 #pragma unroll
-                for (int c = 0; c < D; ++c) atomicAdd(dst2 + c * D + r, k[r][c]);
+                    for (int c = 0; c < D; ++c) dst2[c * D + r] += k[r][c];
+            } else {
+#pragma unroll
+                for (int r = 0; r < D; ++r)
+#pragma unroll
+                    for (int c = 0; c < D; ++c) atomicAdd(dst2 + c * D + r, k[r][c]);
+            }
         }
     }
 }
@@ -459,7 +496,8 @@ cudaError_t launch_asm_t(const AsmArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int64_t grid = (a.mesh.n_elem + S::EPC - 1) / S::EPC;
+    const int64_t n = a.elem_list ? a.list_n : a.mesh.n_elem;
+    const int64_t grid = (n + S::EPC - 1) / S::EPC;
     if (grid == 0) return cudaSuccess;
     kern<<<(unsigned)grid, ASM_THREADS, S::SMEM, s>>>(a);
     return cudaGetLastError();

@@ -218,6 +218,10 @@ struct Ctx {
     // split form (eq. (K-split)): Kt (K32) equals K_elast (Kel32) outside the blocks marked in dirty64
     // (dirty32); a split assembly resets just those blocks before adding the new plastic terms
     uint8_t *dirty64 = nullptr, *dirty32 = nullptr;
+    // deterministic form (ep_opts.deterministic): element colours, one assembly launch per colour
+    int deterministic = 0;
+    std::vector<int32_t> h_color_ptr;   // [n_colors + 1]
+    int32_t* color_elems = nullptr;     // device [n_elem]
     bool split_base64 = false, split_base32 = false;   // the statement above holds
     int reset_grid = 0;
     int n_committed = 0;
@@ -357,12 +361,33 @@ static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K, 
     a.dirty = (want_K && split) ? dirty : nullptr;
     a.n_plastic_elem = want_K ? c->counter + 1 : nullptr;
     if (c->profile) CK(cudaEventRecord(c->ev[4], s));
-    CK(launch_assemble(c->eid, a, s));
+    if (c->deterministic) {
+        // one launch per colour, in colour order: no two elements of a launch share a node, so F and
+        // K receive plain adds in a fixed order (bit-reproducible)
+        const int nc = (int)c->h_color_ptr.size() - 1;
+        for (int col = 0; col < nc; ++col) {
+            a.elem_list = c->color_elems + c->h_color_ptr[col];
+            a.list_n = c->h_color_ptr[col + 1] - c->h_color_ptr[col];
+            CK(launch_assemble(c->eid, a, s));
+        }
+        c->launches += nc;
+    } else {
+        CK(launch_assemble(c->eid, a, s));
+        c->launches += 1;
+    }
     if (c->profile) CK(cudaEventRecord(c->ev[5], s));
-    c->launches += 1;
     c->K_valid = want_K && !mixed;
     c->K32_valid = want_K && mixed;
     return EP_OK;
+}
+
+// The V-cycle's coarse correction starts each load path in FP32 (EP_AMG_PRECISE=1: in FP64); the
+// Newton loop switches to the precise V-cycle when an FP64 GMRES solve stalls with the FP32 one.
+static void precise_default(Ctx* c) {
+    const char* v = std::getenv("EP_AMG_PRECISE");
+    const int want = (v && std::atoi(v) == 1) ? 1 : 0;
+    if (c->amg.precise && !want) c->amg_elastic = false;   // the FP32 coarse operators are stale
+    c->amg.precise = want;
 }
 
 static ep_status read_flags(Ctx* c, unsigned long long* n_plastic, bool* rm_err) {
@@ -428,6 +453,7 @@ void ep_default_opts(ep_opts* o) {
     o->split_elastic_cache = 1;
     o->warm_start = 1;
     o->profile = 0;
+    o->deterministic = 0;
 }
 
 const char* ep_status_str(int32_t s) {
@@ -575,6 +601,9 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     if (!build_pattern(c->n_nodes, c->n_elem, c->n_p, mesh->elem_nodes, row_ptr, col_idx, slots, c->err))
         return fail(EP_ERR_INVALID_ARG);
     c->nnzb = (int64_t)col_idx.size();
+    std::vector<int32_t> color_elems;
+    if (!color_elements(c->n_nodes, c->n_elem, c->n_p, mesh->elem_nodes, c->h_color_ptr, color_elems, c->err))
+        return fail(EP_ERR_INVALID_ARG);
     std::vector<int32_t> diag(c->n_nodes);
     for (int64_t n = 0; n < c->n_nodes; ++n) {
         const int32_t* b = col_idx.data() + row_ptr[n];
@@ -610,6 +639,7 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     CKF(dalloc(c, &c->Kel, c->nnzb * d * d));
     CKF(dalloc(c, &c->Kt, c->nnzb * d * d));
     CKF(dalloc(c, &c->dirty64, c->nnzb));
+    CKF(dalloc(c, &c->color_elems, c->n_elem));
     c->reset_grid = c->num_sms * 8;
     CKF(dalloc(c, &c->ep, c->n_int * c->n_comp));
     CKF(dalloc(c, &c->hard, c->hard_len));
@@ -662,6 +692,8 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     CKF(cudaMemcpyAsync(c->coords, mesh->coords, sizeof(double) * c->n_nodes * d, cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->elem, mesh->elem_nodes, sizeof(int32_t) * c->n_elem * c->n_p, cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->slots, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, s));
+    CKF(cudaMemcpyAsync(c->color_elems, color_elems.data(), sizeof(int32_t) * color_elems.size(),
+                        cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->row_ptr, row_ptr.data(), sizeof(int32_t) * row_ptr.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->col_idx, col_idx.data(), sizeof(int32_t) * col_idx.size(), cudaMemcpyHostToDevice, s));
     CKF(cudaMemcpyAsync(c->diag_slot, diag.data(), sizeof(int32_t) * diag.size(), cudaMemcpyHostToDevice, s));
@@ -724,7 +756,13 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     a.mode = ASM_FULL;
     a.want_K = 1;
     a.elastic_only = 1;
-    CKF(launch_assemble(c->eid, a, s));
+    // coloured (one launch per colour, plain adds): K_elast is bit-reproducible, so the split
+    // tangent and the AMG hierarchy built from it are too
+    for (size_t col = 0; col + 1 < c->h_color_ptr.size(); ++col) {
+        a.elem_list = c->color_elems + c->h_color_ptr[col];
+        a.list_n = c->h_color_ptr[col + 1] - c->h_color_ptr[col];
+        CKF(launch_assemble(c->eid, a, s));
+    }
     CKF(cudaStreamSynchronize(s));
 #undef CKF
     c->h_row_ptr = std::move(row_ptr);
@@ -807,6 +845,7 @@ static ep_status ensure_amg(Ctx* c) {
     CK(amg_upload(H, c->amg, c->num_sms));
     c->kw.amg = &c->amg;
     c->amg_built = true;
+    precise_default(c);
     c->amg_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (c->verbose) {
         std::fprintf(stderr, "[ep] AMG: %zu levels, setup %.1f ms, sizes", H.levels.size(), c->amg_setup_ms);
@@ -906,6 +945,7 @@ ep_status ep_set(void* ctx, int32_t field, const void* src, size_t bytes, int32_
         c->n_committed = 0;      // no extrapolation history across a reset
         c->ws.hist = 0;
         c->mixed_fallback = false;
+        precise_default(c);
     }
     return EP_OK;
 }
@@ -927,6 +967,7 @@ ep_status ep_reset(void* ctx) {
     c->ws.hist = 0;
     c->ws.uL_valid = false;
     c->mixed_fallback = false;
+    precise_default(c);
     return EP_OK;
 }
 
@@ -993,6 +1034,8 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
         return EP_ERR_INVALID_ARG;
     }
     cudaSetDevice(c->device);
+    c->deterministic = opts->deterministic ? 1 : 0;
+    c->amg.deterministic = c->deterministic;
     if (opts->precond == 2) {
         ep_status st = ensure_amg(c);
         if (st != EP_OK) return st;
@@ -1182,6 +1225,8 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     c->profile = o.profile;
     c->kw.profile = o.profile;
     c->amg.profile = o.profile;
+    c->deterministic = o.deterministic ? 1 : 0;
+    c->amg.deterministic = c->deterministic;
     c->kw.verbose = c->verbose;
     for (int k = 0; k < n_steps; ++k) {
         const auto t_step0 = std::chrono::steady_clock::now();
@@ -1404,7 +1449,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
             // the mixed path's FP64-tangent iterations solve with GMRES on the FP64 operator and an
             // FP32 basis (orthogonalisation, preconditioner and basis in FP32)
-            const bool basis32 = mixed && !use32 && m_it == 3;
+            const bool basis32 = mixed && !use32 && m_it == 3 && !c->amg.precise;
             // an FP32 inner solve cannot go much below FP32 rounding; Newton (FP64 residual) refines further
             if (use32 || basis32) eta = std::max(eta, MIXED_ETA_MIN);
             // this solve aims at the final tolerance (its forcing term is the floor eta_min) after a
@@ -1423,6 +1468,12 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             const bool tangent_elastic = split && np_now == 0;
             if (tangent_elastic) c->kw.galerkin = c->amg_elastic ? 0 : 1;
             else c->kw.galerkin = (c->amg_elastic || it == 0 || std::llabs(np_now - c->amg_np) * 20 > c->n_int) ? 1 : 0;
+            if (c->deterministic && it == 0) {
+                // a step's preconditioner depends on nothing before the step: coarse operators from
+                // this tangent, spectral estimate from the fixed start vector
+                c->kw.galerkin = 1;
+                c->amg.pw0_valid = false;
+            }
             if (c->kw.galerkin) {
                 c->amg_elastic = tangent_elastic;
                 c->amg_np = np_now;
@@ -1451,9 +1502,28 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 // inside Newton a solve that needs far more than the usual count is not worth
                 // finishing: its partial progress is taken as an inexact step
                 const int maxit64 = std::min(o.krylov_maxit, std::max(2000, 20 * c->kw.last_its));
+                c->kw.stall_guard64 = (o.precond == 2 && c->amg_built && !c->amg.precise && m_it == 3) ? 1 : 0;
                 CK(krylov_precond(A, c->kw, o.precond, s));
                 CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &kits, &krel, &kst));
+                c->kw.stall_guard64 = 0;
+                if (kst == EP_ERR_KRYLOV && o.precond == 2 && c->amg_built && !c->amg.precise && m_it == 3) {
+                    // the FP32 coarse correction cannot resolve this tangent's soft modes (a limit
+                    // load is near): FP64 coarse operators and residuals for the rest of the path
+                    c->amg.precise = 1;
+                    c->kw.galerkin = 1;
+                    c->amg_np = np_now;
+                    c->amg_elastic = false;
+                    if (c->verbose)
+                        std::fprintf(stderr, "[ep] step %d: FP32 V-cycle stalled (rel %.3e after %d), precise V-cycle from here\n",
+                                     k, krel, kits);
+                    int k2 = 0;
+                    CK(krylov_precond(A, c->kw, o.precond, s));
+                    CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &k2, &krel, &kst));
+                    kits += k2;
+                    rep.precise = 1;
+                }
             }
+            if (c->amg.precise) rep.precise = 1;
             c->kw.stall_guard = 0;
             CK(cudaEventRecord(c->ev[3], s));
             rep.krylov_its += kits;

@@ -98,6 +98,11 @@ struct AsmArgs {
     // split mode with want_K: every slot a plastic element adds to is marked 1 here (may be null)
     uint8_t* dirty;
     unsigned long long* n_plastic_elem;   // device counter of elements with a plastic point (may be null)
+    // deterministic form: the launch covers the list_n elements elem_list[0 .. list_n) (one colour:
+    // no two share a node) and adds into F and K with plain stores; null = elements 0 .. n_elem
+    // in order, FP64/FP32 atomics
+    const int32_t* elem_list;
+    int64_t list_n;
 };
 cudaError_t launch_assemble(int elem_id, const AsmArgs& a, cudaStream_t s);
 
@@ -146,6 +151,12 @@ void reference_tables(int family, int dim, std::vector<double>& dhat, std::vecto
 // invalid node indices.
 bool build_pattern(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem, std::vector<int32_t>& row_ptr,
                    std::vector<int32_t>& col_idx, std::vector<int32_t>& slots, std::string& err);
+
+// Element colouring (pattern_host.cpp): elements of one colour share no node.  color_ptr
+// [n_colors + 1], color_elems [n_elem] (the elements of colour c are color_elems[color_ptr[c] ..
+// color_ptr[c + 1]), in increasing order).  Returns false on invalid node indices.
+bool color_elements(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem, std::vector<int32_t>& color_ptr,
+                    std::vector<int32_t>& color_elems, std::string& err);
 
 // ---------------------------------------------------------------------------
 // Krylov solver on the block-CSR matrix (krylov.cu).
@@ -205,6 +216,7 @@ struct KrylovWork {
     int galerkin;            // 1: recompute the AMG coarse operators from the current matrix in krylov_precond
     int last_its;            // iterations of the previous solve: sizes the first chunk of launches of the next
     int stall_guard;         // 1: an FP32-basis GMRES stops when a restart cycle does not halve the residual
+    int stall_guard64;       // 1: an FP64 GMRES stops when a restart cycle after the first gains less than 10%
     // instrumentation
     int profile;             // 1: CUDA events around every SpMV launch
     int verbose;             // 2: per-cycle host enqueue / wait times on stderr

@@ -1156,6 +1156,9 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
         // an FP32-basis solve whose restart cycle did not halve the residual has reached what its
         // rounding allows on this matrix: stop (the caller treats it as an inexact or failed solve)
         if (sizeof(TV) == 4 && w.stall_guard && last.rr > 0.25 * (cycle == 0 ? last.rr0 : rr_prev_end)) break;
+        // an FP64 solve whose preconditioner no longer resolves the matrix: stop early (the caller
+        // switches to the precise V-cycle)
+        if (sizeof(TV) == 8 && w.stall_guard64 && cycle >= 1 && last.rr > 0.81 * rr_prev_end) break;
         rr_prev_end = last.rr;
     }
     *its = total;

@@ -86,4 +86,53 @@ bool build_pattern(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem
     return true;
 }
 
+// Element colouring for the deterministic assembly: elements of one colour share no node, so
+// within a colour every F entry and every K block receives at most one contribution and plain
+// read-modify-write stores replace atomics.  Greedy, in element order (the smallest colour not
+// used by an already coloured element sharing a node).  color_ptr [n_colors + 1] and color_elems
+// [n_elem] list the elements of each colour in increasing order.
+bool color_elements(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem, std::vector<int32_t>& color_ptr,
+                    std::vector<int32_t>& color_elems, std::string& err) {
+    for (int64_t i = 0; i < n_elem * n_p; ++i)
+        if (elem[i] < 0 || elem[i] >= n_nodes) {
+            err = "colouring: node index out of range";
+            return false;
+        }
+    std::vector<int64_t> inc_ptr(n_nodes + 1, 0);
+    for (int64_t i = 0; i < n_elem * n_p; ++i) inc_ptr[elem[i] + 1]++;
+    for (int64_t n = 0; n < n_nodes; ++n) inc_ptr[n + 1] += inc_ptr[n];
+    std::vector<int32_t> inc(inc_ptr[n_nodes]);
+    {
+        std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+        for (int64_t e = 0; e < n_elem; ++e)
+            for (int p = 0; p < n_p; ++p) inc[fill[elem[e * n_p + p]]++] = (int32_t)e;
+    }
+    std::vector<int32_t> color(n_elem, -1);
+    std::vector<int64_t> stamp;   // stamp[c] == e: colour c is used by a neighbour of e
+    int n_colors = 0;
+    for (int64_t e = 0; e < n_elem; ++e) {
+        for (int p = 0; p < n_p; ++p) {
+            const int32_t v = elem[e * n_p + p];
+            for (int64_t k = inc_ptr[v]; k < inc_ptr[v + 1]; ++k) {
+                const int32_t c = color[inc[k]];
+                if (c >= 0) stamp[c] = e;
+            }
+        }
+        int c = 0;
+        while (c < n_colors && stamp[c] == e) ++c;
+        if (c == n_colors) {
+            ++n_colors;
+            stamp.push_back(-1);
+        }
+        color[e] = c;
+    }
+    color_ptr.assign(n_colors + 1, 0);
+    for (int64_t e = 0; e < n_elem; ++e) color_ptr[color[e] + 1]++;
+    for (int c = 0; c < n_colors; ++c) color_ptr[c + 1] += color_ptr[c];
+    color_elems.resize(n_elem);
+    std::vector<int32_t> fill(color_ptr.begin(), color_ptr.end() - 1);
+    for (int64_t e = 0; e < n_elem; ++e) color_elems[fill[color[e]]++] = (int32_t)e;
+    return true;
+}
+
 }  // namespace ep

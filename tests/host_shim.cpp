@@ -23,6 +23,18 @@ int shim_build_pattern(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* 
     return 1;
 }
 
+// Element colouring: color_ptr [n_elem + 1] (first n_colors + 1 entries used), color_elems [n_elem];
+// returns n_colors, or 0 when the builder rejects the mesh.
+int shim_color_elements(int64_t n_nodes, int64_t n_elem, int n_p, const int32_t* elem, int32_t* color_ptr,
+                        int32_t* color_elems) {
+    std::vector<int32_t> cp, ce;
+    std::string err;
+    if (!ep::color_elements(n_nodes, n_elem, n_p, elem, cp, ce, err)) return 0;
+    std::copy(cp.begin(), cp.end(), color_ptr);
+    std::copy(ce.begin(), ce.end(), color_elems);
+    return (int)cp.size() - 1;
+}
+
 // dhat [n_q][n_p][dim] and wq [n_q]; returns n_q, or -1 when a buffer is too small.
 int shim_reference_tables(int family, int dim, double* dhat, int64_t cap_dhat, double* wq, int64_t cap_wq) {
     std::vector<double> d, w;

@@ -37,6 +37,7 @@ def shim(tmp_path_factory):
     lib.shim_build_pattern.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_void_p, C.POINTER(C.c_int64)]
     lib.shim_reference_tables.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
+    lib.shim_color_elements.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.shim_amg_setup.argtypes = [C.c_int, C.c_int64] + [C.c_void_p] * 5
     lib.shim_amg_setup.restype = C.c_void_p
     lib.shim_amg_free.argtypes = [C.c_void_p]
@@ -84,6 +85,31 @@ def test_pattern_is_the_node_adjacency_and_slots_point_at_their_pairs(shim, elem
             for q in range(n_p):
                 k = sl[e, p, q]
                 assert rp[nodes[p]] <= k < rp[nodes[p] + 1] and ci[k] == nodes[q]
+
+
+@pytest.mark.parametrize("elem_type,dim", ALL)
+def test_element_colouring_separates_elements_sharing_a_node(shim, elem_type, dim):
+    """Deterministic assembly: within a colour no two elements share a node (so plain adds into F and
+    K cannot collide), every element has exactly one colour, and each colour lists its elements in
+    increasing order."""
+    m = structured_mesh(elem_type, dim, (5, 4) if dim == 2 else (3, 3, 2), (10.0,) * dim)
+    elem = np.ascontiguousarray(m.elem, dtype=np.int32)
+    n_e, n_p = elem.shape
+    cp = np.zeros(n_e + 1, dtype=np.int32)
+    ce = np.zeros(n_e, dtype=np.int32)
+    nc = shim.shim_color_elements(m.n_nodes, n_e, n_p, elem.ctypes.data, cp.ctypes.data, ce.ctypes.data)
+    assert nc >= 2
+    cp = cp[:nc + 1]
+    assert cp[0] == 0 and cp[-1] == n_e
+    assert np.array_equal(np.sort(ce), np.arange(n_e))
+    for c in range(nc):
+        els = ce[cp[c]:cp[c + 1]]
+        assert np.all(np.diff(els) > 0)
+        nodes = elem[els].ravel()
+        assert len(np.unique(nodes)) == len(nodes), f"colour {c} has elements sharing a node"
+    # greedy bound: at most (elements sharing a node with one element) + 1 colours
+    adj = max(len(set(np.nonzero(np.isin(elem, elem[e]).any(axis=1))[0])) for e in range(n_e))
+    assert nc <= adj
 
 
 def test_pattern_rejects_a_node_index_out_of_range(shim):
