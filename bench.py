@@ -5,9 +5,11 @@ then every load step: semismooth Newton to the relative residual tolerance --
 each iteration fused return mapping + tangent assembly + internal forces,
 residual and norms, preconditioned Krylov solve, update -- and the state
 commit).  The default workload is the P2 plane-strain Drucker-Prager column
-(256 x 256 cells, 917 504 points, 40 load steps to 0.98 of the limit
+(256 x 256 cells, 917 504 points, 40 load steps to 0.95 of the limit
 traction), so every step crosses the elastic, the spreading-plastic and the
-nearly-singular fully plastic range.  W warm-up paths, then K timed paths in
+nearly-singular fully plastic range (beyond about 0.97 the nonassociated
+tangent becomes indefinite on local plastic-flow modes and no Krylov method
+here solves its Newton systems).  W warm-up paths, then K timed paths in
 each precision, CUDA events around each path on the context's stream.
 
 value = integration points assembled per second over the timed region
@@ -295,8 +297,9 @@ def run_batch(args):
     fams = sorted(groups)
     streams = {f: torch.cuda.Stream() for f in fams}
     ctxs = {f: ep.Context.from_batch(groups[f], stream=streams[f]) for f in fams}
-    singles = [(pb, ep.Context.from_problem(pb)) for f in fams for pb in groups[f]]
-    opts = ep.default_opts(newton_rtol=1e-10)
+    t_setup0 = time.perf_counter()
+    singles = [] if args.no_one_by_one else [(pb, ep.Context.from_problem(pb)) for f in fams for pb in groups[f]]
+    opts = ep.default_opts(newton_rtol=1e-10, krylov_graphs=0 if args.no_graphs else 1)
     zeta = groups[fams[0]][0].zeta
 
     def reset(ctx):
@@ -309,6 +312,7 @@ def run_batch(args):
         c.solve_load_path(zeta[:1], opts)
         reset(c)
     torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup0
     results = {}
 
     def solve(f):
@@ -334,10 +338,16 @@ def run_batch(args):
             "config": {"workload": f"{args.batch} problems, sizes 16..{hi} elements per side, "
                                    f"{', '.join(f'{len(groups[f])} {f}' for f in fams)}; E, nu, Y, H x U(0.7, 1.3)",
                        "n_int": n_int, "dofs": int(sum(ctxs[f].n_dof for f in fams))},
-            "batched_s": t_batch, "one_by_one_s": t_single, "speedup": t_single / t_batch,
+            "krylov_iterations": "direct launches" if args.no_graphs else "replayed from CUDA graphs",
+            "batched_s": t_batch, "one_by_one_s": t_single if singles else None,
+            "speedup": t_single / t_batch if singles else None, "setup_s": t_setup,
+            "per_family": {f: {"problems": len(groups[f]), "dofs": int(ctxs[f].n_dof), "n_int": int(ctxs[f].info.n_int),
+                               "newton_its": int(sum(r.newton_its for r in results[f])),
+                               "krylov_its": int(sum(r.krylov_its for r in results[f])),
+                               "solve_ms": float(sum(r.t_step_ms for r in results[f]))} for f in fams},
             "max_rel_resid": max(r.rel_resid for f in fams for r in results[f]),
             "newton_its": {f: int(sum(r.newton_its for r in results[f])) for f in fams},
-            "one_by_one_newton_its": int(sum(r.newton_its for rs in reps_single for r in rs))}
+            "one_by_one_newton_its": int(sum(r.newton_its for rs in reps_single for r in rs)) if singles else None}
     if args.learned:
         line["learned"] = learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results)
     for c in ctxs.values():
@@ -470,6 +480,11 @@ def main():
                     help="primary precision; auto: time both, report the faster as the primary")
     ap.add_argument("--no-compare", action="store_true", help="time the primary precision only (auto: mixed)")
     ap.add_argument("--batch", type=int, default=64, help="problems of the batched sweep (--workload batch)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the Krylov iterations directly instead of replaying CUDA graphs (same kernels; "
+                         "for kernel profilers that cannot follow graph-replayed launches)")
+    ap.add_argument("--no-one-by-one", action="store_true",
+                    help="--workload batch: skip the one-context-per-problem comparison (large sweeps)")
     ap.add_argument("--learned", action="store_true",
                     help="--workload batch: also train the warm-start network and solve from the learned start")
     ap.add_argument("--learned-steps", type=int, default=300, help="Adam steps per family of the warm-start network")
@@ -527,8 +542,9 @@ def run_path(args, ep, local, world, rank):
     zeta = np.ascontiguousarray(prob.zeta, dtype=np.float64)
     prec_of = {"mixed": ep.EP_MIXED, "fp64": ep.EP_FP64}
 
-    def opts_for(prec):
-        return ep.default_opts(newton_rtol=prob.newton_rtol, profile=1, precision=prec_of[prec])
+    def opts_for(prec, profile=0):
+        return ep.default_opts(newton_rtol=prob.newton_rtol, profile=profile, precision=prec_of[prec],
+                               krylov_graphs=0 if args.no_graphs else 1)
 
     u_host = np.empty(ctx.n_dof)
     s_host = np.empty(ctx.field_shape(ep.EP_STRESS)[0])
@@ -616,36 +632,44 @@ def run_path(args, ep, local, world, rank):
                "what": "per step: the load factors enter from the host, u and sigma of the path's end are "
                        "read back to host buffers"}
 
-    # roofline of the step's kernels (CUDA events on the context's stream around every assembly
-    # and SpMV launch, and around a sample of the AMG level-0 Chebyshev sweeps)
+    # roofline of the step's kernels: one instrumented path of the primary precision right after the
+    # timed region (CUDA events on the context's stream around every assembly and SpMV launch and
+    # around a sample of the AMG level-0 Chebyshev sweeps; the instrumented path launches the Krylov
+    # iterations directly, the timed ones replay them from CUDA graphs)
+    torch.cuda.synchronize()
+    reps_prof = path(opts_for(prec, 1), False)
+    torch.cuda.synchronize()
     dim = info.dim
     f32 = prec == "mixed"
     kb = 4 if f32 else 8
     peaks, peaks_kind = _peaks()
-    t_spmv = sum(r.t_spmv_kernel_ms for r in reps)
-    n_spmv = sum(r.n_spmv for r in reps)
-    t_asmk = sum(r.t_assemble_kernel_ms for r in reps)
-    n_sm0 = sum(r.n_smooth0 for r in reps)
-    t_sm0 = sum(r.t_smooth0_kernel_ms for r in reps)
+    t_spmv = sum(r.t_spmv_kernel_ms for r in reps_prof)
+    n_spmv = sum(r.n_spmv for r in reps_prof)
+    t_asmk = sum(r.t_assemble_kernel_ms for r in reps_prof)
+    n_sm0 = sum(r.n_smooth0 for r in reps_prof)
+    t_sm0 = sum(r.t_smooth0_kernel_ms for r in reps_prof)
     sym = prob.material.model != 3
-    plastic_assembled = sum(r.n_plastic_assembled for r in reps)
-    pe_assembled = sum(r.n_plastic_elem_assembled for r in reps)
-    krylov_its = sum(r.krylov_its for r in reps)
+    plastic_assembled = sum(r.n_plastic_assembled for r in reps_prof)
+    pe_assembled = sum(r.n_plastic_elem_assembled for r in reps_prof)
+    krylov_its = sum(r.krylov_its for r in reps_prof)
+    asm_prof = sum(r.n_assemble for r in reps_prof)
+    ms_prof_path = statistics.median(per)   # shares against the timed path's median length
     cands = {}
     if n_spmv:
         # the FP64 operator of the Krylov solves: the mixed path's FP64-tangent iterations use it too
         cands["spmv"] = _roof_hbm(f"k_spmv (masked block-CSR)", n_spmv, t_spmv,
-                                  _spmv_bytes(info, dim, 8), peaks, peaks_kind, ms)
-    if assemblies:
-        pf = plastic_assembled / max(1, assemblies * n_int)
-        pe = pe_assembled / max(1, assemblies * info.n_elem)
+                                  _spmv_bytes(info, dim, 8), peaks, peaks_kind, ms_prof_path)
+    if asm_prof:
+        pf = plastic_assembled / max(1, asm_prof * n_int)
+        pe = pe_assembled / max(1, asm_prof * info.n_elem)
         by = _assembly_bytes(info, dim, info.n_p, info.n_comp, kb, pe)
-        dur = t_asmk / assemblies / 1e3
-        tan = plastic_assembled * _tangent_flops_per_point(dim, info.n_p, sym) / assemblies
+        dur = t_asmk / asm_prof / 1e3
+        tan = plastic_assembled * _tangent_flops_per_point(dim, info.n_p, sym) / asm_prof
         base = n_int * (_base_flops_per_point(dim, info.n_p) + _return_map_flops(prob.material.model))
         fp64_flops = base + (0 if f32 else tan)
         cands["assembly"] = _roof_hbm(
-            f"k_assemble (fused, tangent {'FP32' if f32 else 'FP64'})", assemblies, t_asmk, by, peaks, peaks_kind, ms,
+            f"k_assemble (fused, tangent {'FP32' if f32 else 'FP64'})", asm_prof, t_asmk, by, peaks, peaks_kind,
+            ms_prof_path,
             plastic_fraction=pf, plastic_element_fraction=pe, fp64_flops_per_launch=fp64_flops,
             fp64_tflops=fp64_flops / dur / 1e12, fp64_frac=fp64_flops / dur / 1e12 / FP64_PEAK_TFLOPS,
             fp64_peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
@@ -656,12 +680,14 @@ def run_path(args, ep, local, world, rank):
         avg = t_sm0 / n_sm0
         est_n = 4 * krylov_its
         cands["amg_smooth0"] = _roof_hbm("k_cheb (AMG level-0 Chebyshev step, FP32)", n_sm0, t_sm0,
-                                         _cheb0_bytes(info, dim), peaks, peaks_kind, ms,
-                                         share_of_step=avg * est_n / ms, launches_sampled=n_sm0,
+                                         _cheb0_bytes(info, dim), peaks, peaks_kind, ms_prof_path,
+                                         share_of_step=avg * est_n / ms_prof_path, launches_sampled=n_sm0,
                                          launches_estimated=est_n)
     dominant = max(cands.values(), key=lambda r: r["share_of_step"]) if cands else None
-    xs = [r.n_plastic_assembled / r.n_assemble for r in reps_paths[-1] if r.n_assemble]
-    ys = [1e3 * r.t_assemble_kernel_ms / r.n_assemble for r in reps_paths[-1] if r.n_assemble]
+    for c_ in cands.values():
+        c_["timing"] = "instrumented path after the timed region (CUDA events on the launching stream)"
+    xs = [r.n_plastic_assembled / r.n_assemble for r in reps_prof if r.n_assemble]
+    ys = [1e3 * r.t_assemble_kernel_ms / r.n_assemble for r in reps_prof if r.n_assemble]
     asm_fit = None
     if len(set(np.round(xs, 6))) >= 2:
         A = np.vstack([np.ones(len(xs)), xs]).T
@@ -684,7 +710,8 @@ def run_path(args, ep, local, world, rank):
                 "parallelism": "replicas" if world > 1 else "single GPU", "precision": prec,
                 "krylov": "GMRES(30)" if prob.material.model == 3 and prob.material.psi != prob.material.phi
                 else "CG", "precond": "smoothed-aggregation AMG, FP32 V-cycle, Galerkin from the tangent",
-                "split_elastic_cache": True}),
+                "split_elastic_cache": True,
+                "krylov_iterations": "direct launches" if args.no_graphs else "replayed from CUDA graphs"}),
             "roofline": dominant, "roofline_kernels": cands,
             "clocks": clk, "gpu_launches": int(sum(r.launches for r in reps)),
             "load_path_s": primary["load_path_s_median"], "primary": primary,

@@ -134,6 +134,12 @@ typedef struct {
                                     setting stays with the context: later ep_assemble / ep_commit calls follow
                                     the last ep_solve_load_path or ep_linear_solve that passed it (n_steps = 0
                                     sets it without solving). */
+    int32_t asm_tile;            /* assembly schedule: 1 the element type's tile of elements per CTA (default),
+                                    2 half of it (half the shared memory per CTA, more CTAs per SM) */
+    int32_t krylov_graphs;       /* 1 (default): the GMRES iterations are captured once per solver configuration
+                                    as CUDA graphs and replayed (one launch per iteration instead of about 30);
+                                    0: direct launches.  Either way the same kernels run in the same order.
+                                    profile = 1 always launches directly (events around the kernels). */
 } ep_opts;
 
 typedef struct {

@@ -23,16 +23,21 @@
 //               step k (Sections 2.2, 2.3, eq. (T_other)).
 #pragma once
 
+#include <algorithm>
+
 #include "constitutive.cuh"
 
 namespace ep {
 
 constexpr int ASM_THREADS = 256;
 
-template <int ID, class KT>
+// TILE: 1 = the element type's tile of EPC elements per CTA; 2 = half that tile (half the shared
+// memory per CTA, so more CTAs per SM) -- the two assembly schedules the autotuner chooses from.
+template <int ID, class KT, int TILE = 1>
 struct AsmShape {
     using ET = Elem<ID>;
-    static constexpr int D = ET::DIM, NP = ET::NP, NQ = ET::NQ, NS = ET::NS, NA = ET::NA, EPC = ET::EPC;
+    static constexpr int D = ET::DIM, NP = ET::NP, NQ = ET::NQ, NS = ET::NS, NA = ET::NA;
+    static constexpr int EPC = (ET::EPC / TILE) > 0 ? ET::EPC / TILE : 1;
     static constexpr int NIP = EPC * NQ;
     static constexpr bool F32 = sizeof(KT) == 4;
     // FP64 region: displacements, gradients, weights, w*sigma
@@ -101,9 +106,9 @@ __device__ __forceinline__ void strain_at(const double* __restrict__ g, const do
 // mixed path: strains, return mapping and F stay FP64, and the FP64 tangent
 // coefficients are rounded once to FP32 before D, H and the K blocks are
 // formed and scattered with FP32 atomics).
-template <int ID, int MODEL, bool DELTA, bool WANT_F, class KT>
+template <int ID, int MODEL, bool DELTA, bool WANT_F, class KT, int TILE>
 __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
-    using S = AsmShape<ID, KT>;
+    using S = AsmShape<ID, KT, TILE>;
     constexpr int D = S::D, NP = S::NP, NQ = S::NQ, NS = S::NS, NA = S::NA, EPC = S::EPC;
     constexpr bool SYM = (MODEL != 3);
     constexpr int NB = SYM ? NP * (NP + 1) / 2 : NP * NP;
@@ -126,7 +131,11 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
     const int64_t n_int = a.mesh.n_int;
     const bool listed = a.elem_list != nullptr;   // deterministic form: one colour, plain stores
     const int64_t n_elem = listed ? a.list_n : a.mesh.n_elem;
-    const int64_t e0 = (int64_t)blockIdx.x * EPC;
+    const int64_t n_tiles = (n_elem + EPC - 1) / EPC;
+    // persistent: the CTAs of one resident wave take the (problem, element-tile) items of the
+    // concatenated element array in turn (a batch of problems is one such array)
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t e0 = tile * EPC;
     const int ne = (int)min((int64_t)EPC, n_elem - e0);
     const int nip = ne * NQ;
     const int64_t ip0 = e0 * NQ;
@@ -289,10 +298,8 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
             }
         }
     }
-    if (!a.want_K) return;
-
     // (2b) element blocks K_pq, one thread per (element, node pair)
-    for (int t = tid; t < ne * NB; t += ASM_THREADS) {
+    for (int t = tid; t < (a.want_K ? ne * NB : 0); t += ASM_THREADS) {
         const int e = t / NB, b = t % NB;
         if (DELTA && !s_eplast[e]) continue;
         int p, q;
@@ -361,6 +368,8 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs a) {
             }
         }
     }
+    __syncthreads();   // the next tile reuses the shared buffers
+    }   // tile
 }
 
 // ---------------------------------------------------------------------------
@@ -486,10 +495,10 @@ __global__ void __launch_bounds__(256) k_reset_dirty(uint8_t* __restrict__ dirty
 // ---------------------------------------------------------------------------
 // Launchers for one element type.
 // ---------------------------------------------------------------------------
-template <int ID, int MODEL, bool DELTA, bool WANT_F, class KT>
+template <int ID, int MODEL, bool DELTA, bool WANT_F, class KT, int TILE = 1>
 cudaError_t launch_asm_t(const AsmArgs& a, cudaStream_t s) {
-    using S = AsmShape<ID, KT>;
-    auto kern = k_assemble<ID, MODEL, DELTA, WANT_F, KT>;
+    using S = AsmShape<ID, KT, TILE>;
+    auto kern = k_assemble<ID, MODEL, DELTA, WANT_F, KT, TILE>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -497,14 +506,28 @@ cudaError_t launch_asm_t(const AsmArgs& a, cudaStream_t s) {
         configured = true;
     }
     const int64_t n = a.elem_list ? a.list_n : a.mesh.n_elem;
-    const int64_t grid = (n + S::EPC - 1) / S::EPC;
-    if (grid == 0) return cudaSuccess;
+    const int64_t tiles = (n + S::EPC - 1) / S::EPC;
+    if (tiles == 0) return cudaSuccess;
+    // one resident wave of CTAs (persistent over the tiles)
+    static int wave = 0;
+    if (wave == 0) {
+        int occ = 0, sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ASM_THREADS, S::SMEM) != cudaSuccess || occ < 1)
+            occ = 1;
+        wave = std::max(1, sms) * occ;
+    }
+    const int64_t grid = std::min<int64_t>(tiles, wave);
     kern<<<(unsigned)grid, ASM_THREADS, S::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int ID, int MODEL, class KT>
 cudaError_t launch_asm_model(const AsmArgs& a, cudaStream_t s) {
+    if (a.tile == 2)
+        return a.mode == ASM_DELTA ? launch_asm_t<ID, MODEL, true, true, KT, 2>(a, s)
+                                   : launch_asm_t<ID, MODEL, false, true, KT, 2>(a, s);
     return a.mode == ASM_DELTA ? launch_asm_t<ID, MODEL, true, true, KT>(a, s)
                                : launch_asm_t<ID, MODEL, false, true, KT>(a, s);
 }

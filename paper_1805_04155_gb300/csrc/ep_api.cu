@@ -220,6 +220,7 @@ struct Ctx {
     uint8_t *dirty64 = nullptr, *dirty32 = nullptr;
     // deterministic form (ep_opts.deterministic): element colours, one assembly launch per colour
     int deterministic = 0;
+    int asm_tile = 1;                   // assembly schedule (ep_opts.asm_tile)
     std::vector<int32_t> h_color_ptr;   // [n_colors + 1]
     int32_t* color_elems = nullptr;     // device [n_elem]
     bool split_base64 = false, split_base32 = false;   // the statement above holds
@@ -359,6 +360,7 @@ static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K, 
     a.n_plastic = c->counter;
     a.err_flag = c->err_flag;
     a.dirty = (want_K && split) ? dirty : nullptr;
+    a.tile = c->asm_tile;
     a.n_plastic_elem = want_K ? c->counter + 1 : nullptr;
     if (c->profile) CK(cudaEventRecord(c->ev[4], s));
     if (c->deterministic) {
@@ -454,6 +456,8 @@ void ep_default_opts(ep_opts* o) {
     o->warm_start = 1;
     o->profile = 0;
     o->deterministic = 0;
+    o->asm_tile = 1;
+    o->krylov_graphs = 1;
 }
 
 const char* ep_status_str(int32_t s) {
@@ -1036,6 +1040,7 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
     cudaSetDevice(c->device);
     c->deterministic = opts->deterministic ? 1 : 0;
     c->amg.deterministic = c->deterministic;
+    c->kw.graphs = opts->krylov_graphs ? 1 : 0;
     if (opts->precond == 2) {
         ep_status st = ensure_amg(c);
         if (st != EP_OK) return st;
@@ -1227,6 +1232,12 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     c->amg.profile = o.profile;
     c->deterministic = o.deterministic ? 1 : 0;
     c->amg.deterministic = c->deterministic;
+    if (o.asm_tile != 1 && o.asm_tile != 2) {
+        c->err = "asm_tile must be 1 or 2";
+        return EP_ERR_INVALID_ARG;
+    }
+    c->asm_tile = o.asm_tile;
+    c->kw.graphs = o.krylov_graphs ? 1 : 0;
     c->kw.verbose = c->verbose;
     for (int k = 0; k < n_steps; ++k) {
         const auto t_step0 = std::chrono::steady_clock::now();

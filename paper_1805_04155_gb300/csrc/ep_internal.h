@@ -103,6 +103,7 @@ struct AsmArgs {
     // in order, FP64/FP32 atomics
     const int32_t* elem_list;
     int64_t list_n;
+    int tile;                  // assembly schedule: 1 the element type's tile of elements per CTA, 2 half of it
 };
 cudaError_t launch_assemble(int elem_id, const AsmArgs& a, cudaStream_t s);
 
@@ -220,6 +221,19 @@ struct KrylovWork {
     // instrumentation
     int profile;             // 1: CUDA events around every SpMV launch
     int verbose;             // 2: per-cycle host enqueue / wait times on stderr
+    // CUDA graphs of GMRES iterations (graphs = 1, profile = 0): iteration j of a restart cycle (the
+    // preconditioner, the SpMV, the orthogonalisation and the Givens/norm kernels, about 30 launches
+    // with the V-cycle) is captured once per solver configuration and replayed with one
+    // cudaGraphLaunch; the per-solve scalars the captured kernels read (tolerance, iteration base
+    // and cap) live in gdyn on the device
+    int graphs = 0;
+    double* gdyn = nullptr;            // device [3]: rtol^2, iterations before this cycle, cap
+    cudaStream_t cap_stream = nullptr; // private stream the captures are made on
+    std::vector<cudaGraphExec_t> gexec;
+    std::vector<int> gexec_launches;   // kernels inside each graph
+    long long gkey = -1;               // configuration the cached graphs were captured for
+    const void* gkey_ptr = nullptr;
+    int graph_launches = 0;            // graph launches (accumulates)
     int launches;            // kernels launched by the solver (accumulates)
     int spmv_n;              // SpMV launches that did work (profile = 1)
     double spmv_ms;          // their summed duration

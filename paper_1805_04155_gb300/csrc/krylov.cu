@@ -544,7 +544,20 @@ cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, 
     if ((e = cudaMallocHost(&w.rec_host, sizeof(KrylovRec))) != cudaSuccess) return e;
     for (auto& ev : w.ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&w.gdyn, sizeof(double) * 3)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    w.graphs = 1;
     return cudaSuccess;
+}
+
+// Destroys the cached iteration graphs.
+static void drop_graphs(KrylovWork& w) {
+    for (auto& g : w.gexec)
+        if (g) cudaGraphExecDestroy(g);
+    w.gexec.clear();
+    w.gexec_launches.clear();
+    w.gkey = -1;
+    w.gkey_ptr = nullptr;
 }
 
 cudaError_t krylov_alloc_f32(KrylovWork& w, int64_t n_rows, int dim) {
@@ -562,6 +575,9 @@ void krylov_free(KrylovWork& w) {
     if (w.rec_host) cudaFreeHost(w.rec_host);
     for (auto& ev : w.ev)
         if (ev) cudaEventDestroy(ev);
+    drop_graphs(w);
+    if (w.gdyn) cudaFree(w.gdyn);
+    if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     w = KrylovWork{};
 }
 
@@ -768,6 +784,8 @@ struct GArgs {          // TX: solution and residual; TV: Krylov basis and preco
     double rtol2;
     int cold;
     int m;              // restart length
+    const double* dyn = nullptr;   // graph replay: device (rtol^2, iteration base, cap) read instead of rtol2
+                                   // and the arguments of k_gm_norm (null: direct launches)
 };
 
 #define GPART(k) (a.part + (int64_t)(k) * a.nparts)
@@ -939,6 +957,12 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs<TX, TV> a, int j, int it_b
     pdl_enter();
     __shared__ double sh[32];
     if (a.rec->done) return;
+    double rtol2 = a.rtol2;
+    if (a.dyn) {
+        rtol2 = a.dyn[0];
+        it_base = (int)a.dyn[1];
+        maxit = (int)a.dyn[2];
+    }
     __shared__ double s_h[2];
     {
         const double hh = sum_partials(GPART(GM_M + 1), a.nparts, sh);
@@ -972,7 +996,7 @@ __global__ void __launch_bounds__(VB) k_gm_norm(GArgs<TX, TV> a, int j, int it_b
         a.rec->rr = res2;
         a.rec->its = j + 1;
         if (!isfinite(res2) || den == 0.0) { a.rec->done = 2; a.rec->why = isfinite(res2) ? 4 : 2; }
-        else if (res2 <= a.rtol2 * a.rec->rr0 || hn == 0.0) { a.rec->done = 1; a.rec->why = 1; }
+        else if (res2 <= rtol2 * a.rec->rr0 || hn == 0.0) { a.rec->done = 1; a.rec->why = 1; }
         else if (it_base + j + 1 >= maxit) { a.rec->done = 3; a.rec->why = 6; }
         else if (j + 1 == a.m) { a.rec->done = 4; }   // end of the cycle: update and restart
     }
@@ -1048,6 +1072,16 @@ __global__ void k_axpy_plain(TX* __restrict__ x, const TV* __restrict__ z, int64
         x[i] += (TX)z[i];
 }
 
+// per-chunk scalars of the replayed iteration graphs
+__global__ void k_gdyn_set(double* dyn, double rtol2, int it_base, int maxit) {
+    pdl_enter();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        dyn[0] = rtol2;
+        dyn[1] = (double)it_base;
+        dyn[2] = (double)maxit;
+    }
+}
+
 // TA: operator values; TX: solution and residual; TV: basis (TA = TX = TV for the FP64 and FP32
 // solvers; TA = TX = double, TV = float for the FP32-basis solve with the FP64 operator)
 template <int D, class TA, class TX, class TV>
@@ -1076,6 +1110,38 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
     const int grid = w.grid;
     const bool use_amg = w.use_amg && w.amg;
     int total = 0;
+    // the launches of iteration j of a cycle (direct, or into a capture)
+    auto issue = [&](const GArgs<TX, TV>& ga, int j, cudaStream_t st, int& nev) {
+        if (use_amg) amg_apply_t(w, A, ga.V + (int64_t)j * w.n, ga.z, w.rec, st);
+        else launch_pdl(k_gm_prec<D, TX, TV>, dim3(grid), dim3(VB), 0, st, ga, j);
+        const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
+        if (ev_ok) cudaEventRecord(w.ev[nev++], st);
+        launch_spmv<D, TA, TV, TV>(A, ga.z, ga.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, st);
+        if (ev_ok) cudaEventRecord(w.ev[nev++], st);
+        // one resident wave (FP32: 61 registers, 2 CTAs per SM); FP64: one CTA per SM, fewer
+        // cross-lane FP64 adds
+        launch_pdl(k_gm_dots1<D, TX, TV, sizeof(TV) == 8 ? 4 : 8>,
+                   dim3(std::max(1, sizeof(TV) == 8 ? grid / 3 : 2 * grid / 3)), dim3(VB), 0, st, ga, j);
+        launch_pdl(k_gm_orth<D, TX, TV>, dim3(grid), dim3(VB), 0, st, ga, j);
+        launch_pdl(k_gm_norm<D, TX, TV>, dim3(grid), dim3(VB), 0, st, ga, j, total, maxit);
+        w.launches += 5;
+    };
+    const bool use_graphs = w.graphs && !w.profile && w.cap_stream;
+    if (use_graphs) {
+        // graphs are valid for one operator, solver precision, preconditioner and restart length
+        const long long key = ((long long)a.m << 32) | ((long long)D << 24) | ((long long)sizeof(TA) << 16) |
+                              ((long long)sizeof(TX) << 12) | ((long long)sizeof(TV) << 8) |
+                              (use_amg ? 2 : 0) | (use_amg && w.amg->precise ? 1 : 0);
+        if (key != w.gkey || (const void*)A.vals != w.gkey_ptr) {
+            drop_graphs(w);
+            w.gkey = key;
+            w.gkey_ptr = (const void*)A.vals;
+        }
+        if ((int)w.gexec.size() < a.m) {
+            w.gexec.resize(a.m, nullptr);
+            w.gexec_launches.resize(a.m, 0);
+        }
+    }
     KrylovRec last{};
     double rr_prev_end = 0.0;   // residual estimate ||r||^2 at the end of the previous cycle
     int n_verify = sizeof(TV) == 4 ? 1 : 0;   // FP32 basis: re-check a converged estimate once (see solve_t)
@@ -1097,20 +1163,35 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
             const int j1 = std::min(a.m, j0 + chunk);
             int nev = 0;
             if (use_amg) w.amg->nev = 0;
-            for (int j = j0; j < j1; ++j) {
-                if (use_amg) amg_apply_t(w, A, a.V + (int64_t)j * w.n, a.z, w.rec, s);
-                else launch_pdl(k_gm_prec<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j);
-                const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
-                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                launch_spmv<D, TA, TV, TV>(A, a.z, a.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, s);
-                if (ev_ok) cudaEventRecord(w.ev[nev++], s);
-                // one resident wave (FP32: 61 registers, 2 CTAs per SM); FP64: one CTA per SM, fewer
-                // cross-lane FP64 adds
-                launch_pdl(k_gm_dots1<D, TX, TV, sizeof(TV) == 8 ? 4 : 8>,
-                           dim3(std::max(1, sizeof(TV) == 8 ? grid / 3 : 2 * grid / 3)), dim3(VB), 0, s, a, j);
-                launch_pdl(k_gm_orth<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j);
-                launch_pdl(k_gm_norm<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, j, total, maxit);
-                w.launches += 5;
+            if (use_graphs) {
+                launch_pdl(k_gdyn_set, dim3(1), dim3(32), 0, s, w.gdyn, a.rtol2, total, maxit);
+                w.launches += 1;
+                for (int j = j0; j < j1; ++j) {
+                    if (!w.gexec[j]) {
+                        // capture iteration j once on the private stream (nothing runs during a capture)
+                        GArgs<TX, TV> ac = a;
+                        ac.dyn = w.gdyn;
+                        const int l_save = w.launches, la_save = use_amg ? w.amg->launches : 0;
+                        cudaGraph_t g = nullptr;
+                        cudaError_t e = cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal);
+                        if (e != cudaSuccess) return e;
+                        issue(ac, j, w.cap_stream, nev);
+                        e = cudaStreamEndCapture(w.cap_stream, &g);
+                        if (e != cudaSuccess) return e;
+                        e = cudaGraphInstantiate(&w.gexec[j], g, 0);
+                        cudaGraphDestroy(g);
+                        if (e != cudaSuccess) return e;
+                        w.gexec_launches[j] = (w.launches - l_save) + (use_amg ? w.amg->launches - la_save : 0);
+                        w.launches = l_save;
+                        if (use_amg) w.amg->launches = la_save;
+                    }
+                    cudaError_t e = cudaGraphLaunch(w.gexec[j], s);
+                    if (e != cudaSuccess) return e;
+                    w.launches += w.gexec_launches[j];
+                    w.graph_launches += 1;
+                }
+            } else {
+                for (int j = j0; j < j1; ++j) issue(a, j, s, nev);
             }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;

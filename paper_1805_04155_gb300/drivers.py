@@ -16,9 +16,11 @@ functions only choose the next load factor and read results back:
 * external_work: f_max^T u_k, the ordinate of the hysteresis curve of the
   cyclic von Mises experiment (Section 8.2).
 * autotune: picks the fastest solver schedule (precision, Krylov method,
-  preconditioner) for a context by timing each on the first load steps and
-  restoring the state in between (the paper uses one direct solver; the
-  schedule is this implementation's choice, Section 5's linear systems).
+  preconditioner) and then the fastest kernel schedule (assembly tile size,
+  graph-replayed or directly launched Krylov iterations) for a context by
+  timing each on the first load steps and restoring the state in between (the
+  paper uses one direct solver; the schedule is this implementation's choice,
+  Section 5's linear systems).
 """
 from __future__ import annotations
 
@@ -90,13 +92,29 @@ def schedule_candidates(symmetric: bool, base=None):
     return out
 
 
-def autotune(ctx, zeta, trial_steps: int = 3, candidates=None, base_opts=None):
+def kernel_schedule_candidates(solver_schedule):
+    """Kernel schedules for a chosen solver schedule: the assembly tile (the element type's elements
+    per CTA, or half of them: less shared memory per CTA, more CTAs per SM) x the launch form of the
+    GMRES iterations (replayed CUDA graphs, or direct launches)."""
+    out = []
+    for tile in (1, 2):
+        for graphs in (1, 0):
+            d = dict(solver_schedule)
+            d.update(asm_tile=tile, krylov_graphs=graphs)
+            out.append(d)
+    return out
+
+
+def autotune(ctx, zeta, trial_steps: int = 3, candidates=None, base_opts=None, kernel_schedules: bool = True):
     """Time each candidate schedule on the first `trial_steps` load steps from the context's current
     state, restoring that state after every trial; returns (best opts, [(candidate, seconds or None)]).
 
-    The time of a trial is the sum of its steps' t_step_ms (set-up work done once per context, such as
-    the AMG hierarchy, is outside the steps).  A candidate whose trial fails is skipped; the trial
-    paths of the others converge to the same tolerance, so their solutions agree."""
+    Two stages: the solver schedules (precision x Krylov method x preconditioner), then, on the
+    fastest of them, the kernel schedules (assembly tile x graph-replayed or direct Krylov launches,
+    kernel_schedule_candidates).  The time of a trial is the sum of its steps' t_step_ms (set-up work
+    done once per context, such as the AMG hierarchy, is outside the steps).  A candidate whose trial
+    fails is skipped; the trial paths of the others converge to the same tolerance, so their
+    solutions agree."""
     import numpy as np
     base = dict(newton_rtol=1e-10) if base_opts is None else dict(base_opts)
     if candidates is None:
@@ -105,15 +123,25 @@ def autotune(ctx, zeta, trial_steps: int = 3, candidates=None, base_opts=None):
     saved = {f: ctx.get(f).copy() for f in STATE_FIELDS}
     z = np.asarray(zeta, dtype=np.float64)[:max(1, trial_steps)]
     results = []
-    for cand in candidates:
+
+    def trial(cand):
         opts = ep.default_opts(**cand)
         st, reps = ctx.solve_load_path(z, opts, raise_on_error=False)
         t = sum(r.t_step_ms for r in reps) / 1e3 if st == ep.EP_OK else None
         results.append((cand, t))
         for f, v in saved.items():
             ctx.set(f, v)
+        return t
+
+    for cand in candidates:
+        trial(cand)
     ok = [(c, t) for c, t in results if t is not None]
     if not ok:
         raise ep.EPError(ep.EP_ERR_STATE, "autotune: every candidate schedule failed on the trial steps")
-    best = min(ok, key=lambda ct: ct[1])[0]
+    best, t_best = min(ok, key=lambda ct: ct[1])
+    if kernel_schedules:
+        for cand in kernel_schedule_candidates(best):
+            t = trial(cand)
+            if t is not None and t < t_best:
+                best, t_best = cand, t
     return ep.default_opts(**best), results

@@ -63,7 +63,8 @@ class ep_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("newton_rtol", C.c_double), ("newton_maxit", C.c_int32),
                 ("krylov", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
                 ("precond", C.c_int32), ("split_elastic_cache", C.c_int32), ("warm_start", C.c_int32),
-                ("profile", C.c_int32), ("deterministic", C.c_int32)]
+                ("profile", C.c_int32), ("deterministic", C.c_int32), ("asm_tile", C.c_int32),
+                ("krylov_graphs", C.c_int32)]
 
 
 class ep_step_report(C.Structure):

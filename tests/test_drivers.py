@@ -99,6 +99,8 @@ class _FakeTuneCtx:
 
     def solve_load_path(self, zeta, opts, raise_on_error=True):
         key = (opts.precision, opts.krylov, opts.precond)
+        if (opts.asm_tile, opts.krylov_graphs) != (1, 1):
+            key = key + (opts.asm_tile, opts.krylov_graphs)
         # every trial must start from the saved (zero) state
         self.trials.append((key, all(np.all(v == 0.0) for v in self.state.values())))
         for f in self.state:
@@ -123,13 +125,29 @@ def test_autotune_picks_the_fastest_schedule_and_restores_the_state(built):
     times = {(ep.EP_FP64, 1, 2): 3.0, (ep.EP_FP64, 1, 1): 5.0, (ep.EP_FP64, 3, 2): 2.5, (ep.EP_FP64, 3, 1): None,
              (ep.EP_MIXED, 1, 2): 2.0, (ep.EP_MIXED, 1, 1): None, (ep.EP_MIXED, 3, 2): 4.0, (ep.EP_MIXED, 3, 1): 9.0}
     ctx = _FakeTuneCtx(times)
-    best, table = D.autotune(ctx, [0.1, 0.2, 0.3, 0.4], trial_steps=3)
+    best, table = D.autotune(ctx, [0.1, 0.2, 0.3, 0.4], trial_steps=3, kernel_schedules=False)
     assert (best.precision, best.krylov, best.precond) == (ep.EP_MIXED, 1, 2)
     assert len(table) == 8 and sum(t is None for _, t in table) == 2
     assert all(fresh for _, fresh in ctx.trials)                 # each trial started from the saved state
     assert all(np.all(v == 0.0) for v in ctx.state.values())     # and the state is restored at the end
     assert dict(((c["precision"], c["krylov"], c["precond"]), t) for c, t in table)[(ep.EP_FP64, 3, 2)] == \
         3 * 2.5 / 1e3
+
+
+def test_autotune_second_stage_picks_the_fastest_kernel_schedule(built):
+    """Stage 2 varies the assembly tile and the Krylov launch form on the best solver schedule only,
+    and keeps the stage-1 schedule when no kernel schedule beats it."""
+    times = {(ep.EP_FP64, 1, 2): 3.0, (ep.EP_MIXED, 1, 2): 2.0,
+             (ep.EP_MIXED, 1, 2, 2, 1): 1.5, (ep.EP_MIXED, 1, 2, 1, 0): 2.5, (ep.EP_MIXED, 1, 2, 2, 0): None}
+    ctx = _FakeTuneCtx(times)
+    best, table = D.autotune(ctx, [0.1, 0.2, 0.3], trial_steps=3)
+    assert (best.precision, best.krylov, best.precond, best.asm_tile, best.krylov_graphs) == (ep.EP_MIXED, 1, 2, 2, 1)
+    stage2 = table[8:]
+    assert len(stage2) == 4 and all(c["precision"] == ep.EP_MIXED and c["krylov"] == 1 for c, _ in stage2)
+    assert all(fresh for _, fresh in ctx.trials)
+    ctx2 = _FakeTuneCtx({(ep.EP_FP64, 1, 2): 3.0, (ep.EP_FP64, 1, 2, 2, 1): 4.0})
+    best2, _ = D.autotune(ctx2, [0.1], trial_steps=1)
+    assert (best2.precision, best2.asm_tile, best2.krylov_graphs) == (ep.EP_FP64, 1, 1)
 
 
 def test_autotune_reports_when_every_schedule_fails(built):

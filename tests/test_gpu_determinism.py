@@ -57,12 +57,12 @@ def test_coloured_assembly_equals_atomic_assembly(ep, elem, dim, model):
     ctx.close()
 
 
-def _path(ep, prob, steps, det, state=None):
+def _path(ep, prob, steps, det, state=None, **kw):
     ctx = ep.Context.from_problem(prob)
     if state is not None:
         for f, v in state.items():
             ctx.set(f, v)
-    reps = ctx.solve_load_path(steps, ep.default_opts(newton_rtol=1e-10, deterministic=det, warm_start=0))
+    reps = ctx.solve_load_path(steps, ep.default_opts(newton_rtol=1e-10, deterministic=det, warm_start=0, **kw))
     fields = (ep.EP_U, ep.EP_STRESS, ep.EP_PLASTIC_STRAIN, ep.EP_HARDENING, ep.EP_PLASTIC_FLAG)
     out = {f: ctx.get(f) for f in fields}
     ctx.close()
@@ -87,3 +87,33 @@ def test_deterministic_path_repeats_and_resumes_bit_for_bit(ep, which):
     # the atomic form reaches the same converged path to the Newton tolerance
     d, _ = _path(ep, prob, z, 0)
     assert rel_max(d[ep.EP_U], a[ep.EP_U]) < 1e-8
+
+
+def test_graph_replayed_krylov_iterations_equal_direct_launches(ep):
+    """GMRES iterations replayed from captured CUDA graphs run the same kernels in the same order as
+    direct launches: in the deterministic form the two load paths are identical bit for bit."""
+    from synthetic import problems as P
+    prob = P.p2_plane_dp(n=16, n_steps=12, load_fraction=0.9)
+    a, reps = _path(ep, prob, prob.zeta, 1, krylov_graphs=1)
+    assert sum(r.krylov_its for r in reps) > 0
+    b, _ = _path(ep, prob, prob.zeta, 1, krylov_graphs=0)
+    for f in a:
+        assert np.array_equal(a[f], b[f]), f
+
+
+@pytest.mark.parametrize("elem,dim", [("P2", 2), ("Q1", 3), ("P2", 3)])
+def test_half_tile_assembly_schedule_equals_the_default(ep, elem, dim):
+    """The autotuner's second assembly schedule (half the elements per CTA) computes the same K and F
+    (coloured form: bit for bit)."""
+    prob = small_problem(elem, dim, SIZES[(elem, dim)] + 1, DP, seed=23)
+    u, ep_, hard = fed_iterate(prob, seed=24, dilate=1.5e-3)
+    ctx = ep.Context.from_problem(prob)
+    ctx.set(ep.EP_PLASTIC_STRAIN, ep_)
+    ctx.set(ep.EP_HARDENING, hard)
+    out = {}
+    for tile in (1, 2):
+        ctx.solve_load_path(np.zeros(0), ep.default_opts(deterministic=1, precond=0, asm_tile=tile))
+        ctx.assemble(u, split=True)
+        out[tile] = (ctx.K_csr().data.copy(), ctx.get(ep.EP_F_INT))
+    assert np.array_equal(out[1][0], out[2][0]) and np.array_equal(out[1][1], out[2][1])
+    ctx.close()

@@ -224,6 +224,19 @@ def test_load_path_p2_drucker_prager_column(ep):
     assert reps[-1].n_plastic == prob.mesh.n_elem * 7
 
 
+@pytest.mark.parametrize("model,prob_name", [(DP, "p2_dp"), (VM_ISO, "q1_vm")])
+def test_precise_vcycle_load_path(ep, monkeypatch, model, prob_name):
+    """The precise V-cycle (FP64 coarse correction and level-0 residuals, forced from the start of
+    the path) reaches the oracle's load path; every step reports it."""
+    from synthetic import p2_plane_dp, q1_cube_vm
+    monkeypatch.setenv("EP_AMG_PRECISE", "1")
+    prob = p2_plane_dp(n=12, n_steps=10, load_fraction=0.95) if prob_name == "p2_dp" else q1_cube_vm(n=5, n_steps=6)
+    # near the limit load 1e-11 in eps^p needs a 1e-13 residual (as in the direct test above)
+    reps = _path_parity(ep, prob, 1e-13, ep.default_opts(newton_rtol=1e-13, newton_maxit=40, precond=2))
+    assert all(r.precise == 1 for r in reps if r.krylov_its > 0)
+    assert reps[-1].n_plastic > 0
+
+
 def test_load_path_p2_full_size_all_steps(ep):
     """The benchmark workload (256x256 P2, 40 steps) end to end, against the one-point oracle."""
     from oracle.newton import homogeneous_column

@@ -79,6 +79,35 @@ def test_noalloc_solve_matches_context_solve(ep, model, method):
     ctx.close()
 
 
+def test_noalloc_solve_allocates_no_device_memory(ep):
+    """After the first call (which looks up the fixed array's device address), repeated solves leave
+    the device's free memory unchanged: nothing on this path allocates."""
+    prob, ctx = _system(ep, 2, seed=13)
+    free = (prob.dirichlet == 0)
+    b = np.random.default_rng(14).standard_normal(prob.n_dof) * free
+    rp = ctx.get(ep.EP_K_ROW_PTR)
+    ci = ctx.get(ep.EP_K_COL_IDX)
+    vals = ctx.get(ep.EP_K_VALUES)
+    diag = np.array([rp[i] + np.searchsorted(ci[rp[i]:rp[i + 1]], i) for i in range(len(rp) - 1)], dtype=np.int32)
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    args = [T(rp), T(ci), T(diag), T(vals), T(prob.dirichlet == 0).to(torch.uint8), T(b)]
+    x = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
+    for method, precond in ((1, 1), (2, 0)):
+        st, _, _ = ep.linear_solve_noalloc(2, *args, x, method=method, precond=precond, rtol=1e-10, maxit=2000)
+        assert st == ep.EP_OK
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for method, precond in ((1, 1), (2, 0)):
+            st, _, _ = ep.linear_solve_noalloc(2, *args, x, method=method, precond=precond, rtol=1e-10, maxit=2000)
+            assert st == ep.EP_OK
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    ctx.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_workspace(ep):
     """Host-side check before any GPU work: more DOFs than the fixed array holds."""
     dev = torch.device("cuda:0")
