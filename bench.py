@@ -150,6 +150,13 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# DRAM bytes of the FP64 plane SpMV (k_spmv<2, 2, double>) per 2x2 block, from one ncu capture of
+# the current kernel on the 320 x 320 P2 column (dram__bytes_read.sum + dram__bytes_write.sum =
+# 209 646 080 + 8 653 568 B for 4 715 521 blocks; profiles/k_spmv_fp64_p2_plane_dp_n320.md);
+# the traffic grows with the blocks, so the bench scales it to the run's pattern.
+SPMV64_2D_DRAM_BYTES_PER_BLOCK = (209646080 + 8653568) / 4715521
+
+
 def _spmv_bytes(info, dim, vb=8):
     """Algorithmic bytes of one masked block-CSR SpMV with vb-byte values and vectors: values +
     column indices + row pointers + x read once + y written once + free mask."""
@@ -158,13 +165,17 @@ def _spmv_bytes(info, dim, vb=8):
     return nnzb * (dim * dim * vb + 4) + (n_rows + 1) * 4 + n * vb * 2 + n
 
 
-def _cheb0_bytes(info, dim):
-    """Algorithmic bytes of one level-0 Chebyshev step of the AMG V-cycle (k_cheb, FP32): the
-    matrix (values, column indices, row pointers), its block-Jacobi inverse, the free mask, and the
-    vectors b, x_in, d read and d, x_out written once."""
+def _cheb0_bytes(info, dim, deg=2):
+    """Algorithmic bytes per launch of the level-0 Chebyshev steps of the AMG V-cycle (k_cheb, FP32),
+    averaged over the timed sweep (the pre-smoothing: `deg` steps from zero).  Step 0 starts from
+    x = 0 and reads no matrix: block-Jacobi inverse, free mask and b read, d and x written.  Every
+    later step reads the matrix (values, column indices, row pointers), the inverse, the mask, and
+    b, x_in, d, and writes d and x_out, each once."""
     nnzb, n_rows = info.nnz_blocks, info.n_nodes
     n = n_rows * dim
-    return nnzb * (dim * dim * 4 + 4) + (n_rows + 1) * 4 + n_rows * dim * dim * 4 + n + 5 * 4 * n
+    step0 = n_rows * dim * dim * 4 + n + 3 * 4 * n
+    later = nnzb * (dim * dim * 4 + 4) + (n_rows + 1) * 4 + n_rows * dim * dim * 4 + n + 5 * 4 * n
+    return (step0 + (deg - 1) * later) / deg
 
 
 def _assembly_bytes(info, dim, n_p, n_comp, kb=8, pe=1.0):
@@ -326,6 +337,25 @@ def run_batch(args):
         t.join()
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    # the same sweep in mixed precision (FP32 tangent and inner Krylov, FP64 residual), batched
+    mopts = ep.default_opts(newton_rtol=opts.newton_rtol, precision=ep.EP_MIXED, krylov_graphs=opts.krylov_graphs)
+    for c in ctxs.values():
+        c.solve_load_path(zeta[:1], mopts)   # FP32 buffers on first use, outside the timed region
+        reset(c)
+    torch.cuda.synchronize()
+    results_m = {}
+
+    def solve_m(f):
+        results_m[f] = ctxs[f].solve_load_path(zeta, mopts)
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=solve_m, args=(f,)) for f in fams]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    t_batch_mixed = time.perf_counter() - t0
     t0 = time.perf_counter()
     reps_single = [c.solve_load_path(zeta, opts) for _, c in singles]
     torch.cuda.synchronize()
@@ -346,10 +376,20 @@ def run_batch(args):
                                "krylov_its": int(sum(r.krylov_its for r in results[f])),
                                "solve_ms": float(sum(r.t_step_ms for r in results[f]))} for f in fams},
             "max_rel_resid": max(r.rel_resid for f in fams for r in results[f]),
+            "mixed_batched_s": t_batch_mixed,
+            "mixed_max_rel_resid": max(r.rel_resid for f in fams for r in results_m[f]),
+            "mixed_newton_its": {f: int(sum(r.newton_its for r in results_m[f])) for f in fams},
             "newton_its": {f: int(sum(r.newton_its for r in results[f])) for f in fams},
             "one_by_one_newton_its": int(sum(r.newton_its for rs in reps_single for r in rs)) if singles else None}
     if args.learned:
         line["learned"] = learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results)
+        # the benchmark spec's combined form (mixed precision, batched, learned start) against the plain
+        # FP64 GPU form (batched, extrapolated start) on time to solution at the same tolerance
+        line["combined_vs_fp64"] = {"fp64_batched_s": t_batch, "mixed_batched_s": t_batch_mixed,
+                                    "fp64_learned_batched_s": line["learned"]["batched_s"],
+                                    "mixed_learned_batched_s": line["learned"]["mixed_batched_s"],
+                                    "one_by_one_fp64_s": t_single if singles else None,
+                                    "tolerance": opts.newton_rtol}
     for c in ctxs.values():
         c.close()
     for _, c in singles:
@@ -391,24 +431,29 @@ def learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results
     train_tflops = args.learned_steps * n_rows * 2 * MLP_FMA_TRAIN / t_train / 1e12
     for c in rec.values():
         c.close()
-    lopts = ep.default_opts(newton_rtol=opts.newton_rtol, warm_start=2)
-    for f in fams:
-        reset(ctxs[f])
-        ctxs[f].ws_attach(net)
-    torch.cuda.synchronize()
-    res = {}
+    def timed_learned(prec):
+        lopts = ep.default_opts(newton_rtol=opts.newton_rtol, warm_start=2, precision=prec,
+                                krylov_graphs=opts.krylov_graphs)
+        for f in fams:
+            reset(ctxs[f])
+            ctxs[f].ws_attach(net)
+        torch.cuda.synchronize()
+        res = {}
 
-    def solve(f):
-        res[f] = ctxs[f].solve_load_path(zeta, lopts)
+        def solve(f):
+            res[f] = ctxs[f].solve_load_path(zeta, lopts)
 
-    t0 = time.perf_counter()
-    th = [threading.Thread(target=solve, args=(f,)) for f in fams]
-    for t in th:
-        t.start()
-    for t in th:
-        t.join()
-    torch.cuda.synchronize()
-    t_learned = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        th = [threading.Thread(target=solve, args=(f,)) for f in fams]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    t_learned, res = timed_learned(ep.EP_FP64)
+    t_learned_mixed, res_mixed = timed_learned(ep.EP_MIXED)
     for f in fams:
         ctxs[f].ws_attach(None)
     net.close()
@@ -417,7 +462,8 @@ def learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results
             "record_s": t_record, "train_s": t_train,
             "train_tflops_wall": train_tflops, "train_frac_of_fp32_fma_peak": train_tflops / FP32_PEAK_TFLOPS,
             "loss": {f: [loss0[f], loss1[f]] for f in loss0},
-            "batched_s": t_learned,
+            "batched_s": t_learned, "mixed_batched_s": t_learned_mixed,
+            "mixed_newton_its": {f: int(sum(r.newton_its for r in res_mixed[f])) for f in fams},
             "newton_its": {f: int(sum(r.newton_its for r in res[f])) for f in fams},
             "extrapolated_newton_its": {f: int(sum(r.newton_its for r in results[f])) for f in fams},
             "problems_on_learned_start": {f: [int(r.n_learned) for r in res[f]] for f in fams},
@@ -659,6 +705,9 @@ def run_path(args, ep, local, world, rank):
         # the FP64 operator of the Krylov solves: the mixed path's FP64-tangent iterations use it too
         cands["spmv"] = _roof_hbm(f"k_spmv (masked block-CSR)", n_spmv, t_spmv,
                                   _spmv_bytes(info, dim, 8), peaks, peaks_kind, ms_prof_path)
+        if dim == 2:
+            cands["spmv"]["traffic"] = SPMV64_2D_DRAM_BYTES_PER_BLOCK * info.nnz_blocks
+            cands["spmv"]["traffic_source"] = "ncu capture at 320x320 cells, scaled by blocks"
     if asm_prof:
         pf = plastic_assembled / max(1, asm_prof * n_int)
         pe = pe_assembled / max(1, asm_prof * info.n_elem)

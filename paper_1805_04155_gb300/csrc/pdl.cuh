@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <utility>
 
 namespace ep {
@@ -24,6 +25,16 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_enter() {
     pdl_wait();
     pdl_launch_dependents();
+}
+
+// EP_NO_PDL=1 launches these kernels without the attribute (plain stream order; griddepcontrol.wait
+// then returns at once): for kernel profilers that cannot follow programmatic dependencies.
+inline bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("EP_NO_PDL");
+        return !(v && v[0] == '1');
+    }();
+    return on;
 }
 
 template <typename... KArgs, typename... Args>
@@ -38,7 +49,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
