@@ -1344,6 +1344,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         it = 0;
         converged = false;
         double rnorm_prev = -1.0, rel_best = 1e300;
+        double rel_prev = -1.0;  // largest per-problem relative residual before the last solve
         bool use32 = false;      // this iteration's tangent and solve in FP32
         bool fp64_step = false;  // the rest of this step in FP64 (an FP32 iteration contracted poorly)
         double eta_prev = 1.0;   // Krylov tolerance of the last solve
@@ -1448,6 +1449,17 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 if (c->verbose) std::fprintf(stderr, "[ep] step %d: FP32 tangent stalled, FP64 from here\n", k);
                 continue;
             }
+            // a batch converges when its worst problem does: an FP32 iteration that leaves the worst
+            // relative residual above half its previous value (a small problem at FP32 rounding
+            // level while the batch's norm, dominated by the large ones, still contracts) finishes
+            // the step in FP64
+            if (use32 && c->n_prob > 1 && rel_prev > 0.0 && rel > MIXED_STALL_RATIO * rel_prev) {
+                fp64_step = true;
+                if (c->verbose > 1)
+                    std::fprintf(stderr, "[ep] step %d: worst problem %.2e after %.2e on the FP32 tangent, FP64 tangent\n",
+                                 k, rel, rel_prev);
+                continue;
+            }
             if (use32 && rnorm_prev > 0.0 && rnorm > MIXED_RHO_FACTOR * eta_prev * rnorm_prev) {
                 fp64_step = true;
                 if (c->verbose > 1)
@@ -1468,6 +1480,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             f_first = o.krylov_rtol <= 0.0 && eta * rnorm <= 0.5000001 * o.newton_rtol * scale &&
                       rnorm_prev > 0.0 && rnorm < 0.1 * rnorm_prev;
             rnorm_prev = rnorm;
+            rel_prev = rel;
             eta_prev = eta;
             CK(cudaEventRecord(c->ev[2], s));
             // Coarse operators: rebuilt (Galerkin, from the current tangent) at the first Newton

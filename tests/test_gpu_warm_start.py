@@ -291,18 +291,20 @@ def test_learned_start_needs_a_network(ep):
     ctx.close()
 
 
-def test_learned_start_reaches_the_oracle_path_and_reports_iterations(ep):
-    """Train on recorded trajectories of one batch of columns, then solve other columns from the
-    learned start: the converged path equals the oracle's, and the Newton iterations are reported
-    against the plain extrapolated start (the learned start is taken per problem only where it has
-    the smaller residual, so it may cost at most a few iterations more; measured: 23 -> 22)."""
+def test_learned_start_saves_newton_iterations_on_unseen_problems(ep):
+    """Train on recorded trajectories of one batch of columns, then solve other columns (unseen sizes
+    and materials) from the learned start with large load increments (7 steps to 1.5x first yield):
+    the converged path equals the oracle's and the learned start needs fewer Newton iterations than
+    the plain extrapolated start.  Everything runs in the deterministic form, so the recorded rows,
+    the trained network and the iteration counts are reproducible (measured: 16 -> 13)."""
     from oracle.newton import OracleSolver
+    n_steps = 7
     g = np.random.default_rng(31)
-    train = [_column(int(g.integers(4, 9)), tuple(g.uniform(0.8, 1.2, 4)), n_steps=16) for _ in range(6)]
-    test = [_column(int(g.integers(4, 9)), tuple(g.uniform(0.8, 1.2, 4)), n_steps=16) for _ in range(3)]
+    train = [_column(int(g.integers(4, 9)), tuple(g.uniform(0.8, 1.2, 4)), n_steps=n_steps) for _ in range(6)]
+    test = [_column(int(g.integers(4, 9)), tuple(g.uniform(0.8, 1.2, 4)), n_steps=n_steps) for _ in range(3)]
     ctx = ep.Context.from_batch(train)
-    ctx.ws_record(sum(pb.mesh.n_nodes for pb in train) * 16)
-    opts1 = ep.default_opts(newton_rtol=1e-12, warm_start=1, newton_maxit=40)
+    ctx.ws_record(sum(pb.mesh.n_nodes for pb in train) * n_steps)
+    opts1 = ep.default_opts(newton_rtol=1e-12, warm_start=1, newton_maxit=40, deterministic=1)
     ctx.solve_load_path(train[0].zeta, opts1)
     xp, tp, n = ctx.ws_samples_ptr()
     net = ep.MLP(mlp_init(0))
@@ -313,14 +315,17 @@ def test_learned_start_reaches_the_oracle_path_and_reports_iterations(ep):
     ctx.close()
     its = {}
     us = {}
+    learned = []
     for ws in (1, 2):
         c = ep.Context.from_batch(test)
         if ws == 2:
             c.ws_attach(net)
-        reps = c.solve_load_path(test[0].zeta, ep.default_opts(newton_rtol=1e-12, warm_start=ws, newton_maxit=40))
+        reps = c.solve_load_path(test[0].zeta, ep.default_opts(newton_rtol=1e-12, warm_start=ws, newton_maxit=40,
+                                                              deterministic=1))
         its[ws] = [r.newton_its for r in reps]
         us[ws] = c.split(ep.EP_U, c.get(ep.EP_U))
-        learned = [r.n_learned for r in reps]
+        if ws == 2:
+            learned = [r.n_learned for r in reps]
         c.close()
     for i, pb in enumerate(test):
         ref = OracleSolver(pb)
@@ -330,5 +335,6 @@ def test_learned_start_reaches_the_oracle_path_and_reports_iterations(ep):
     print(f"\ntraining loss {l0:.3e} -> {l1:.3e} on {n} rows; Newton its extrapolated {sum(its[1])} {its[1]}, "
           f"learned {sum(its[2])} {its[2]}; problems on the learned start per step {learned}")
     assert l1 < 0.1 * l0
-    assert sum(its[2]) <= 1.1 * sum(its[1]) + 1
+    assert sum(learned) > 0
+    assert sum(its[2]) < sum(its[1])
     net.close()
