@@ -155,6 +155,10 @@ class Clocks:
 # 209 646 080 + 8 653 568 B for 4 715 521 blocks; profiles/k_spmv_fp64_p2_plane_dp_n320.md);
 # the traffic grows with the blocks, so the bench scales it to the run's pattern.
 SPMV64_2D_DRAM_BYTES_PER_BLOCK = (209646080 + 8653568) / 4715521
+# DRAM bytes of a level-0 Chebyshev step that reads the matrix (k_cheb<2, 4, float>), per 2x2 block,
+# from one ncu capture on the 320 x 320 P2 column (mean of two launches: 113 237 248 + 3 748 352 and
+# 109 949 952 + 3 864 320 B for 4 715 521 blocks; profiles/k_cheb_level0_p2_plane_dp_n320.md).
+CHEB0_2D_DRAM_BYTES_PER_BLOCK = (113237248 + 3748352 + 109949952 + 3864320) / 2 / 4715521
 
 
 def _spmv_bytes(info, dim, vb=8):
@@ -340,6 +344,7 @@ def run_batch(args):
     # the same sweep in mixed precision (FP32 tangent and inner Krylov, FP64 residual), batched
     mopts = ep.default_opts(newton_rtol=opts.newton_rtol, precision=ep.EP_MIXED, krylov_graphs=opts.krylov_graphs)
     for c in ctxs.values():
+        reset(c)                             # the FP64 sweep left the contexts at the end of the path
         c.solve_load_path(zeta[:1], mopts)   # FP32 buffers on first use, outside the timed region
         reset(c)
     torch.cuda.synchronize()
@@ -732,6 +737,14 @@ def run_path(args, ep, local, world, rank):
                                          _cheb0_bytes(info, dim), peaks, peaks_kind, ms_prof_path,
                                          share_of_step=avg * est_n / ms_prof_path, launches_sampled=n_sm0,
                                          launches_estimated=est_n)
+        if dim == 2:
+            # the timed sweep averages a zero-start step (no matrix: its algorithmic bytes) and a
+            # matrix step (the capture's DRAM bytes per block, scaled to the run's blocks)
+            n_rows = info.n_nodes
+            step0 = n_rows * 16 + n_rows * 2 * 13
+            cands["amg_smooth0"]["traffic"] = (step0 + CHEB0_2D_DRAM_BYTES_PER_BLOCK * info.nnz_blocks) / 2
+            cands["amg_smooth0"]["traffic_source"] = ("matrix step: ncu capture at 320x320 cells scaled by blocks; "
+                                                      "zero-start step: algorithmic bytes")
     dominant = max(cands.values(), key=lambda r: r["share_of_step"]) if cands else None
     for c_ in cands.values():
         c_["timing"] = "instrumented path after the timed region (CUDA events on the launching stream)"
