@@ -701,7 +701,9 @@ cudaError_t amg_upload(const AmgHierarchy& H, AmgDev& D, int num_sms) {
         if (!L.dense_inv.empty() && (e = up_f(D, &d.dense_inv, L.dense_inv, L.dense_inv.size())) != cudaSuccess)
             return e;
     }
-    D.nparts = 2 * (num_sms > 0 ? num_sms : 152);
+    // one partial per CTA of the power iteration's SpMV, whose grid is one resident wave of AB-thread
+    // CTAs (RES_CTAS per SM): fewer CTAs left it latency-bound (53 us against 18 us for a Chebyshev step)
+    D.nparts = RES_CTAS * (num_sms > 0 ? num_sms : 152);
     D.nnzb0 = H.nnzb0;
     {
         const int64_t rows0 = H.levels[0].n / H.levels[0].bs;

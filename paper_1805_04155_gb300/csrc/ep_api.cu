@@ -221,6 +221,9 @@ struct Ctx {
     // deterministic form (ep_opts.deterministic): element colours, one assembly launch per colour
     int deterministic = 0;
     int asm_tile = 1;                   // assembly schedule (ep_opts.asm_tile)
+    // Eisenstat-Walker forcing terms of the inexact Newton iteration: the first iteration of a step
+    // and the cap (tuning knobs EP_NEWTON_ETA0, EP_NEWTON_ETA_MAX)
+    double eta0 = 1e-3, eta_max = 1e-2;
     std::vector<int32_t> h_color_ptr;   // [n_colors + 1]
     int32_t* color_elems = nullptr;     // device [n_elem]
     bool split_base64 = false, split_base32 = false;   // the statement above holds
@@ -528,6 +531,8 @@ static ep_status create_impl(void** out, const ep_mesh* mesh, const ep_material*
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     if (const char* v = std::getenv("EP_VERBOSE")) c->verbose = std::atoi(v);
+    if (const char* v = std::getenv("EP_NEWTON_ETA0")) c->eta0 = std::max(1e-12, std::min(0.5, std::atof(v)));
+    if (const char* v = std::getenv("EP_NEWTON_ETA_MAX")) c->eta_max = std::max(1e-12, std::min(0.5, std::atof(v)));
     if (cudaSetDevice(device) != cudaSuccess) {
         c->err = "cudaSetDevice failed";
         return fail(EP_ERR_CUDA);
@@ -1436,8 +1441,8 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             if (o.krylov_rtol > 0.0) eta = o.krylov_rtol;
             else {
                 const double eta_min = 0.5 * o.newton_rtol * scale / rnorm;
-                const double eta_ew = (rnorm_prev < 0.0) ? 1e-3 : 0.9 * (rnorm / rnorm_prev) * (rnorm / rnorm_prev);
-                eta = std::min(1e-2, std::max(eta_ew, eta_min));
+                const double eta_ew = (rnorm_prev < 0.0) ? c->eta0 : 0.9 * (rnorm / rnorm_prev) * (rnorm / rnorm_prev);
+                eta = std::min(c->eta_max, std::max(eta_ew, eta_min));
                 eta = std::max(eta, 1e-14);
             }
             // FP32 phase of the mixed path: if the last FP32 Newton step barely reduced the FP64
