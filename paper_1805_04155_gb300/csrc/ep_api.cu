@@ -1449,7 +1449,10 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             if (o.krylov_rtol > 0.0) eta = o.krylov_rtol;
             else {
                 const double eta_min = 0.5 * o.newton_rtol * scale / rnorm;
-                const double e0 = mixed ? c->eta0_mixed : c->eta0, emax = mixed ? c->eta_max_mixed : c->eta_max;
+                // the mixed path's FP32 iterations keep the tighter terms (see eta0_mixed); its
+                // FP64-tangent iterations take the FP64 path's
+                const bool t32 = mixed && !c->mixed_fallback && !fp64_step;
+                const double e0 = t32 ? c->eta0_mixed : c->eta0, emax = t32 ? c->eta_max_mixed : c->eta_max;
                 const double eta_ew = (rnorm_prev < 0.0) ? e0 : 0.9 * (rnorm / rnorm_prev) * (rnorm / rnorm_prev);
                 eta = std::min(emax, std::max(eta_ew, eta_min));
                 eta = std::max(eta, 1e-14);
