@@ -47,3 +47,25 @@ def test_spmv_bytes_formula():
 
 def test_job_value_counts_every_rank():
     assert bench.job_value(4, 1000, 10, 2.0) == 4 * 1000 * 10 / 0.002 / 1e9
+
+
+def test_assembly_bytes_scale_the_tangent_part_with_the_plastic_elements():
+    class Info:
+        n_int, n_elem, n_nodes, nnz_blocks = 700, 100, 250, 2000
+    full = bench._assembly_bytes(Info, 2, 6, 4, 8, 1.0)
+    none = bench._assembly_bytes(Info, 2, 6, 4, 8, 0.0)
+    half = bench._assembly_bytes(Info, 2, 6, 4, 8, 0.5)
+    # the plastic elements' slot map and K blocks (read and written once) are the only difference
+    assert full - none == 100 * 36 * 4 + 2000 * 4 * 8 * 2
+    assert abs(half - (none + full) / 2) < 1e-6
+
+
+def test_chebyshev_bytes_average_the_zero_start_step():
+    class Info:
+        nnz_blocks, n_nodes = 3000, 400
+    n = 800
+    step0 = 400 * 16 + n + 12 * n                     # no matrix: inverse, mask, b read; d, x written
+    later = 3000 * 20 + 401 * 4 + 400 * 16 + n + 20 * n
+    assert bench._cheb0_bytes(Info, 2, deg=1) == step0
+    assert bench._cheb0_bytes(Info, 2, deg=2) == (step0 + later) / 2
+    assert bench._cheb0_bytes(Info, 2, deg=3) == (step0 + 2 * later) / 3
