@@ -5,12 +5,13 @@ then every load step: semismooth Newton to the relative residual tolerance --
 each iteration fused return mapping + tangent assembly + internal forces,
 residual and norms, preconditioned Krylov solve, update -- and the state
 commit).  The default workload is the P2 plane-strain Drucker-Prager column
-(256 x 256 cells, 917 504 points, 40 load steps to 0.95 of the limit
-traction), so every step crosses the elastic, the spreading-plastic and the
-nearly-singular fully plastic range (beyond about 0.97 the nonassociated
-tangent becomes indefinite on local plastic-flow modes and no Krylov method
-here solves its Newton systems).  W warm-up paths, then K timed paths in
-each precision, CUDA events around each path on the context's stream.
+(256 x 256 cells, 917 504 points, 40 load steps to 0.98 of the limit
+traction), so every path crosses the elastic, the spreading-plastic and the
+nearly-singular fully plastic range: at the last step the nonassociated
+tangent is indefinite on local plastic-flow modes, GMRES with the V-cycle
+stalls, and the solver switches to its sparse LU (one factorisation per
+Newton iteration).  W warm-up paths, then K timed paths in each precision,
+CUDA events around each path on the context's stream.
 
 value = integration points assembled per second over the timed region
         (n_int x assemblies / elapsed): the rate at which the solver drives
@@ -22,11 +23,12 @@ value = integration points assembled per second over the timed region
         the primary and the other is reported under "compare".  load_path_s
         is the median of the K measured path times.
 roofline: the kernel with the largest share of the step among the assembly,
-        the SpMV of the Krylov solves and the AMG level-0 Chebyshev step
-        (CUDA events around every assembly and SpMV launch and around a sample
-        of the smoothing sweeps, inside the timed region), algorithmic bytes
-        per launch over the average launch time; all three under
-        roofline_kernels.
+        the SpMV of the Krylov solves, the AMG level-0 Chebyshev step and the
+        sparse LU's factorisation and solve (CUDA events around every
+        assembly, SpMV, factorisation and solve and around a sample of the
+        smoothing sweeps, in one instrumented path after the timed region),
+        algorithmic bytes (FLOPs for the factorisation) per launch over the
+        average launch time; all of them under roofline_kernels.
 e2e:    the same metric through the C ABI with host buffers: each path takes
         its load factors from the host and reads u and sigma back to host
         buffers.
@@ -663,6 +665,8 @@ def run_path(args, ep, local, world, rank):
                 "krylov_its_per_path": int(sum(r.krylov_its for r in last)),
                 "assemblies_per_path": int(sum(r.n_assemble for r in last)),
                 "n_plastic_final": int(last[-1].n_plastic),
+                "sparse_lu_steps_per_path": int(sum(r.direct for r in last)),
+                "sparse_lu_factorisations_per_path": int(sum(r.n_direct_factor for r in last)),
                 "max_rel_resid": max(r.rel_resid for r in rr)}
 
     compare = None
@@ -745,6 +749,32 @@ def run_path(args, ep, local, world, rank):
             cands["amg_smooth0"]["traffic"] = (step0 + CHEB0_2D_DRAM_BYTES_PER_BLOCK * info.nnz_blocks) / 2
             cands["amg_smooth0"]["traffic_source"] = ("matrix step: ncu capture at 320x320 cells scaled by blocks; "
                                                       "zero-start step: algorithmic bytes")
+    # the sparse LU of the steps near the limit load (the Newton loop switches to it where the V-cycle
+    # stalls): one factorisation per Newton iteration (FP32 FMA bound: the fronts' rank-32 updates),
+    # a forward and a backward solve per GMRES iteration (reads the factors' pivot rows and columns)
+    n_df = sum(r.n_direct_factor for r in reps_prof)
+    if n_df:
+        t_df = sum(r.t_direct_factor_ms for r in reps_prof)
+        flop = max(r.direct_factor_flop for r in reps_prof)
+        dur = t_df / n_df / 1e3
+        tf = flop / dur / 1e12
+        f64_fronts = os.environ.get("EP_DIRECT_FP32", "0") != "1"
+        peak = FP64_PEAK_TFLOPS if f64_fronts else FP32_PEAK_TFLOPS
+        cands["sparse_lu_factor"] = {
+            "bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "traffic": None, "kernel": "sparse LU factorisation (k_df_scatter, k_df_diag, k_df_panel, k_df_update, "
+                                       f"k_df_extend over the levels; {'FP64' if f64_fronts else 'FP32'} fronts)",
+            "launches": n_df, "what_is_a_launch": "one factorisation (all levels)", "avg_us": dur * 1e6,
+            "flop_per_launch": flop,
+            "peak_source": ("FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived)" if f64_fronts
+                            else "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived)"),
+            "share_of_step": t_df / ms_prof_path}
+    n_ds = sum(r.n_direct_solve for r in reps_prof)
+    if n_ds:
+        t_ds = sum(r.t_direct_solve_ms for r in reps_prof)
+        cands["sparse_lu_solve"] = _roof_hbm("sparse LU solve (k_ds_fwd, k_ds_bwd over the levels)", n_ds, t_ds,
+                                             max(r.direct_solve_bytes for r in reps_prof), peaks, peaks_kind,
+                                             ms_prof_path, what_is_a_launch="one forward and backward solve")
     dominant = max(cands.values(), key=lambda r: r["share_of_step"]) if cands else None
     for c_ in cands.values():
         c_["timing"] = "instrumented path after the timed region (CUDA events on the launching stream)"
@@ -771,7 +801,8 @@ def run_path(args, ep, local, world, rank):
                 "n_int": n_int, "step": f"one whole load path ({n_path} load steps from the virgin state)",
                 "parallelism": "replicas" if world > 1 else "single GPU", "precision": prec,
                 "krylov": "GMRES(30)" if prob.material.model == 3 and prob.material.psi != prob.material.phi
-                else "CG", "precond": "smoothed-aggregation AMG, FP32 V-cycle, Galerkin from the tangent",
+                else "CG", "precond": "smoothed-aggregation AMG, FP32 V-cycle, Galerkin from the tangent; "
+                                      "sparse LU where GMRES stalls with it (near the limit load)",
                 "split_elastic_cache": True,
                 "krylov_iterations": "direct launches" if args.no_graphs else "replayed from CUDA graphs"}),
             "roofline": dominant, "roofline_kernels": cands,

@@ -118,7 +118,12 @@ typedef struct {
     double krylov_rtol;          /* > 0: fixed relative tolerance; 0: adaptive forcing term */
     int32_t krylov_maxit;
     int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks), 2 smoothed-aggregation AMG
-                                    (built from K_elast on first use; Chebyshev/block-Jacobi smoothing) */
+                                    (built from K_elast on first use; Chebyshev/block-Jacobi smoothing),
+                                    3 sparse LU of the tangent (multifrontal, nested-dissection order, FP32
+                                    factors with static pivoting, refactored at every Newton iteration; with
+                                    GMRES, which refines to the FP64 tolerance).  The paper solves eq.
+                                    (lin_syst) directly; 3 is its counterpart here.  Set up on first use:
+                                    EP_ERR_STATE if the factors would not fit in 60% of the free device memory */
     int32_t split_elastic_cache; /* 1: K = K_elast + sum over plastic points (eq. (K-split)); 0: K = B^T D B */
     int32_t warm_start;          /* 0: last converged u; 1: linear extrapolation of the last two steps;
                                     2: the extrapolation corrected by the attached warm-start network
@@ -140,6 +145,11 @@ typedef struct {
                                     as CUDA graphs and replayed (one launch per iteration instead of about 30);
                                     0: direct launches.  Either way the same kernels run in the same order.
                                     profile = 1 always launches directly (events around the kernels). */
+    int32_t direct_fallback;     /* 1 (default): with precond = 2, when a GMRES solve stalls with the V-cycle
+                                    (near a limit load the nonassociated tangent has eigenvalues with negative
+                                    real parts, Section 2.3), the rest of the load path is solved with the
+                                    sparse LU (precond 3), or, where its factors do not fit, with the precise
+                                    V-cycle; 0: always the precise V-cycle */
 } ep_opts;
 
 typedef struct {
@@ -166,7 +176,14 @@ typedef struct {
                                            formed a tangent (their blocks are the ones the split form rewrites) */
     int32_t precise;             /* 1: the step's preconditioner used the precise V-cycle (FP64 coarse correction;
                                     switched on for the rest of the path when GMRES stalled with the FP32 one) */
-    int32_t reserved;
+    int32_t direct;              /* 1: the step solved with the sparse LU (precond 3, or switched to it for the
+                                    rest of the path when GMRES stalled with the V-cycle) */
+    int32_t n_direct_factor;     /* sparse-LU factorisations of the step */
+    int32_t n_direct_solve;      /* sparse-LU solves (preconditioner applications) of the step */
+    double t_direct_factor_ms;   /* their summed durations (profile = 1) */
+    double t_direct_solve_ms;
+    double direct_factor_flop;   /* FLOP of one factorisation (partial LU of every front) */
+    double direct_solve_bytes;   /* bytes of the factors one solve reads */
 } ep_step_report;
 
 /* Fields readable with ep_get / writable with ep_set. */

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "amg.h"
+#include "direct.h"
 #include "ep_internal.h"
 
 namespace ep {
@@ -245,6 +246,11 @@ struct Ctx {
     std::vector<double> h_coords;
     std::vector<uint8_t> h_free;
     AmgDev amg;
+    // sparse LU (precond 3): set up on first use; direct_mode = the Newton loop solves with it for
+    // the rest of the load path (switched on when a GMRES solve with the V-cycle stalled)
+    DirectDev direct;
+    bool direct_mode = false;
+    double direct_setup_ms = 0.0;
     bool amg_built = false;
     bool amg_elastic = true;     // the AMG coarse operators currently come from K_elast
     int64_t amg_np = -1;         // plastic points of the tangent the coarse operators were last built from
@@ -392,13 +398,15 @@ static ep_status assemble(Ctx* c, const double* u_dev, bool split, bool want_K, 
     return EP_OK;
 }
 
-// The V-cycle's coarse correction starts each load path in FP32 (EP_AMG_PRECISE=1: in FP64); the
-// Newton loop switches to the precise V-cycle when an FP64 GMRES solve stalls with the FP32 one.
+// A load path starts with the V-cycle's coarse correction in FP32 (EP_AMG_PRECISE=1: in FP64) and
+// the preconditioner the options name; the Newton loop switches to the sparse LU (or, where that
+// cannot be set up, to the precise V-cycle) when an FP64 GMRES solve stalls with the FP32 V-cycle.
 static void precise_default(Ctx* c) {
     const char* v = std::getenv("EP_AMG_PRECISE");
     const int want = (v && std::atoi(v) == 1) ? 1 : 0;
     if (c->amg.precise && !want) c->amg_elastic = false;   // the FP32 coarse operators are stale
     c->amg.precise = want;
+    c->direct_mode = false;
 }
 
 static ep_status read_flags(Ctx* c, unsigned long long* n_plastic, bool* rm_err) {
@@ -467,6 +475,7 @@ void ep_default_opts(ep_opts* o) {
     o->deterministic = 0;
     o->asm_tile = 1;
     o->krylov_graphs = 1;
+    o->direct_fallback = 1;
 }
 
 const char* ep_status_str(int32_t s) {
@@ -507,6 +516,7 @@ ep_status ep_destroy(void* ctx) {
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     amg_free(c->amg);
+    direct_free(c->direct);
     cudaSetDevice(prev);
     delete c;
     return EP_OK;
@@ -872,6 +882,47 @@ static ep_status ensure_amg(Ctx* c) {
     return EP_OK;
 }
 
+// nodes factored together at the leaves of the nested dissection
+constexpr int DIRECT_LEAF = 64;
+// Relative tolerance of the Newton systems solved with the sparse LU (one to three GMRES iterations
+// with FP64 fronts).  Near a limit load the tangent is nearly singular: the oracle's FP64 direct
+// solves follow the homogeneous branch, while GMRES stopped at 1e-10 left O(1) errors in the Newton
+// step along the soft modes and the iteration diverged (measured, 256x256 column at 0.98 t_lim).
+constexpr double DIRECT_ETA = 1e-13;
+
+// The sparse LU's symbolic analysis (host) and device memory, on first use; false (reason in
+// c->direct.why) when the factors would not fit in 60% of the free device memory.
+static bool ensure_direct(Ctx* c) {
+    if (c->direct.ready) return true;
+    if (c->direct.refused) return false;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::string err;
+    if (!direct_analyse(c->dim, c->n_nodes, c->h_row_ptr.data(), c->h_col_idx.data(), c->h_coords.data(), DIRECT_LEAF,
+                        c->direct.plan, err)) {
+        c->direct.refused = true;
+        c->direct.why = err;
+        return false;
+    }
+    // fronts in FP64 (EP_DIRECT_FP32=1: FP32, 1/30 of the factorisation time, but GMRES then needs
+    // tens of iterations on a nearly singular tangent where FP64 fronts need one to three)
+    const char* f32 = std::getenv("EP_DIRECT_FP32");
+    c->direct.fp64 = (f32 && std::atoi(f32) == 1) ? 0 : 1;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    if (!direct_setup(c->direct, (int64_t)(0.6 * (double)fr))) return false;
+    c->kw.direct = &c->direct;
+    c->direct_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (c->verbose) {
+        const DirectPlan& P = c->direct.plan;
+        int mmax = 0;
+        for (int v : P.lvl_mmax) mmax = std::max(mmax, v);
+        std::fprintf(stderr, "[ep] sparse LU: %d fronts on %zu levels, largest front %d, %s factors %.1f MiB, %.2f GFLOP, "
+                     "setup %.1f ms\n", P.n_fronts, P.level_ptr.size() - 1, mmax, c->direct.fp64 ? "FP64" : "FP32",
+                     (double)P.factor_vals() * (c->direct.fp64 ? 8.0 : 4.0) / 1048576.0, P.flops * 1e-9, c->direct_setup_ms);
+    }
+    return true;
+}
+
 ep_status ep_get_info(const void* ctx, ep_info* info) {
     if (!ctx || !info) return EP_ERR_INVALID_ARG;
     const Ctx* c = static_cast<const Ctx*>(ctx);
@@ -1054,10 +1105,20 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
     c->deterministic = opts->deterministic ? 1 : 0;
     c->amg.deterministic = c->deterministic;
     c->kw.graphs = opts->krylov_graphs ? 1 : 0;
+    if (opts->precond < 0 || opts->precond > 3) {
+        c->err = "precond must be 0, 1, 2 or 3";
+        return EP_ERR_INVALID_ARG;
+    }
     if (opts->precond == 2) {
         ep_status st = ensure_amg(c);
         if (st != EP_OK) return st;
     }
+    if (opts->precond == 3 && !ensure_direct(c)) {
+        c->err = c->direct.why;
+        return EP_ERR_STATE;
+    }
+    // the sparse LU is nonsymmetric in rounding: it preconditions GMRES
+    const int lmethod = opts->precond == 3 ? 3 : krylov_method(c, *opts);
     CK(cudaMemcpyAsync(c->r, b, sizeof(double) * c->n_dof, b_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->stream));
     c->kw.galerkin = 1;
@@ -1068,15 +1129,15 @@ ep_status ep_linear_solve(void* ctx, const double* b, int32_t b_is_device, const
         const BsrF A = bsr_dev(c, (const float*)c->K32);
         CK(vec_cvt_f32(c->r, c->r32, c->n_dof, c->stream));
         CK(krylov_precond(A, c->kw, opts->precond, c->stream));
-        CK(krylov_solve(A, c->kw, c->r32, krylov_method(c, *opts), opts->krylov_rtol, opts->krylov_maxit, c->stream,
-                        &its, &rel, &status));
+        CK(krylov_solve(A, c->kw, c->r32, lmethod, opts->krylov_rtol, opts->krylov_maxit, c->stream, &its, &rel,
+                        &status));
         CK(vec_cvt_f64(c->kw.f.x, c->kw.d.x, c->n_dof, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } else {
         const BsrDev A = bsr_dev(c, (const double*)c->Kt);
         CK(krylov_precond(A, c->kw, opts->precond, c->stream));
-        CK(krylov_solve(A, c->kw, c->r, krylov_method(c, *opts), opts->krylov_rtol, opts->krylov_maxit, c->stream,
-                        &its, &rel, &status));
+        CK(krylov_solve(A, c->kw, c->r, lmethod, opts->krylov_rtol, opts->krylov_maxit, c->stream, &its, &rel,
+                        &status));
     }
     if (iterations) *iterations = its;
     if (rel_resid) *rel_resid = rel;
@@ -1228,11 +1289,19 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
     if (!(o.newton_rtol > 0.0) || o.newton_maxit < 1 || o.krylov_maxit < 1) return EP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
+    if (o.precond < 0 || o.precond > 3) {
+        c->err = "precond must be 0, 1, 2 or 3";
+        return EP_ERR_INVALID_ARG;
+    }
     if (o.precond == 2) {
         ep_status st = ensure_amg(c);
         if (st != EP_OK) return st;
     }
-    const int method = krylov_method(c, o);
+    if (o.precond == 3 && !ensure_direct(c)) {
+        c->err = c->direct.why;
+        return EP_ERR_STATE;
+    }
+    const int method = o.precond == 3 ? 3 : krylov_method(c, o);
     const bool split = o.split_elastic_cache != 0;
     const BsrDev A = bsr_dev(c, (const double*)c->Kt);
     if (mixed) {
@@ -1259,6 +1328,10 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         c->launches = 0;
         c->kw.launches = 0;
         c->amg.launches = 0;
+        c->direct.launches = 0;
+        c->direct.profile = o.profile;
+        const int dfac0 = c->direct.n_factor, dsol0 = c->direct.n_solve;
+        const double dfms0 = c->direct.factor_ms, dsms0 = c->direct.solve_ms;
         c->kw.spmv_n = 0;
         c->kw.spmv_ms = 0.0;
         c->amg.smooth0_ms = 0.0;
@@ -1295,6 +1368,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         // (warm_start = 2) the network's correction where it lowers the residual.  A step that
         // does not converge from the extrapolated start (a predictor past a change of the plastic
         // regime) is retried once from the unextrapolated one.
+        bool redo_step = false;   // the attempt runs again (the path switched to the sparse LU in it)
         for (int attempt = 0; attempt < 2; ++attempt) {
         bool extrapolated = false;
         rep.start = 0;
@@ -1365,7 +1439,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         // is expected to converge, so F is evaluated alone first and the tangent only if it does not.
         bool f_first = false;
         for (;;) {
-            use32 = mixed && !c->mixed_fallback && !fp64_step;
+            use32 = mixed && !c->mixed_fallback && !fp64_step && !c->direct_mode;
             CK(cudaEventRecord(c->ev[0], s));
             st = assemble(c, c->u_it, split, !f_first, use32);
             if (st != EP_OK) break;
@@ -1486,10 +1560,13 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             }
             // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
             // nonassociated model
-            const int m_it = (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
+            // the preconditioner of this solve: the sparse LU once the path has switched to it (with
+            // GMRES: its FP32 factors are not symmetric in rounding)
+            const int pk = c->direct_mode ? 3 : o.precond;
+            const int m_it = pk == 3 ? 3 : (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
             // the mixed path's FP64-tangent iterations solve with GMRES on the FP64 operator and an
             // FP32 basis (orthogonalisation, preconditioner and basis in FP32)
-            const bool basis32 = mixed && !use32 && m_it == 3 && !c->amg.precise;
+            const bool basis32 = mixed && !use32 && m_it == 3 && !c->amg.precise && !c->direct_mode;
             // an FP32 inner solve cannot go much below FP32 rounding; Newton (FP64 residual) refines further
             if (use32 || basis32) eta = std::max(eta, MIXED_ETA_MIN);
             // this solve aims at the final tolerance (its forcing term is the floor eta_min) after a
@@ -1521,47 +1598,92 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             }
             int kits = 0, kst = 0;
             double krel = 0.0;
+            const bool direct_before = c->direct_mode;
+            // The FP64 solve: the sparse LU once the path has switched to it (to DIRECT_ETA: near a
+            // limit load the tangent is nearly singular, and a loose forcing term leaves large errors
+            // along its soft modes, from which the semismooth iteration diverges), else the options'
+            // preconditioner; a GMRES solve that stalls with the V-cycle switches the path to the
+            // sparse LU, or where that cannot be set up to the precise V-cycle.
+            auto solve64 = [&](int& its_out, double& rel_out, int& st_out) -> ep_status {
+                // inside Newton a solve that needs far more than the usual count is not worth
+                // finishing: its partial progress is taken as an inexact step
+                const int maxit64 = std::min(o.krylov_maxit, std::max(2000, 20 * c->kw.last_its));
+                const double eta_d = o.krylov_rtol > 0.0 ? eta : std::min(eta, DIRECT_ETA);
+                if (c->direct_mode || pk == 3) {
+                    c->kw.stall_guard64 = 1;   // a solve at the rounding floor of the FP64 residual stops
+                    CK(krylov_precond(A, c->kw, 3, s));
+                    CK(krylov_solve(A, c->kw, c->r, 3, eta_d, maxit64, s, &its_out, &rel_out, &st_out));
+                    c->kw.stall_guard64 = 0;
+                    return EP_OK;
+                }
+                const bool can_switch = pk == 2 && c->amg_built && !c->amg.precise && m_it == 3;
+                c->kw.stall_guard64 = can_switch ? 1 : 0;
+                CK(krylov_precond(A, c->kw, pk, s));
+                CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &its_out, &rel_out, &st_out));
+                c->kw.stall_guard64 = 0;
+                if (st_out == EP_ERR_KRYLOV && can_switch) {
+                    // the V-cycle cannot resolve this tangent's soft modes (a limit load is near:
+                    // eigenvalues with negative real parts, around which restarted GMRES stalls)
+                    int k2 = 0;
+                    if (o.direct_fallback && ensure_direct(c)) {
+                        c->direct_mode = true;
+                        if (c->verbose)
+                            std::fprintf(stderr, "[ep] step %d: V-cycle GMRES stalled (rel %.3e after %d), sparse LU from here\n",
+                                         k, rel_out, its_out);
+                        // after earlier V-cycle iterations of this step the step starts again (see
+                        // below): nothing to solve at this iterate
+                        if (it == 0) {
+                            c->kw.stall_guard64 = 1;
+                            CK(krylov_precond(A, c->kw, 3, s));
+                            CK(krylov_solve(A, c->kw, c->r, 3, eta_d, maxit64, s, &k2, &rel_out, &st_out));
+                            c->kw.stall_guard64 = 0;
+                        }
+                    } else {
+                        c->amg.precise = 1;
+                        c->kw.galerkin = 1;
+                        c->amg_np = np_now;
+                        c->amg_elastic = false;
+                        if (c->verbose)
+                            std::fprintf(stderr, "[ep] step %d: FP32 V-cycle stalled (rel %.3e after %d), precise V-cycle from here%s%s\n",
+                                         k, rel_out, its_out, o.direct_fallback ? " (" : "",
+                                         o.direct_fallback ? (c->direct.why + ")").c_str() : "");
+                        CK(krylov_precond(A, c->kw, pk, s));
+                        CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &k2, &rel_out, &st_out));
+                        rep.precise = 1;
+                    }
+                    its_out += k2;
+                }
+                return EP_OK;
+            };
             // inside Newton a stagnating FP32-basis solve is cut short (the FP64 path takes over)
             c->kw.stall_guard = 1;
             if (use32) {
                 rep.newton_its_fp32 += 1;
                 // an FP32 solve that needs far more iterations than usual is stagnating on rounding
                 const int maxit32 = std::min(o.krylov_maxit, std::max(300, 4 * c->kw.last_its));
-                CK(krylov_precond(Af, c->kw, o.precond, s));
+                CK(krylov_precond(Af, c->kw, pk, s));
                 CK(krylov_solve(Af, c->kw, c->r32, m_it, eta, maxit32, s, &kits, &krel, &kst));
             } else if (basis32) {
                 const int maxit32 = std::min(o.krylov_maxit, std::max(300, 4 * c->kw.last_its));
-                CK(krylov_precond(A, c->kw, o.precond, s));
+                CK(krylov_precond(A, c->kw, pk, s));
                 CK(krylov_solve_fp32_basis(A, c->kw, c->r, eta, maxit32, s, &kits, &krel, &kst));
                 if (kst != EP_OK && !(krel < 0.5)) {   // no progress with the FP32 basis: the FP64 solve
                     int k2 = 0;
-                    CK(krylov_solve(A, c->kw, c->r, m_it, eta, o.krylov_maxit, s, &k2, &krel, &kst));
+                    st = solve64(k2, krel, kst);
+                    if (st != EP_OK) return st;
                     kits += k2;
                 }
                 if (kst != EP_OK && krel < 0.5) kst = EP_OK;   // partial progress: an inexact Newton step
             } else {
-                // inside Newton a solve that needs far more than the usual count is not worth
-                // finishing: its partial progress is taken as an inexact step
-                const int maxit64 = std::min(o.krylov_maxit, std::max(2000, 20 * c->kw.last_its));
-                c->kw.stall_guard64 = (o.precond == 2 && c->amg_built && !c->amg.precise && m_it == 3) ? 1 : 0;
-                CK(krylov_precond(A, c->kw, o.precond, s));
-                CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &kits, &krel, &kst));
-                c->kw.stall_guard64 = 0;
-                if (kst == EP_ERR_KRYLOV && o.precond == 2 && c->amg_built && !c->amg.precise && m_it == 3) {
-                    // the FP32 coarse correction cannot resolve this tangent's soft modes (a limit
-                    // load is near): FP64 coarse operators and residuals for the rest of the path
-                    c->amg.precise = 1;
-                    c->kw.galerkin = 1;
-                    c->amg_np = np_now;
-                    c->amg_elastic = false;
-                    if (c->verbose)
-                        std::fprintf(stderr, "[ep] step %d: FP32 V-cycle stalled (rel %.3e after %d), precise V-cycle from here\n",
-                                     k, krel, kits);
-                    int k2 = 0;
-                    CK(krylov_precond(A, c->kw, o.precond, s));
-                    CK(krylov_solve(A, c->kw, c->r, m_it, eta, maxit64, s, &k2, &krel, &kst));
-                    kits += k2;
-                    rep.precise = 1;
+                st = solve64(kits, krel, kst);
+                if (st != EP_OK) return st;
+            }
+            if (c->direct_mode || pk == 3) {
+                rep.direct = 1;
+                if (c->verbose) {
+                    unsigned int npert = 0;
+                    cudaMemcpy(&npert, c->direct.n_perturbed, sizeof(npert), cudaMemcpyDeviceToHost);
+                    std::fprintf(stderr, "[ep] step %d: sparse LU, %u perturbed pivots\n", k, npert);
                 }
             }
             if (c->amg.precise) rep.precise = 1;
@@ -1579,6 +1701,18 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
                 for (int j = std::max(0, n - 6); j < n; ++j)
                     std::fprintf(stderr, "[ep]   it %d rho %.6e alpha %.6e omega %.6e\n", j, h[j], h[c->kw.hist_len + j],
                                  h[2 * c->kw.hist_len + j]);
+            }
+            if (!direct_before && c->direct_mode && it > 0) {
+                // switched to the sparse LU after iterations with the V-cycle: the step starts again
+                // from its start iterate, every Newton step now solved accurately.  (Near the limit
+                // load the tangent has unstable modes: the non-homogeneous error a loose solve leaves
+                // in the iterate grows, and Newton can settle on another solution branch.)
+                CK(cudaEventSynchronize(c->ev[3]));
+                CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+                t_sol += ms;
+                redo_step = true;
+                if (c->verbose) std::fprintf(stderr, "[ep] step %d: again from the start iterate with the sparse LU\n", k);
+                break;
             }
             if (kst == EP_ERR_NAN) {
                 st = EP_ERR_NAN;
@@ -1606,6 +1740,11 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
             t_sol += ms;
             ++it;
+        }
+        if (redo_step) {
+            redo_step = false;
+            --attempt;
+            continue;
         }
         if (converged || !extrapolated ||
             (st != EP_ERR_NEWTON_NO_CONVERGENCE && st != EP_ERR_KRYLOV && st != EP_ERR_NAN))
@@ -1659,7 +1798,13 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
         CK(cudaStreamSynchronize(s));
         rep.t_step_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_step0).count();
         rep.status = st;
-        rep.launches = c->launches + c->kw.launches + c->amg.launches;
+        rep.launches = c->launches + c->kw.launches + c->amg.launches + c->direct.launches;
+        rep.n_direct_factor = c->direct.n_factor - dfac0;
+        rep.n_direct_solve = c->direct.n_solve - dsol0;
+        rep.t_direct_factor_ms = c->direct.factor_ms - dfms0;
+        rep.t_direct_solve_ms = c->direct.solve_ms - dsms0;
+        rep.direct_factor_flop = c->direct.ready ? c->direct.plan.flops : 0.0;
+        rep.direct_solve_bytes = c->direct.ready ? c->direct.solve_bytes : 0.0;
         rep.n_spmv = c->kw.spmv_n;
         rep.t_spmv_kernel_ms = c->kw.spmv_ms;
         rep.n_smooth0 = c->amg.smooth0_n;

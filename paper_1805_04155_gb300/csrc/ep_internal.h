@@ -189,6 +189,7 @@ struct KrylovRec {
 };
 
 struct AmgDev;
+struct DirectDev;
 
 // Solver vectors of one precision.
 template <class T>
@@ -213,6 +214,8 @@ struct KrylovWork {
     KrylovRec* rec_host;     // pinned host mirror
     AmgDev* amg;             // AMG hierarchy (precond 2), owned by the context; null if not built
     int use_amg;             // set by krylov_precond: 1 when the current preconditioner is the AMG V-cycle
+    DirectDev* direct = nullptr;   // sparse LU (precond 3), owned by the context; null if not set up
+    int use_direct = 0;      // set by krylov_precond: 1 when the current preconditioner is the sparse LU
     int gm_m;                // GMRES restart length (<= GM_M)
     int galerkin;            // 1: recompute the AMG coarse operators from the current matrix in krylov_precond
     int last_its;            // iterations of the previous solve: sizes the first chunk of launches of the next
@@ -244,7 +247,8 @@ constexpr int GM_M = 128;    // largest GMRES restart length (buffers); the run-
 cudaError_t krylov_alloc(KrylovWork& w, int64_t n_rows, int dim, int maxit_cap, int num_sms);
 cudaError_t krylov_alloc_f32(KrylovWork& w, int64_t n_rows, int dim);
 void krylov_free(KrylovWork& w);
-// Preconditioner of A (kind 0 Jacobi, 1 block Jacobi, 2 AMG with block-Jacobi smoothing) in A's precision.
+// Preconditioner of A (kind 0 Jacobi, 1 block Jacobi, 2 AMG with block-Jacobi smoothing, 3 the sparse
+// LU of w.direct, which must be set up) in A's precision.
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s);
 cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t s);
 // Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab, 3 GMRES(m).

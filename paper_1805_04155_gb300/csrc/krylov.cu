@@ -28,6 +28,7 @@
 #include <cstdlib>
 
 #include "amg.h"
+#include "direct.h"
 #include "ep_internal.h"
 #include "pdl.cuh"
 
@@ -595,9 +596,16 @@ static cudaError_t precond_t(const BsrT<T>& A, KrylovWork& w, int kind, cudaStre
     else k_precond<3, T><<<g, 256, 0, s>>>(A, minv, bj);
     w.launches += 1;
     w.use_amg = (kind == 2 && w.amg) ? 1 : 0;
+    w.use_direct = 0;
     if (w.use_amg) {
         cudaError_t e = amg_refresh(*w.amg, A, minv, w.galerkin, s);
         if (e != cudaSuccess) return e;
+    }
+    if (kind == 3) {
+        if (!w.direct || !w.direct->ready) return cudaErrorInvalidValue;
+        cudaError_t e = direct_factor(*w.direct, A, s);
+        if (e != cudaSuccess) return e;
+        w.use_direct = 1;
     }
     return cudaGetLastError();
 }
@@ -630,6 +638,13 @@ static cudaError_t amg_apply_t(KrylovWork& w, const BsrDev& A, const float* in, 
     const BsrF pat{A.n_rows, A.dim, A.row_ptr, A.col_idx, A.diag_slot, nullptr, A.free_dof};
     return amg_apply(*w.amg, pat, in, out, rec, s);
 }
+// out = M^-1 in with the current operator preconditioner: the sparse LU (precond 3) or the V-cycle
+template <class TA, class TV>
+static cudaError_t prec_apply_t(KrylovWork& w, const BsrT<TA>& A, const TV* in, TV* out, const KrylovRec* rec,
+                                cudaStream_t s) {
+    if (w.use_direct) return direct_solve(*w.direct, in, out, A.free_dof, rec, s);
+    return amg_apply_t(w, A, in, out, rec, s);
+}
 
 template <int D, class T>
 static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int method, double rtol, int maxit,
@@ -650,7 +665,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
     a.rec = w.rec;
     a.rtol2 = rtol * rtol;
     a.maxit = maxit;
-    a.amg = (w.use_amg && w.amg) ? 1 : 0;
+    a.amg = ((w.use_amg && w.amg) || (w.use_direct && w.direct)) ? 1 : 0;   // an operator preconditioner
     const int grid = w.grid;
     const bool bicg = (method == 2);
     // Iterations enqueued between two polls of the device record: the first chunk covers the
@@ -674,7 +689,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
     launch_pdl(k_init<D, T>, dim3(grid), dim3(VB), 0, s, a, b, bicg ? 1 : 0, restart > 0 ? 1 : 0, restart);
     w.launches += 1;
     if (a.amg && !bicg) {   // z = M^-1 r0, then (r, z)
-        amg_apply_t(w, A, vv.r, vv.z, w.rec, s);
+        prec_apply_t(w, A, vv.r, vv.z, w.rec, s);
         launch_pdl(k_dot<T>, dim3(grid), dim3(VB), 0, s, a, vv.r, vv.z, w.n, P_RZ);
         w.launches += 1;
     }
@@ -683,7 +698,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
         const int first = it;
         const int stop = std::min(it + chunk, a.maxit + 1);
         int nev = 0;
-        if (a.amg) w.amg->nev = 0;
+        if (a.amg && w.use_amg) w.amg->nev = 0;
         for (; it < stop; ++it) {
             // profiling events: as many iterations of the chunk as the event array holds
             const bool ev_ok = w.profile && nev + (bicg ? 4 : 2) <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
@@ -695,18 +710,18 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
                 launch_pdl(k_cg_update<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
                 w.launches += 3;
                 if (a.amg) {
-                    amg_apply_t(w, A, vv.r, vv.z, w.rec, s);
+                    prec_apply_t(w, A, vv.r, vv.z, w.rec, s);
                     launch_pdl(k_dot<T>, dim3(grid), dim3(VB), 0, s, a, vv.r, vv.z, w.n, P_RZ);
                     w.launches += 1;
                 }
             } else {
                 launch_pdl(k_bicg_p<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
-                if (a.amg) amg_apply_t(w, A, vv.p, vv.phat, w.rec, s);
+                if (a.amg) prec_apply_t(w, A, vv.p, vv.phat, w.rec, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D, T, T, T>(A, vv.phat, vv.v, vv.rhat, a.part + (int64_t)P_PQ * a.nparts, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_pdl(k_bicg_s<D, T>, dim3(grid), dim3(VB), 0, s, a, it);
-                if (a.amg) amg_apply_t(w, A, vv.s, vv.shat, w.rec, s);
+                if (a.amg) prec_apply_t(w, A, vv.s, vv.shat, w.rec, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
                 launch_spmv<D, T, T, T>(A, vv.shat, vv.t, nullptr, nullptr, w.rec, grid, s);
                 if (ev_ok) cudaEventRecord(w.ev[nev++], s);
@@ -725,7 +740,7 @@ static cudaError_t solve_t(const BsrT<T>& A, KrylovWork& w, const T* b, int meth
             // SpMVs of iterations before the converged one did work; later ones exited at once
             const int done_at = w.rec_host->done ? w.rec_host->its : it;
             const int per = bicg ? 2 : 1;
-            if (a.amg) amg_profile_collect(*w.amg, per * std::max(0, done_at - first));
+            if (a.amg && w.use_amg) amg_profile_collect(*w.amg, per * std::max(0, done_at - first));
             for (int j = 0; j < nev / 2; ++j) {
                 if (first + j / per >= done_at) break;
                 float ms = 0.f;
@@ -1109,10 +1124,12 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
     a.m = std::max(2, std::min(GM_M, w.gm_m > 0 ? w.gm_m : 30));
     const int grid = w.grid;
     const bool use_amg = w.use_amg && w.amg;
+    const bool use_direct = w.use_direct && w.direct;
+    const bool use_op = use_amg || use_direct;   // an operator preconditioner (z = M^-1 v by its own kernels)
     int total = 0;
     // the launches of iteration j of a cycle (direct, or into a capture)
     auto issue = [&](const GArgs<TX, TV>& ga, int j, cudaStream_t st, int& nev) {
-        if (use_amg) amg_apply_t(w, A, ga.V + (int64_t)j * w.n, ga.z, w.rec, st);
+        if (use_op) prec_apply_t(w, A, ga.V + (int64_t)j * w.n, ga.z, w.rec, st);
         else launch_pdl(k_gm_prec<D, TX, TV>, dim3(grid), dim3(VB), 0, st, ga, j);
         const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
         if (ev_ok) cudaEventRecord(w.ev[nev++], st);
@@ -1131,7 +1148,7 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
         // graphs are valid for one operator, solver precision, preconditioner and restart length
         const long long key = ((long long)a.m << 32) | ((long long)D << 24) | ((long long)sizeof(TA) << 16) |
                               ((long long)sizeof(TX) << 12) | ((long long)sizeof(TV) << 8) |
-                              (use_amg ? 2 : 0) | (use_amg && w.amg->precise ? 1 : 0);
+                              (use_amg ? 2 : 0) | (use_amg && w.amg->precise ? 1 : 0) | (use_direct ? 4 : 0);
         if (key != w.gkey || (const void*)A.vals != w.gkey_ptr) {
             drop_graphs(w);
             w.gkey = key;
@@ -1144,7 +1161,11 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
     }
     KrylovRec last{};
     double rr_prev_end = 0.0;   // residual estimate ||r||^2 at the end of the previous cycle
-    int n_verify = sizeof(TV) == 4 ? 1 : 0;   // FP32 basis: re-check a converged estimate once (see solve_t)
+    // FP32 basis: re-check a converged estimate once (see solve_t).  Sparse LU: its FP32 solve is not
+    // linear in rounding, so the update M^-1 (V y) differs from the combination of the M^-1 v_j the
+    // Arnoldi relation holds for by O(u32) of the correction; a tight solve restarts once from its x
+    // (FP64 residual b - A x; a second cycle refines what the FP32 factors left)
+    int n_verify = (sizeof(TV) == 4 || (use_direct && rtol < 1e-5)) ? 1 : 0;
     for (int cycle = 0;; ++cycle) {
         a.cold = (cycle == 0);
         if (cycle > 0) {
@@ -1172,6 +1193,7 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
                         GArgs<TX, TV> ac = a;
                         ac.dyn = w.gdyn;
                         const int l_save = w.launches, la_save = use_amg ? w.amg->launches : 0;
+                        const int ld_save = use_direct ? w.direct->launches : 0;
                         cudaGraph_t g = nullptr;
                         cudaError_t e = cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal);
                         if (e != cudaSuccess) return e;
@@ -1181,9 +1203,11 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
                         e = cudaGraphInstantiate(&w.gexec[j], g, 0);
                         cudaGraphDestroy(g);
                         if (e != cudaSuccess) return e;
-                        w.gexec_launches[j] = (w.launches - l_save) + (use_amg ? w.amg->launches - la_save : 0);
+                        w.gexec_launches[j] = (w.launches - l_save) + (use_amg ? w.amg->launches - la_save : 0) +
+                                              (use_direct ? w.direct->launches - ld_save : 0);
                         w.launches = l_save;
                         if (use_amg) w.amg->launches = la_save;
+                        if (use_direct) w.direct->launches = ld_save;
                     }
                     cudaError_t e = cudaGraphLaunch(w.gexec[j], s);
                     if (e != cudaSuccess) return e;
@@ -1202,6 +1226,8 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
             t_enq += std::chrono::duration<double, std::milli>(t1 - t0).count();
             t_wait += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
             last = *w.rec_host;
+            // sparse-LU solves that did work (replayed graphs included)
+            if (use_direct) w.direct->n_solve += std::max(0, std::min(j1, last.its) - j0);
             if (w.profile) {
                 if (use_amg) amg_profile_collect(*w.amg, std::max(0, std::min(j1, last.its) - j0));
                 for (int q = 0; q < nev / 2 && j0 + q < last.its; ++q) {
@@ -1218,9 +1244,10 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
             std::fprintf(stderr, "[ep]   gmres cycle %d: its %d, host enqueue %.3f ms, wait %.3f ms\n", cycle,
                          last.its, t_enq, t_wait);
         if (last.its > 0) {
-            if (use_amg) {
+            if (use_op) {
                 launch_pdl(k_gm_combine<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, last.its, vv.q);
-                amg_apply_t(w, A, vv.q, vv.z, nullptr, s);
+                prec_apply_t(w, A, vv.q, vv.z, nullptr, s);
+                if (use_direct) w.direct->n_solve += 1;
                 launch_pdl(k_axpy_plain<TX, TV>, dim3(grid), dim3(VB), 0, s, vx.x, vv.z, w.n);
                 w.launches += 2;
             } else {

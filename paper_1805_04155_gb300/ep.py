@@ -64,7 +64,7 @@ class ep_opts(C.Structure):
                 ("krylov", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
                 ("precond", C.c_int32), ("split_elastic_cache", C.c_int32), ("warm_start", C.c_int32),
                 ("profile", C.c_int32), ("deterministic", C.c_int32), ("asm_tile", C.c_int32),
-                ("krylov_graphs", C.c_int32)]
+                ("krylov_graphs", C.c_int32), ("direct_fallback", C.c_int32)]
 
 
 class ep_step_report(C.Structure):
@@ -75,7 +75,10 @@ class ep_step_report(C.Structure):
                 ("t_spmv_kernel_ms", C.c_double), ("n_plastic_assembled", C.c_int64),
                 ("newton_its_fp32", C.c_int32), ("start", C.c_int32), ("n_learned", C.c_int32),
                 ("n_smooth0", C.c_int32), ("t_smooth0_kernel_ms", C.c_double),
-                ("n_plastic_elem_assembled", C.c_int64), ("precise", C.c_int32), ("reserved", C.c_int32)]
+                ("n_plastic_elem_assembled", C.c_int64), ("precise", C.c_int32), ("direct", C.c_int32),
+                ("n_direct_factor", C.c_int32), ("n_direct_solve", C.c_int32), ("t_direct_factor_ms", C.c_double),
+                ("t_direct_solve_ms", C.c_double), ("direct_factor_flop", C.c_double),
+                ("direct_solve_bytes", C.c_double)]
 
 
 class ep_info(C.Structure):

@@ -113,3 +113,52 @@ void shim_amg_inv_copy(void* h, int l, double* dinv, double* dense) {
 }
 
 }  // extern "C"
+
+// -- sparse LU: symbolic analysis ----------------------------------------------------------------
+#include "../paper_1805_04155_gb300/csrc/direct.h"
+
+extern "C" {
+
+// Analyses the pattern; a heap plan (free with shim_direct_free) or null.
+void* shim_direct_analyse(int dim, int64_t n_nodes, const int32_t* row_ptr, const int32_t* col_idx,
+                          const double* coords, int leaf) {
+    auto* P = new ep::DirectPlan();
+    std::string err;
+    if (!ep::direct_analyse(dim, n_nodes, row_ptr, col_idx, coords, leaf, *P, err)) {
+        delete P;
+        return nullptr;
+    }
+    return P;
+}
+
+void shim_direct_free(void* h) { delete static_cast<ep::DirectPlan*>(h); }
+
+// n_fronts, n_levels, length of the node lists, front values, update-vector values
+void shim_direct_sizes(void* h, int64_t* out) {
+    const ep::DirectPlan& P = *static_cast<ep::DirectPlan*>(h);
+    out[0] = P.n_fronts;
+    out[1] = (int64_t)P.level_ptr.size() - 1;
+    out[2] = (int64_t)P.nodes.size();
+    out[3] = P.factor_vals();
+    out[4] = P.v_off.back();
+}
+
+void shim_direct_copy(void* h, int32_t* level_ptr, int32_t* parent, int32_t* npiv, int32_t* nupd, int64_t* node_off,
+                      int32_t* nodes, int32_t* umap, int32_t* blk_front, int32_t* blk_row, int32_t* blk_col,
+                      int32_t* pos, double* flops) {
+    const ep::DirectPlan& P = *static_cast<ep::DirectPlan*>(h);
+    std::copy(P.level_ptr.begin(), P.level_ptr.end(), level_ptr);
+    std::copy(P.parent.begin(), P.parent.end(), parent);
+    std::copy(P.npiv.begin(), P.npiv.end(), npiv);
+    std::copy(P.nupd.begin(), P.nupd.end(), nupd);
+    std::copy(P.node_off.begin(), P.node_off.end(), node_off);
+    std::copy(P.nodes.begin(), P.nodes.end(), nodes);
+    std::copy(P.umap.begin(), P.umap.end(), umap);
+    std::copy(P.blk_front.begin(), P.blk_front.end(), blk_front);
+    std::copy(P.blk_row.begin(), P.blk_row.end(), blk_row);
+    std::copy(P.blk_col.begin(), P.blk_col.end(), blk_col);
+    std::copy(P.pos.begin(), P.pos.end(), pos);
+    *flops = P.flops;
+}
+
+}  // extern "C"

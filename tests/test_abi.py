@@ -49,10 +49,11 @@ def test_struct_layouts_match_header(libpath):
     import paper_1805_04155_gb300.ep as ep
     assert ctypes.sizeof(ep.ep_mesh) == 4 + 4 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(ep.ep_material) == 8 + 8 * 8
-    assert ctypes.sizeof(ep.ep_opts) == 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4 + 4 + 4   # ..., asm_tile, krylov_graphs
-    assert ctypes.sizeof(ep.ep_step_report) == 4 + 4 + 8 + 8 * 4 + 4 * 4 + 8 * 2 + 8 + 4 * 4 + 8 + 8 + 4 + 4
+    # ..., asm_tile, krylov_graphs, direct_fallback and 4 bytes of padding to the struct's 8-byte alignment
+    assert ctypes.sizeof(ep.ep_opts) == 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4 + 4 + 4 + 4 + 4
+    assert ctypes.sizeof(ep.ep_step_report) == 4 + 4 + 8 + 8 * 4 + 4 * 4 + 8 * 2 + 8 + 4 * 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 * 4
     o = ep.default_opts()   # calls into the library (host only)
-    assert o.newton_rtol == 1e-10 and o.precond == 2 and o.split_elastic_cache == 1
+    assert o.newton_rtol == 1e-10 and o.precond == 2 and o.split_elastic_cache == 1 and o.direct_fallback == 1
 
 
 def test_create_rejects_bad_input_without_gpu_work(libpath):

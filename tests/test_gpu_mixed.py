@@ -171,10 +171,10 @@ def test_mixed_load_path_p2_tet_strip(ep):
 
 
 def test_mixed_full_size_p2_matches_fp64(ep):
-    """The benchmark workload (256x256 P2, 40 steps) in both precisions: the same converged path."""
+    """The 256x256 P2 column to 0.95 t_lim (40 steps) in both precisions: the same converged path."""
     from oracle.newton import homogeneous_column
     from synthetic import p2_plane_dp
-    prob = p2_plane_dp()
+    prob = p2_plane_dp(load_fraction=0.95)
     out = {}
     for prec in (ep.EP_FP64, ep.EP_MIXED):
         ctx = ep.Context.from_problem(prob)

@@ -238,10 +238,11 @@ def test_precise_vcycle_load_path(ep, monkeypatch, model, prob_name):
 
 
 def test_load_path_p2_full_size_all_steps(ep):
-    """The benchmark workload (256x256 P2, 40 steps) end to end, against the one-point oracle."""
+    """The 256x256 P2 column to 0.95 t_lim (40 steps, V-cycle GMRES throughout) end to end, against the
+    one-point oracle (0.98 t_lim: tests/test_gpu_direct.py)."""
     from oracle.newton import homogeneous_column
     from synthetic import p2_plane_dp
-    prob = p2_plane_dp()
+    prob = p2_plane_dp(load_fraction=0.95)
     ctx = ep.Context.from_problem(prob)
     reps = ctx.solve_load_path(prob.zeta, ep.default_opts(newton_rtol=1e-10))
     sig = ctx.get(ep.EP_STRESS)
@@ -264,10 +265,11 @@ def test_load_path_p2_tet_strip(ep):
 
 
 def test_homogeneous_column_full_size_p2(ep):
-    """Full-size P2 workload (256x256, 917504 points): every point equals the one-point oracle."""
+    """Full-size P2 column (256x256, 917504 points) to 0.95 t_lim in 10 steps: every point equals the
+    one-point oracle."""
     from oracle.newton import homogeneous_column
     from synthetic import p2_plane_dp
-    prob = p2_plane_dp()
+    prob = p2_plane_dp(load_fraction=0.95)
     ctx = ep.Context.from_problem(prob)
     zs = prob.zeta[::4]           # 10 of the 40 steps, same end point
     reps = ctx.solve_load_path(zs, ep.default_opts(newton_rtol=1e-10))
@@ -350,7 +352,7 @@ def test_resume_from_saved_state(ep):
     FP64 atomics make the summation order, hence the last bits, differ from run to run, so the
     two runs agree to the accuracy the Newton tolerance fixes (tight here), not bit for bit."""
     from synthetic import p2_plane_dp
-    prob = p2_plane_dp(n=6, n_steps=10)
+    prob = p2_plane_dp(n=6, n_steps=10, load_fraction=0.95)
     opts = ep.default_opts(newton_rtol=1e-13, newton_maxit=40, warm_start=0)
     a = ep.Context.from_problem(prob)
     a.solve_load_path(prob.zeta, opts)

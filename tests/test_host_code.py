@@ -29,7 +29,8 @@ def shim(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("shim") / "libhostshim.so")
     cmd = [nvcc, "-std=c++17", "-O1", "-Xcompiler", "-fPIC,-fopenmp", "-shared", "-x", "c++",
            os.path.join(ROOT, "tests", "host_shim.cpp"), os.path.join(SRC, "pattern_host.cpp"),
-           os.path.join(SRC, "elements_host.cpp"), os.path.join(SRC, "amg_host.cpp"), "-I", os.path.join(ROOT, "include"),
+           os.path.join(SRC, "elements_host.cpp"), os.path.join(SRC, "amg_host.cpp"), os.path.join(SRC, "direct_host.cpp"),
+           "-I", os.path.join(ROOT, "include"),
            "-o", out]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
@@ -49,6 +50,11 @@ def shim(tmp_path_factory):
     lib.shim_amg_mat_copy.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.shim_amg_inv_sizes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.shim_amg_inv_copy.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    lib.shim_direct_analyse.argtypes = [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    lib.shim_direct_analyse.restype = C.c_void_p
+    lib.shim_direct_free.argtypes = [C.c_void_p]
+    lib.shim_direct_sizes.argtypes = [C.c_void_p, C.c_void_p]
+    lib.shim_direct_copy.argtypes = [C.c_void_p] + [C.c_void_p] * 12
     return lib
 
 
@@ -223,3 +229,159 @@ def test_amg_setup_galerkin_hierarchy(shim, make):
         assert all(a > b for a, b in zip(sizes, sizes[1:])) and sizes[-1] <= 600
     finally:
         shim.shim_amg_free(h)
+
+
+# -- sparse LU: symbolic analysis ----------------------------------------------------------------
+
+def _direct_plan(shim, dim, n_nodes, rp, ci, coords, leaf):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    h = shim.shim_direct_analyse(dim, n_nodes, rp.ctypes.data, ci.ctypes.data, coords.ctypes.data, leaf)
+    assert h
+    try:
+        sz = np.zeros(5, dtype=np.int64)
+        shim.shim_direct_sizes(h, sz.ctypes.data)
+        nf, nl, nlist = int(sz[0]), int(sz[1]), int(sz[2])
+        P = dict(level_ptr=np.zeros(nl + 1, np.int32), parent=np.zeros(nf, np.int32), npiv=np.zeros(nf, np.int32),
+                 nupd=np.zeros(nf, np.int32), node_off=np.zeros(nf + 1, np.int64), nodes=np.zeros(nlist, np.int32),
+                 umap=np.zeros(nlist, np.int32), blk_front=np.zeros(len(ci), np.int32),
+                 blk_row=np.zeros(len(ci), np.int32), blk_col=np.zeros(len(ci), np.int32),
+                 pos=np.zeros(n_nodes, np.int32))
+        flops = C.c_double(0.0)
+        shim.shim_direct_copy(h, *[P[k].ctypes.data for k in ("level_ptr", "parent", "npiv", "nupd", "node_off",
+                                                               "nodes", "umap", "blk_front", "blk_row", "blk_col",
+                                                               "pos")], C.byref(flops))
+        P["flops"] = flops.value
+    finally:
+        shim.shim_direct_free(h)
+    P["n_fronts"] = nf
+    return P
+
+
+def _direct_cases():
+    from synthetic import structured_mesh
+    out = []
+    for et, dim, n in (("P2", 2, (7, 5)), ("P1", 2, (9, 9)), ("Q1", 3, (4, 3, 3)), ("P2", 3, (2, 2, 2))):
+        m = structured_mesh(et, dim, n, (10.0,) * dim)
+        out.append((f"{et}-{dim}d", dim, m.n_nodes, m.elem, m.coords))
+    # two meshes with overlapping coordinates in one graph (a batch): disconnected components
+    m = structured_mesh("Q2", 2, (3, 4), (10.0, 10.0))
+    elem = np.vstack([m.elem, m.elem + m.n_nodes])
+    out.append(("batch-Q2", 2, 2 * m.n_nodes, elem, np.vstack([m.coords, m.coords + 0.5])))
+    return out
+
+
+@pytest.mark.parametrize("case", _direct_cases(), ids=lambda c: c[0])
+@pytest.mark.parametrize("leaf", [1, 8, 40])
+def test_direct_analysis_fronts_are_the_filled_graph(shim, case, leaf):
+    """The nested-dissection plan against brute-force symbolic elimination: the order is a permutation,
+    every front's update set is exactly the set of later nodes its pivots are joined to in the filled
+    graph, children precede parents and fit into them, and every block lands in the front of its
+    first-eliminated node."""
+    _, dim, n, elem, coords = case
+    st, rp, ci, _ = _pattern(shim, n, elem)
+    assert st == 1
+    P = _direct_plan(shim, dim, n, rp, ci, coords, leaf)
+    pos = P["pos"]
+    assert sorted(pos.tolist()) == list(range(n))
+    # filled graph by elimination in pos order
+    order = np.argsort(pos)
+    higher = [set(int(w) for w in ci[rp[v]:rp[v + 1]] if pos[w] > pos[v]) for v in range(n)]
+    for v in order:
+        hv = sorted(higher[v], key=lambda w: pos[w])
+        for i, a in enumerate(hv):
+            higher[a].update(hv[i + 1:])
+    nf = P["n_fronts"]
+    lists = [P["nodes"][P["node_off"][s]:P["node_off"][s + 1]] for s in range(nf)]
+    assert P["level_ptr"][0] == 0 and P["level_ptr"][-1] == nf
+    seen = 0
+    for s in range(nf):
+        k, u = P["npiv"][s], P["nupd"][s]
+        piv, upd = lists[s][:k].tolist(), lists[s][k:].tolist()
+        assert k >= 1 and len(upd) == u
+        assert sorted(pos[piv].tolist()) == list(range(seen, seen + k))    # processing order = elimination order
+        seen += k
+        want = set().union(*[higher[v] for v in piv]) - set(piv)
+        assert set(upd) == want
+        assert all(pos[a] < pos[b] for a, b in zip(upd, upd[1:]))
+        p = P["parent"][s]
+        if p >= 0:
+            assert p > s
+            plist = lists[p].tolist()
+            for a, w in enumerate(upd):
+                assert plist[P["umap"][P["node_off"][s] + k + a]] == w
+        else:
+            assert u == 0
+    assert seen == n
+    # blocks
+    for r in range(n):
+        for b in range(rp[r], rp[r + 1]):
+            c = ci[b]
+            s = P["blk_front"][b]
+            lst = lists[s]
+            assert lst[P["blk_row"][b]] == r and lst[P["blk_col"][b]] == c
+            first = r if pos[r] <= pos[c] else c
+            assert first in lst[:P["npiv"][s]].tolist()
+
+
+def test_direct_plan_factorises_exactly(shim):
+    """A plain numpy multifrontal pass over the plan (assemble the blocks, partial LU without row
+    exchanges, extend-add into the parent) gives factors with L U = P A P^T for a nonsymmetric,
+    diagonally dominant matrix on a P2 pattern; nested dissection beats the natural order on fill."""
+    from synthetic import structured_mesh
+    dim = 2
+    m = structured_mesh("P2", 2, (6, 6), (10.0, 10.0))
+    n = m.n_nodes
+    st, rp, ci, _ = _pattern(shim, n, m.elem)
+    rng = np.random.default_rng(7)
+    nnzb = len(ci)
+    vals = rng.uniform(-1.0, 1.0, (nnzb, dim, dim))
+    A = np.zeros((n * dim, n * dim))
+    for r in range(n):
+        for b in range(rp[r], rp[r + 1]):
+            A[r * dim:(r + 1) * dim, ci[b] * dim:(ci[b] + 1) * dim] = vals[b]
+    A += np.diag(np.abs(A).sum(axis=1) + 1.0)
+    for r in range(n):
+        for b in range(rp[r], rp[r + 1]):
+            if ci[b] == r:
+                vals[b] = A[r * dim:(r + 1) * dim, r * dim:(r + 1) * dim]
+    P = _direct_plan(shim, dim, n, rp, ci, m.coords, 8)
+    nf = P["n_fronts"]
+    F = []
+    for s in range(nf):
+        sz = (P["npiv"][s] + P["nupd"][s]) * dim
+        F.append(np.zeros((sz, sz)))
+    for r in range(n):
+        for b in range(rp[r], rp[r + 1]):
+            s = P["blk_front"][b]
+            i, j = P["blk_row"][b] * dim, P["blk_col"][b] * dim
+            F[s][i:i + dim, j:j + dim] = vals[b]
+    dof = lambda node, c: node * dim + c
+    L = np.eye(n * dim)
+    U = np.zeros((n * dim, n * dim))
+    gpos = np.zeros(n * dim, dtype=np.int64)   # global DOF -> position in the permuted order
+    for v in range(n):
+        for c in range(dim):
+            gpos[dof(v, c)] = P["pos"][v] * dim + c
+    for s in range(nf):
+        lst = P["nodes"][P["node_off"][s]:P["node_off"][s + 1]]
+        gl = np.array([gpos[dof(v, c)] for v in lst for c in range(dim)])
+        k = P["npiv"][s] * dim
+        Fs = F[s]
+        for t in range(k):
+            Fs[t + 1:, t] /= Fs[t, t]
+            Fs[t + 1:, t + 1:] -= np.outer(Fs[t + 1:, t], Fs[t, t + 1:])
+        for t in range(k):
+            U[gl[t], gl[t:]] = Fs[t, t:]
+            L[gl[t + 1:], gl[t]] = Fs[t + 1:, t]
+        p = P["parent"][s]
+        if p >= 0:
+            um = P["umap"][P["node_off"][s] + P["npiv"][s]:P["node_off"][s + 1]]
+            idx = np.array([a * dim + c for a in um for c in range(dim)])
+            F[p][np.ix_(idx, idx)] += Fs[k:, k:]
+    perm = np.argsort(gpos)
+    Ap = A[np.ix_(perm, perm)]
+    assert np.abs(L @ U - Ap).max() <= 1e-12 * np.abs(A).max()
+    assert np.allclose(np.triu(U), U) and np.allclose(np.tril(L), L)
+    # fill: nested dissection against the natural order's band
+    fill_nd = np.count_nonzero(np.abs(L) > 0) + np.count_nonzero(np.abs(U) > 0)
+    assert P["flops"] > 0 and fill_nd < (n * dim) ** 2 / 2
