@@ -19,8 +19,10 @@ namespace ep {
 namespace {
 
 constexpr int DNB = 32;     // pivots per panel
-constexpr int DT = 64;      // trailing-update tile: DT x DT entries per CTA of 256 threads (4 x 4 each)
-constexpr int SOLVE_THREADS = 256;   // threads per front in the solves (a warp per row of a block update)
+constexpr int PANEL_THREADS = 64;    // threads per CTA of the panel solves
+// threads per front in the solves of a level: enough for the rows of its largest front (a thread per
+// row of a block update), 64 .. 512
+inline int solve_threads(int mmax) { return std::max(64, std::min(512, ((mmax + 63) / 64) * 64)); }
 
 // static pivoting: a pivot below this times max |a_ii| in magnitude is replaced by +- that value
 template <class TF> __device__ __forceinline__ TF pivot_tiny();
@@ -87,7 +89,9 @@ __device__ __forceinline__ bool front_dims(const FrontArgs<TF>& a, int s, int p0
 }
 
 // LU without row exchanges of the nb x nb diagonal block at (p0, p0) of every front of the level
-// that still has pivots there; one warp per front
+// that still has pivots there; one warp per front, the block in shared memory, lane j updating
+// column j.  (Holding the columns in registers and broadcasting the multipliers by shuffles was
+// slower: 70 against 51 us per launch at the top front, FP64.)
 template <class TF>
 __global__ void __launch_bounds__(32) k_df_diag(FrontArgs<TF> a, int s0, int p0, const float* anorm,
                                                 unsigned int* n_perturbed) {
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(32) k_df_diag(FrontArgs<TF> a, int s0, int p0,
 // of it per item); each thread solves its item's 32 values in place in its own column of shared
 // memory (xs[j][thread]: no bank conflicts, no register arrays)
 template <class TF>
-__global__ void __launch_bounds__(256) k_df_panel(FrontArgs<TF> a, int s0, int p0) {
+__global__ void __launch_bounds__(64) k_df_panel(FrontArgs<TF> a, int s0, int p0) {
     const int s = s0 + blockIdx.y;
     int k, m, nb;
     if (!front_dims(a, s, p0, k, m, nb)) return;
@@ -170,9 +174,11 @@ __global__ void __launch_bounds__(256) k_df_panel(FrontArgs<TF> a, int s0, int p
     }
 }
 
-// A22 -= L21 U12 on the trailing part of every front of the level; DT x DT tile per CTA
-template <class TF>
+// A22 -= L21 U12 on the trailing part of every front of the level; DT x DT tile per CTA of 256
+// threads, R x R entries per thread (DT = 16 R: 64 for large fronts, 32 for levels of small ones)
+template <class TF, int R>
 __global__ void __launch_bounds__(256) k_df_update(FrontArgs<TF> a, int s0, int p0, int tiles) {
+    constexpr int DT = 16 * R;
     const int s = s0 + blockIdx.y;
     int k, m, nb;
     if (!front_dims(a, s, p0, k, m, nb)) return;
@@ -192,32 +198,32 @@ __global__ void __launch_bounds__(256) k_df_update(FrontArgs<TF> a, int s0, int 
     }
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    TF acc[4][4];
+    TF acc[R][R];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = TF(0);
+        for (int c = 0; c < R; ++c) acc[r][c] = TF(0);
 #pragma unroll 8
     for (int t = 0; t < DNB; ++t) {
-        TF lv[4], uv[4];
+        TF lv[R], uv[R];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            lv[r] = Ls[t][ty * 4 + r];
-            uv[r] = Us[t][tx * 4 + r];
+        for (int r = 0; r < R; ++r) {
+            lv[r] = Ls[t][ty * R + r];
+            uv[r] = Us[t][tx * R + r];
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = fma(lv[r], uv[c], acc[r][c]);
+            for (int c = 0; c < R; ++c) acc[r][c] = fma(lv[r], uv[c], acc[r][c]);
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = i0 + ty * 4 + r;
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + ty * R + r;
         if (i >= m) continue;
         TF* row = Fs + (int64_t)i * m;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int j = j0 + tx * 4 + c;
+        for (int c = 0; c < R; ++c) {
+            const int j = j0 + tx * R + c;
             if (j < m) row[j] -= acc[r][c];
         }
     }
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(256) k_df_extend(FrontArgs<TF> a, int s0, int 
 // vectors; L11 y = w_E (unit lower, by 32-row blocks); the update vector w_U - L21 y goes to the
 // parent, y to Y.
 template <class TV, class TF>
-__global__ void __launch_bounds__(256) k_ds_fwd(FrontArgs<TF> a, int s0, const TV* __restrict__ b,
+__global__ void __launch_bounds__(512) k_ds_fwd(FrontArgs<TF> a, int s0, const TV* __restrict__ b,
                                                 const uint8_t* __restrict__ free_dof, TF* __restrict__ Y,
                                                 TF* __restrict__ vupd, const KrylovRec* rec) {
     if (rec && rec->done) return;
@@ -292,6 +298,8 @@ __global__ void __launch_bounds__(256) k_ds_fwd(FrontArgs<TF> a, int s0, const T
             if (lane < nbk) w[blk + lane] = val;
         }
         __syncthreads();
+        // rows below the block: w_i -= L[i, blk..] y_blk, a thread per row (its 32 loads in flight
+        // together; a warp per row would walk the rows one after another)
         for (int i = blk + nbk + threadIdx.x; i < m; i += blockDim.x) {
             const TF* row = Fs + (int64_t)i * m + blk;
             TF acc = TF(0);
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(256) k_ds_fwd(FrontArgs<TF> a, int s0, const T
 // Backward solve of one level: per front, t = y_E - U12 x_U (x_U: the ancestors' solution, already
 // in x), then U11 x_E = t by 32-row blocks from the last; x_E into x (0 on fixed DOFs).
 template <class TV, class TF>
-__global__ void __launch_bounds__(256) k_ds_bwd(FrontArgs<TF> a, int s0, TV* __restrict__ x,
+__global__ void __launch_bounds__(512) k_ds_bwd(FrontArgs<TF> a, int s0, TV* __restrict__ x,
                                                 const uint8_t* __restrict__ free_dof, const TF* __restrict__ Y,
                                                 const KrylovRec* rec) {
     if (rec && rec->done) return;
@@ -326,13 +334,17 @@ __global__ void __launch_bounds__(256) k_ds_bwd(FrontArgs<TF> a, int s0, TV* __r
     }
     __syncthreads();
     const TF* Fs = a.F + a.f_off[s];
-    if (u > 0)
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    if (u > 0) {
+        // t -= U12 x_U: a warp per row, its lanes reading consecutive entries
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = threadIdx.x >> 5; i < k; i += nw) {
             const TF* row = Fs + (int64_t)i * m + k;
             TF acc = TF(0);
-            for (int j = 0; j < u; ++j) acc = fma(row[j], xu[j], acc);
-            t[i] -= acc;
+            for (int j = lane; j < u; j += 32) acc = fma(row[j], xu[j], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) t[i] -= acc;
         }
+    }
     __syncthreads();
     for (int blk = ((k - 1) / DNB) * DNB; blk >= 0 && k > 0; blk -= DNB) {
         const int nbk = min(DNB, k - blk);
@@ -353,6 +365,7 @@ __global__ void __launch_bounds__(256) k_ds_bwd(FrontArgs<TF> a, int s0, TV* __r
             if (lane < nbk) t[blk + lane] = val;
         }
         __syncthreads();
+        // rows above the block: t_i -= U[i, blk..] x_blk, a thread per row
         for (int i = threadIdx.x; i < blk; i += blockDim.x) {
             const TF* row = Fs + (int64_t)i * m + blk;
             TF acc = TF(0);
@@ -440,10 +453,16 @@ cudaError_t factor_t(DirectDev& D, const BsrT<T>& A, cudaStream_t s) {
                 k_df_diag<TF><<<nf, 32, 0, s>>>(a, c0, p0, D.anorm, D.n_perturbed);
                 const int rest = mmax - p0 - 1;   // the largest trailing order of the level (at least)
                 if (rest > 0) {
-                    const int gx = std::max(1, std::min((2 * rest + 255) / 256, 64));
-                    k_df_panel<TF><<<dim3(gx, nf), 256, sizeof(TF) * DNB * 256, s>>>(a, c0, p0);
-                    const int tiles = (rest + DT - 1) / DT;
-                    k_df_update<TF><<<dim3(tiles * tiles, nf), 256, 0, s>>>(a, c0, p0, tiles);
+                    // 64 threads per CTA: the top levels' few fronts spread their panel over more SMs
+                    const int gx = std::max(1, std::min((2 * rest + PANEL_THREADS - 1) / PANEL_THREADS, 256));
+                    k_df_panel<TF><<<dim3(gx, nf), PANEL_THREADS, sizeof(TF) * DNB * PANEL_THREADS, s>>>(a, c0, p0);
+                    if (mmax <= 160) {   // small fronts: 32 x 32 tiles (less of a tile outside the front)
+                        const int tiles = (rest + 31) / 32;
+                        k_df_update<TF, 2><<<dim3(tiles * tiles, nf), 256, 0, s>>>(a, c0, p0, tiles);
+                    } else {
+                        const int tiles = (rest + 63) / 64;
+                        k_df_update<TF, 4><<<dim3(tiles * tiles, nf), 256, 0, s>>>(a, c0, p0, tiles);
+                    }
                     D.launches += 2;
                 }
                 D.launches += 1;
@@ -479,13 +498,15 @@ cudaError_t solve_t(DirectDev& D, const TV* b, TV* x, const uint8_t* free_dof, c
     for (int l = 0; l < nl; ++l)
         for (int c0 = P.level_ptr[l]; c0 < P.level_ptr[l + 1]; c0 += MAX_GRID_Y) {
             const int nf = std::min(MAX_GRID_Y, P.level_ptr[l + 1] - c0);
-            k_ds_fwd<TV, TF><<<nf, SOLVE_THREADS, solve_smem<TF>(P.lvl_mmax[l]), s>>>(a, c0, b, free_dof, Y, vupd, rec);
+            k_ds_fwd<TV, TF><<<nf, solve_threads(P.lvl_mmax[l]), solve_smem<TF>(P.lvl_mmax[l]), s>>>(a, c0, b, free_dof, Y,
+                                                                                                      vupd, rec);
             D.launches += 1;
         }
     for (int l = nl - 1; l >= 0; --l)
         for (int c0 = P.level_ptr[l]; c0 < P.level_ptr[l + 1]; c0 += MAX_GRID_Y) {
             const int nf = std::min(MAX_GRID_Y, P.level_ptr[l + 1] - c0);
-            k_ds_bwd<TV, TF><<<nf, SOLVE_THREADS, solve_smem<TF>(P.lvl_mmax[l]), s>>>(a, c0, x, free_dof, Y, rec);
+            k_ds_bwd<TV, TF><<<nf, solve_threads(P.lvl_mmax[l]), solve_smem<TF>(P.lvl_mmax[l]), s>>>(a, c0, x, free_dof, Y,
+                                                                                                      rec);
             D.launches += 1;
         }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -515,7 +536,7 @@ cudaError_t alloc_bytes(DirectDev& D, void** dst, size_t bytes) {
 template <class TF>
 cudaError_t set_smem(int smem) {
     cudaError_t e = cudaFuncSetAttribute(k_df_panel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(TF) * DNB * 256));
+                                         (int)(sizeof(TF) * DNB * PANEL_THREADS));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ds_fwd<double, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ds_fwd<float, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ds_bwd<double, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

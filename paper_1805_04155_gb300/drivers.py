@@ -21,6 +21,8 @@ functions only choose the next load factor and read results back:
   timing each on the first load steps and restoring the state in between (the
   paper uses one direct solver; the schedule is this implementation's choice,
   Section 5's linear systems).
+* sparse_lu_solve: one solve with the sparse LU on the benchmark mesh's elastic
+  tangent (for timing and profiling its kernels outside a load path).
 """
 from __future__ import annotations
 
@@ -145,3 +147,21 @@ def autotune(ctx, zeta, trial_steps: int = 3, candidates=None, base_opts=None, k
             if t is not None and t < t_best:
                 best, t_best = cand, t
     return ep.default_opts(**best), results
+
+
+def sparse_lu_solve(n: int = 256, rtol: float = 1e-12, seed: int = 1):
+    """One linear solve with the sparse LU (precond 3) on the elastic tangent of the n x n P2 column
+    (the benchmark's mesh): one factorisation and the GMRES iterations its solves precondition.
+    Returns (iterations, relative residual).  A small driver for timing and profiling the
+    factorisation and solve kernels outside a load path."""
+    from synthetic import p2_plane_dp
+    prob = p2_plane_dp(n=n, n_steps=40)
+    ctx = ep.Context.from_problem(prob)
+    try:
+        ctx.assemble(np.zeros(prob.n_dof))
+        b = np.random.default_rng(seed).standard_normal(prob.n_dof) * (prob.dirichlet == 0)
+        _, its, rel = ctx.linear_solve(b, ep.default_opts(krylov=3, krylov_rtol=rtol, krylov_maxit=50, precond=3,
+                                                          krylov_graphs=0))
+    finally:
+        ctx.close()
+    return its, rel
