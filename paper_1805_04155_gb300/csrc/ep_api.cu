@@ -892,7 +892,8 @@ constexpr int DIRECT_LEAF = 16;
 constexpr double DIRECT_ETA = 1e-13;
 
 // The sparse LU's symbolic analysis (host) and device memory, on first use; false (reason in
-// c->direct.why) when the factors would not fit in 60% of the free device memory.
+// c->direct.why) when the factors would not fit in 60% of the free device memory (or in
+// EP_DIRECT_MAX_MB MiB).
 static bool ensure_direct(Ctx* c) {
     if (c->direct.ready) return true;
     if (c->direct.refused) return false;
@@ -910,7 +911,9 @@ static bool ensure_direct(Ctx* c) {
     c->direct.fp64 = (f32 && std::atoi(f32) == 1) ? 0 : 1;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
-    if (!direct_setup(c->direct, (int64_t)(0.6 * (double)fr))) return false;
+    int64_t cap = (int64_t)(0.6 * (double)fr);
+    if (const char* mb = std::getenv("EP_DIRECT_MAX_MB")) cap = std::min<int64_t>(cap, (int64_t)std::atoll(mb) << 20);
+    if (!direct_setup(c->direct, cap)) return false;
     c->kw.direct = &c->direct;
     c->direct_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (c->verbose) {

@@ -1,4 +1,4 @@
-"""The sparse LU (precond 3: multifrontal, nested-dissection order, FP32 factors with static
+"""The sparse LU (precond 3: multifrontal, nested-dissection order, FP64 fronts with static
 pivoting, refined by FP64 GMRES) against sparse direct solves and the oracle, and the Newton loop's
 switch to it near the limit load of the nonassociated Drucker-Prager column (Section 2.3)."""
 import numpy as np
@@ -30,7 +30,7 @@ SIZES = {("P1", 2): 10, ("P2", 2): 8, ("Q1", 2): 10, ("Q2", 2): 6, ("P1", 3): 4,
 @pytest.mark.parametrize("elem,dim", ALL_ELEMS)
 def test_sparse_lu_solve_matches_a_direct_solve(ep, elem, dim, model):
     """GMRES with the sparse LU reaches 1e-13 within a few iterations on a plastic tangent of every
-    element type and matches scipy's sparse direct solve (the FP32 factors only precondition)."""
+    element type and matches scipy's sparse direct solve."""
     import scipy.sparse.linalg as spla
     prob = small_problem(elem, dim, SIZES[(elem, dim)], model, seed=11)
     u, ep_, hard = fed_iterate(prob, seed=12, dilate=(1.0e-3 if model == DP else 0.0))
@@ -148,3 +148,34 @@ def test_full_size_p2_column_to_098_of_the_limit_load(ep):
         assert reps[-1].direct == 1 and reps[0].direct == 0
     ctx.close()
     assert errs[1] < 0.2 * errs[0]
+
+
+def test_sparse_lu_refused_when_its_factors_do_not_fit(ep, monkeypatch):
+    """precond 3 with the factors capped below their size: ep_linear_solve reports EP_ERR_STATE with
+    the reason, and the context stays usable (a block-Jacobi solve afterwards succeeds)."""
+    monkeypatch.setenv("EP_DIRECT_MAX_MB", "0")
+    prob = small_problem("P2", 2, 12, DP, seed=21)
+    ctx = ep.Context.from_problem(prob)
+    ctx.assemble(np.zeros(prob.n_dof))
+    b = np.random.default_rng(22).standard_normal(prob.n_dof) * (prob.dirichlet == 0)
+    with pytest.raises(ep.EPError) as ei:
+        ctx.linear_solve(b, ep.default_opts(krylov=3, krylov_rtol=1e-10, krylov_maxit=200, precond=3))
+    assert ei.value.status == ep.EP_ERR_STATE and "MiB" in str(ei.value)
+    x, its, rel = ctx.linear_solve(b, ep.default_opts(krylov=3, krylov_rtol=1e-10, krylov_maxit=5000, precond=1))
+    assert rel <= 1e-10
+    ctx.close()
+
+
+def test_sparse_lu_path_repeats_bit_for_bit_in_the_deterministic_form(ep):
+    """The factorisation sums in a fixed order (extend-add by child rank, no atomics): with the
+    deterministic form a load path solved with the sparse LU repeats bit for bit."""
+    from synthetic import p2_plane_dp
+    prob = p2_plane_dp(n=12, n_steps=10, load_fraction=0.98)
+    out = []
+    for _ in range(2):
+        ctx = ep.Context.from_problem(prob)
+        ctx.solve_load_path(prob.zeta, ep.default_opts(newton_rtol=1e-12, newton_maxit=40, precond=3,
+                                                       deterministic=1))
+        out.append((ctx.get(ep.EP_U), ctx.get(ep.EP_STRESS)))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
