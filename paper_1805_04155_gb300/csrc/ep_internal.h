@@ -231,6 +231,10 @@ struct KrylovWork {
     // and cap) live in gdyn on the device
     int graphs = 0;
     double* gdyn = nullptr;            // device [3]: rtol^2, iterations before this cycle, cap
+    // GMRES with the sparse LU keeps z_j = M^-1 v_j of the cycle ([z_cap][n], allocated on first
+    // use) and updates x += Z y: no preconditioner solve at the end of a cycle
+    void* Z = nullptr;
+    int z_cap = 0, z_bytes = 0;
     cudaStream_t cap_stream = nullptr; // private stream the captures are made on
     std::vector<cudaGraphExec_t> gexec;
     std::vector<int> gexec_launches;   // kernels inside each graph

@@ -578,6 +578,7 @@ void krylov_free(KrylovWork& w) {
         if (ev) cudaEventDestroy(ev);
     drop_graphs(w);
     if (w.gdyn) cudaFree(w.gdyn);
+    if (w.Z) cudaFree(w.Z);
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     w = KrylovWork{};
 }
@@ -1079,6 +1080,20 @@ __global__ void __launch_bounds__(VB) k_gm_combine(GArgs<TX, TV> a, int k, TV* _
     }
 }
 
+// x += Z_k y (Z: the cycle's preconditioned vectors z_j = M^-1 v_j; y = R^-1 g solved by every CTA)
+template <int D, class TX, class TV>
+__global__ void __launch_bounds__(VB) k_gm_zupdate(GArgs<TX, TV> a, int k, const TV* __restrict__ Z) {
+    pdl_enter();
+    __shared__ TV y[GM_M];
+    gm_solve_y(a, k, y);
+    const int64_t n = a.n_rows * D;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        TV s = TV(0);
+        for (int i = 0; i < k; ++i) s += y[i] * Z[(int64_t)i * n + t];
+        a.x[t] += (TX)s;
+    }
+}
+
 // x += z (z of the basis precision)
 template <class TX, class TV>
 __global__ void k_axpy_plain(TX* __restrict__ x, const TV* __restrict__ z, int64_t n) {
@@ -1127,13 +1142,28 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
     const bool use_direct = w.use_direct && w.direct;
     const bool use_op = use_amg || use_direct;   // an operator preconditioner (z = M^-1 v by its own kernels)
     int total = 0;
+    // sparse LU: z_j kept in Z (allocated on first use, reallocated for a longer restart)
+    TV* Zb = nullptr;
+    if (use_direct) {
+        if (!w.Z || w.z_cap < a.m || w.z_bytes != (int)sizeof(TV)) {
+            if (w.Z) cudaFree(w.Z);
+            w.Z = nullptr;
+            cudaError_t e = cudaMalloc(&w.Z, sizeof(TV) * (size_t)a.m * (size_t)w.n);
+            if (e != cudaSuccess) return e;
+            w.z_cap = a.m;
+            w.z_bytes = (int)sizeof(TV);
+            drop_graphs(w);   // captured iterations name the old buffer
+        }
+        Zb = static_cast<TV*>(w.Z);
+    }
     // the launches of iteration j of a cycle (direct, or into a capture)
     auto issue = [&](const GArgs<TX, TV>& ga, int j, cudaStream_t st, int& nev) {
-        if (use_op) prec_apply_t(w, A, ga.V + (int64_t)j * w.n, ga.z, w.rec, st);
+        TV* zj = use_direct ? Zb + (int64_t)j * w.n : ga.z;
+        if (use_op) prec_apply_t(w, A, ga.V + (int64_t)j * w.n, zj, w.rec, st);
         else launch_pdl(k_gm_prec<D, TX, TV>, dim3(grid), dim3(VB), 0, st, ga, j);
         const bool ev_ok = w.profile && nev + 2 <= (int)(sizeof(w.ev) / sizeof(w.ev[0]));
         if (ev_ok) cudaEventRecord(w.ev[nev++], st);
-        launch_spmv<D, TA, TV, TV>(A, ga.z, ga.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, st);
+        launch_spmv<D, TA, TV, TV>(A, zj, ga.V + (int64_t)(j + 1) * w.n, nullptr, nullptr, w.rec, grid, st);
         if (ev_ok) cudaEventRecord(w.ev[nev++], st);
         // one resident wave (FP32: 61 registers, 2 CTAs per SM); FP64: one CTA per SM, fewer
         // cross-lane FP64 adds
@@ -1161,10 +1191,11 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
     }
     KrylovRec last{};
     double rr_prev_end = 0.0;   // residual estimate ||r||^2 at the end of the previous cycle
-    // FP32 basis: re-check a converged estimate once (see solve_t).  Sparse LU: its FP32 solve is not
-    // linear in rounding, so the update M^-1 (V y) differs from the combination of the M^-1 v_j the
-    // Arnoldi relation holds for by O(u32) of the correction; a tight solve restarts once from its x
-    // (FP64 residual b - A x; a second cycle refines what the FP32 factors left)
+    // FP32 basis: re-check a converged estimate once (see solve_t).  Sparse LU: a tight solve restarts
+    // once from its x, so that the FP64 residual b - A x, not the Arnoldi estimate, ends it.  (Its
+    // update is x += Z y with the stored z_j = M^-1 v_j, consistent with the Arnoldi relation; the
+    // first form, x += M^-1 (V y), carried the rounding of an FP32 solve of the combination: 5e-7
+    // instead of 1e-13.)
     int n_verify = (sizeof(TV) == 4 || (use_direct && rtol < 1e-5)) ? 1 : 0;
     for (int cycle = 0;; ++cycle) {
         a.cold = (cycle == 0);
@@ -1244,10 +1275,12 @@ static cudaError_t solve_gmres_t(const BsrT<TA>& A, KrylovWork& w, const TX* b, 
             std::fprintf(stderr, "[ep]   gmres cycle %d: its %d, host enqueue %.3f ms, wait %.3f ms\n", cycle,
                          last.its, t_enq, t_wait);
         if (last.its > 0) {
-            if (use_op) {
+            if (use_direct) {
+                launch_pdl(k_gm_zupdate<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, last.its, (const TV*)Zb);
+                w.launches += 1;
+            } else if (use_op) {
                 launch_pdl(k_gm_combine<D, TX, TV>, dim3(grid), dim3(VB), 0, s, a, last.its, vv.q);
                 prec_apply_t(w, A, vv.q, vv.z, nullptr, s);
-                if (use_direct) w.direct->n_solve += 1;
                 launch_pdl(k_axpy_plain<TX, TV>, dim3(grid), dim3(VB), 0, s, vx.x, vv.z, w.n);
                 w.launches += 2;
             } else {
