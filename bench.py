@@ -390,7 +390,7 @@ def run_batch(args):
             "one_by_one_newton_its": int(sum(r.newton_its for rs in reps_single for r in rs)) if singles else None}
     if args.learned:
         line["learned"] = learned_start_batch(args, ep, ctxs, groups, fams, zeta, opts, reset, results)
-        # the benchmark spec's combined form (mixed precision, batched, learned start) against the plain
+        # the combined form (mixed precision, batched, learned start) against the plain
         # FP64 GPU form (batched, extrapolated start) on time to solution at the same tolerance
         line["combined_vs_fp64"] = {"fp64_batched_s": t_batch, "mixed_batched_s": t_batch_mixed,
                                     "fp64_learned_batched_s": line["learned"]["batched_s"],
