@@ -1565,7 +1565,7 @@ ep_status ep_solve_load_path(void* ctx, int32_t n_steps, const double* zeta, con
             // with no plastic point the tangent is K_elast, symmetric: CG suffices even for a
             // nonassociated model
             // the preconditioner of this solve: the sparse LU once the path has switched to it (with
-            // GMRES: its FP32 factors are not symmetric in rounding)
+            // GMRES: its factors are not symmetric in rounding)
             const int pk = c->direct_mode ? 3 : o.precond;
             const int m_it = pk == 3 ? 3 : (o.krylov == 0 && *c->counter_host == 0) ? 1 : method;
             // the mixed path's FP64-tangent iterations solve with GMRES on the FP64 operator and an
