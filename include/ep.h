@@ -119,11 +119,12 @@ typedef struct {
     int32_t krylov_maxit;
     int32_t precond;             /* 0 Jacobi, 1 block Jacobi (dim x dim node blocks), 2 smoothed-aggregation AMG
                                     (built from K_elast on first use; Chebyshev/block-Jacobi smoothing),
-                                    3 sparse LU of the tangent (multifrontal, nested-dissection order, FP32
+                                    3 sparse LU of the tangent (multifrontal, nested-dissection order, FP64
                                     factors with static pivoting, refactored at every Newton iteration; with
                                     GMRES, which refines to the FP64 tolerance).  The paper solves eq.
                                     (lin_syst) directly; 3 is its counterpart here.  Set up on first use:
-                                    EP_ERR_STATE if the factors would not fit in 60% of the free device memory */
+                                    EP_ERR_STATE if the factors would not fit in 60% of the free device memory
+                                    or a front exceeds the solve's shared-memory limit (order 24 000) */
     int32_t split_elastic_cache; /* 1: K = K_elast + sum over plastic points (eq. (K-split)); 0: K = B^T D B */
     int32_t warm_start;          /* 0: last converged u; 1: linear extrapolation of the last two steps;
                                     2: the extrapolation corrected by the attached warm-start network
