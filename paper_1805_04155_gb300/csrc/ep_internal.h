@@ -255,6 +255,9 @@ void krylov_free(KrylovWork& w);
 // LU of w.direct, which must be set up) in A's precision.
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s);
 cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t s);
+// The sparse LU's current factors (of an earlier matrix) as the preconditioner of the next solve,
+// without refactoring; false if none have been computed.
+bool krylov_keep_direct(KrylovWork& w);
 // Solves A x = b on the free DOFs; x starts at zero.  method 1 CG, 2 BiCGStab, 3 GMRES(m).
 // The FP64 overload works on w.d, the FP32 overload on w.f (solution in w.f.x).
 // Returns cudaSuccess; *status receives EP_OK / EP_ERR_KRYLOV / EP_ERR_NAN.

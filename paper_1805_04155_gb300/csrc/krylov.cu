@@ -614,6 +614,13 @@ static cudaError_t precond_t(const BsrT<T>& A, KrylovWork& w, int kind, cudaStre
 cudaError_t krylov_precond(const BsrDev& A, KrylovWork& w, int kind, cudaStream_t s) { return precond_t(A, w, kind, s); }
 cudaError_t krylov_precond(const BsrF& A, KrylovWork& w, int kind, cudaStream_t s) { return precond_t(A, w, kind, s); }
 
+bool krylov_keep_direct(KrylovWork& w) {
+    if (!w.direct || !w.direct->ready || w.direct->n_factor == 0) return false;
+    w.use_direct = 1;
+    w.use_amg = 0;
+    return true;
+}
+
 // y = P A x with A's values TA (accumulation in TA), x and y of their own types
 template <int D, class TA, class TX, class TY>
 static void launch_spmv(const BsrT<TA>& A, const TX* x, TY* y, const TY* dv, double* part, const KrylovRec* rec,
